@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark of the per-level switched BFS on GB300.
+
+Workload: R-MAT scale 22, edge factor 16 (a/b/c/d = .57/.19/.19/.05),
+symmetrised and deduplicated (4,194,304 vertices, ~128M directed edges), 64
+seeded roots in the giant component. One step = one switched BFS from each
+root (the whole hot path: init, per-level tree decision on the device, level
+kernels). Reported value: GTEPS, harmonic mean over the roots, GTEPS_i =
+(edges_reached_i / 2) / t_i / 1e9 with t_i the device time of run i (CUDA
+events on the launching stream, depth init included, graph upload excluded).
+
+Also reported on the same line: every fixed variant on the same roots, the
+end-to-end number through the C ABI with host output buffers, the roofline of
+the dominant kernel, the CPU oracle baseline and the SM clocks seen while
+timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFS GTEPS (harmonic mean, 16 roots) vs best fixed kernel; serve p50/p99 ms"
+UNIT = "GTEPS"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--roots", type=int, default=64)
+    p.add_argument("--scale", type=int, default=22)
+    p.add_argument("--edge-factor", type=int, default=16)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fixed", action="store_true")
+    p.add_argument("--no-roofline", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.25)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_workload(args, rank):
+    import graphgen as gg
+    g = gg.rmat(args.scale, args.edge_factor, seed=gg.SEED_GRAPH + 1)
+    roots = gg.sample_roots(g, args.roots, seed=gg.SEED_ROOTS + 1 + 100 * rank, giant=True)
+    return g, roots
+
+
+def workload_name(args, g):
+    return (f"R-MAT scale {args.scale} edge factor {args.edge_factor} (a/b/c/d .57/.19/.19/.05, symmetrised, "
+            f"deduplicated): {g.n:,} vertices, {g.m:,} directed edges; {args.roots} roots in the giant component")
+
+
+def harmonic_gteps(times_s, edges):
+    """k / sum(1 / GTEPS_i), GTEPS_i = (edges_i / 2) / t_i / 1e9."""
+    inv = [t / (e / 2.0 / 1e9) for t, e in zip(times_s, edges)]
+    return len(inv) / sum(inv)
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    """The CPU oracle, as it stands, timed on the host: each step is one root."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    g, roots = make_workload(args, 0)
+    times, edges = [], []
+    for step in range(args.warmup + args.steps):
+        r = int(roots[step % len(roots)])
+        t0 = time.perf_counter()
+        res = oracle.bfs(g.off, g.idx, r)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            edges.append(res.edges_reached)
+    value = harmonic_gteps(times, edges)
+    sample = f"{args.steps} single-root traversals (one per step) of the {args.roots}-root workload"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": workload_name(args, g), "roots_per_step": 1},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def algorithmic_bytes(g, depth, feats, L, variant):
+    """Bytes level L must move for the variant that expanded it (HBM traffic the
+    method needs; the visited bitmaps, n/8 bytes, stay in L2 and are not counted)."""
+    n = g.n
+    F_FRONTIER, F_DISC, F_FE = 8, 10, 12
+    f = int(feats[L][F_FRONTIER])
+    nxt = int(feats[L + 1][F_FRONTIER]) if L + 1 < len(feats) else 0
+    if variant != 4:  # push: queue read, row extents, adjacency, depth + queue writes, degree of new vertices
+        e = int(feats[L][F_FE])
+        return 4 * f + 8 * f + 4 * e + 4 * nxt + 4 * nxt + 8 * nxt
+    # pull: bitmap words read/written, row extents of unvisited vertices, the
+    # adjacency entries scanned up to the first frontier neighbour, writes
+    words = (n + 31) // 32
+    unvis = (depth < 0) | (depth > L)
+    deg = np.diff(g.off.astype(np.int64))
+    hit = depth[g.idx] == L
+    pos = np.arange(g.m, dtype=np.int64)
+    cand = np.where(hit, pos, np.int64(g.m + 1))
+    rows = np.nonzero(unvis & (deg > 0))[0]
+    first = np.minimum.reduceat(cand, g.off[:-1].astype(np.int64)[rows]) if rows.size else np.zeros(0, np.int64)
+    # reduceat over the selected starts spans to the next selected start; clip to the row end
+    ends = g.off[1:].astype(np.int64)[rows]
+    starts = g.off[:-1].astype(np.int64)[rows]
+    scanned = np.where(first < ends, first - starts + 1, ends - starts)
+    return 8 * words + 4 * int(unvis.sum()) + 4 * int(scanned.sum()) + 8 * nxt
+
+
+def traffic_for(kernel_key):
+    """Per-launch DRAM bytes from a committed ncu summary, if it still matches the kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        import hashlib
+        d = json.load(open(path))
+        src = os.path.join(ROOT, "paper_1708_01159_gb300", "csrc", "bfs_kernels.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("kernels_sha") != h:
+            return None
+        return d.get("per_launch_bytes", {}).get(kernel_key)
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1708_01159_gb300 as bfs
+
+    g, roots = make_workload(args, rank)
+    R = len(roots)
+    G = bfs.Graph(g.off, g.idx)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    depth = [torch.empty(g.n, dtype=torch.int32, device=dev) for _ in range(2)]
+    stream = torch.cuda.current_stream()
+
+    # per-root edges and levels (one stats run each, untimed)
+    edges, launches = [], 0
+    for r in roots:
+        st = bfs.bfs_run_ex(G.handle, int(r), depth[0], stats=True, log_capacity=4096)
+        edges.append(st["edges_reached"])
+        kern = {0: 1, 1: 1, 2: 1, 3: 4, 4: 1}
+        launches += 1 + 1 + sum(1 + kern[int(v)] for v in st["variant"])  # init, final decide, per level
+    edges = np.array(edges, dtype=np.int64)
+
+    def step(forced=-1):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(R + 1)]
+        # hold the stream while the host enqueues the whole step, so host-side
+        # launch overhead never shows up inside a timed interval
+        torch.cuda._sleep(20_000_000)
+        evs[0].record(stream)
+        for i, r in enumerate(roots):
+            if forced < 0:
+                bfs.bfs_run(G.handle, int(r), depth[i & 1], stream)
+            else:
+                bfs.bfs_run_ex(G.handle, int(r), depth[i & 1], stream, forced_variant=forced)
+            evs[i + 1].record(stream)
+        return evs
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    all_evs = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    times = []
+    for evs in all_evs:
+        times += [evs[i].elapsed_time(evs[i + 1]) * 1e-3 for i in range(R)]
+    total_s = sum(times)
+    value_local = harmonic_gteps(times, np.tile(edges, args.steps))
+    total_edges_local = float(edges.sum()) * args.steps / 2.0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e = torch.tensor([total_edges_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+        value = float(e.item()) / float(t.item()) / 1e9
+        total_s = float(t.item())
+    else:
+        value = value_local
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": workload_name(args, g), "roots": R, "switching": "decision tree on the device",
+                   "l2": "inputs larger than L2 (CSR %.0f MB vs 129 MB L2)" % ((g.off.nbytes + g.idx.nbytes) / 1e6),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+
+    # every fixed variant on the same roots (the "best fixed kernel" comparison)
+    if not args.no_fixed:
+        fixed = {}
+        for v, name in enumerate(bfs.VARIANTS):
+            step(v)
+            torch.cuda.synchronize()
+            evs = step(v)
+            torch.cuda.synchronize()
+            ts = [evs[i].elapsed_time(evs[i + 1]) * 1e-3 for i in range(R)]
+            fixed[name] = harmonic_gteps(ts, edges)
+        best = max(fixed, key=fixed.get)
+        line["fixed_variants_gteps"] = fixed
+        line["best_fixed"] = {"variant": best, "gteps": fixed[best], "switched_over_best_fixed": value_local / fixed[best]}
+
+    # end to end through the C ABI with host output buffers (pinned), copies timed
+    pinned = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    bfs.bfs_run_ex(G.handle, int(roots[0]), pinned, stream, depth_on_host=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in roots:
+        bfs.bfs_run_ex(G.handle, int(r), pinned, stream, depth_on_host=True)
+    e2e_s = time.perf_counter() - t0
+    line["e2e"] = {"value": float(edges.sum()) / 2.0 / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * R,
+                   "d2h_bytes_per_step": 4 * g.n * R,
+                   "note": "one step: every root, depth copied to pinned host memory inside the timed region"}
+
+    # roofline of the dominant kernel: per-level launches timed with CUDA events
+    # on the launching stream (per-level harness, same state for every variant)
+    if not args.no_roofline:
+        hbm, src = peaks()
+        r0 = int(roots[0])
+        feats, ms, tv = bfs.bfs_profile_levels(G.handle, r0, reps=5, stream=stream)
+        chosen = np.array([ms[L, tv[L]] for L in range(len(tv))])
+        L = int(np.argmax(chosen))
+        v = int(tv[L])
+        bfs.bfs_run(G.handle, r0, depth[0], stream)
+        torch.cuda.synchronize()
+        dep = depth[0].cpu().numpy()
+        nbytes = algorithmic_bytes(g, dep, feats, L, v)
+        t = float(chosen[L]) * 1e-3
+        achieved = nbytes / t / 1e9
+        key = f"{bfs.VARIANTS[v]}"
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                            "traffic": traffic_for(key), "peak_source": src,
+                            "kernel": f"{bfs.VARIANTS[v]} at level {L} of root {r0}",
+                            "algorithmic_bytes": int(nbytes), "launch_ms": float(chosen[L]),
+                            "share_of_traversal": float(chosen[L] / chosen.sum()),
+                            "per_level_ms_chosen": [round(float(x), 4) for x in chosen],
+                            "per_level_optimal_ms": float(ms.min(axis=1).sum()),
+                            "per_level_tree_ms": float(chosen.sum())}
+
+    # the oracle on the host, bounded sample (rank 0, one GPU)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        ts, es = [], []
+        t_start = time.perf_counter()
+        for r in roots:
+            t0 = time.perf_counter()
+            res = oracle.bfs(g.off, g.idx, int(r))
+            ts.append(time.perf_counter() - t0)
+            es.append(res.edges_reached)
+            if time.perf_counter() - t_start > 10.0 or len(ts) >= 8:
+                break
+        line["cpu_baseline"] = {"value": harmonic_gteps(ts, es), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{len(ts)} of the {R} roots, single-threaded FIFO BFS on the same graph"}
+
+    G.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

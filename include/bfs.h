@@ -1,0 +1,216 @@
+/*
+ * bfs.h -- C ABI of the GB300 level-synchronous BFS library (libbfs.so).
+ *
+ * The operation (Section 2.2 of "Using Graph Properties to Speed-up GPU-based
+ * Graph Traversal: A Model-driven Approach", Verstraaten, Varbanescu, de Laat):
+ * given a graph and a root vertex, find every vertex reachable from the root
+ * and its shortest hop distance. The traversal is level-synchronous (Section
+ * 3.1): depths start at "infinity" (written -1 here), the root at 0, and level
+ * L expands every vertex at depth L, assigning L + 1 to newly reached
+ * vertices, until a level discovers nothing. At every level a binary decision
+ * tree (Section 2.1, Section 4.1) over graph and frontier properties chooses
+ * the kernel that expands the level; the choice is made on the device, so no
+ * host round trip separates levels.
+ *
+ * Conventions for every entry point:
+ *   - Return value: BFS_OK (0) or one of the BFS_ERR_* codes; no exception
+ *     crosses this boundary. bfs_status_string() names a code and
+ *     bfs_last_error_detail() gives the calling thread's last failure text.
+ *   - Vertex ids are int32 in [0, n); the CSR uses int32 offsets and indices
+ *     (m < 2^31). Depth is int32, -1 for unreached vertices.
+ *   - "device" pointers are CUDA global-memory pointers of the current device;
+ *     "host" pointers are ordinary CPU memory.
+ *   - Runs are stream-ordered and asynchronous unless stated otherwise.
+ *   - A bfs_graph_t may be used from several threads; each run takes its own
+ *     workspace from a per-graph pool, so concurrent runs on distinct streams
+ *     are safe as long as their depth outputs do not alias.
+ */
+#ifndef BFS_GB300_H
+#define BFS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* bfs_stream_t;
+
+typedef struct bfs_graph* bfs_graph_t;
+
+enum bfs_status {
+  BFS_OK = 0,
+  BFS_ERR_INVALID_ARG = 1, /* null pointer, negative size, root out of range, bad option */
+  BFS_ERR_BAD_GRAPH = 2,   /* CSR malformed: off[0] != 0, off decreasing, off[n] != m, idx out of range */
+  BFS_ERR_OOM = 3,         /* a device or host allocation failed */
+  BFS_ERR_CUDA = 4,        /* a CUDA runtime call failed; see bfs_last_error_detail() */
+  BFS_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (reported through a status word) */
+  BFS_ERR_BUSY = 6,        /* a queue or pool is full; retry later */
+  BFS_ERR_CANCELLED = 7,   /* work was cancelled before it ran */
+  BFS_ERR_NOT_FOUND = 8,   /* unknown ticket, graph id or file */
+};
+
+/* Variants a level can run (the classes the decision tree predicts). */
+enum bfs_variant {
+  BFS_VARIANT_TREE = -1,        /* let the decision tree choose per level (default) */
+  BFS_VARIANT_PUSH_THREAD = 0,  /* top-down, one thread per frontier vertex (Section 3.1.2, vertex push) */
+  BFS_VARIANT_PUSH_WARP = 1,    /* top-down, virtual warp per frontier vertex (Section 3.1.3) */
+  BFS_VARIANT_PUSH_CTA = 2,     /* top-down, one CTA per frontier vertex, adjacency staged in shared memory */
+  BFS_VARIANT_PUSH_EDGE = 3,    /* top-down, one thread per frontier edge (Section 3.1.1, edge list) */
+  BFS_VARIANT_PULL = 4,         /* bottom-up over the visited bitmap, early exit (Section 3.1.2, vertex pull) */
+  BFS_NUM_VARIANTS = 5,
+};
+
+/* Flags of bfs_graph_create. */
+enum bfs_graph_flags {
+  BFS_SYMMETRIC = 1u,       /* caller asserts every edge u->v has v->u; pull then reuses the CSR */
+  BFS_INPUT_ON_DEVICE = 2u, /* row_offsets / col_indices are device pointers (else host) */
+  BFS_VALIDATE = 4u,        /* accepted for clarity: the CSR is always validated on the device */
+};
+
+/* Feature vector layout of the decision tree (Section 4.1 features). */
+enum bfs_feature {
+  BFS_F_N = 0, BFS_F_M = 1, BFS_F_DEG_MIN = 2, BFS_F_DEG_Q1 = 3, BFS_F_DEG_MED = 4, BFS_F_DEG_Q3 = 5,
+  BFS_F_DEG_MAX = 6, BFS_F_DEG_SD256 = 7, BFS_F_FRONTIER = 8, BFS_F_FRONTIER_PPM = 9, BFS_F_DISCOVERED = 10,
+  BFS_F_DISCOVERED_PPM = 11, BFS_F_FRONTIER_EDGES = 12, BFS_F_LEVEL = 13, BFS_NUM_FEATURES = 14,
+};
+
+typedef struct bfs_graph_info {
+  int64_t n;                 /* vertices */
+  int64_t m;                 /* directed CSR entries */
+  int64_t deg_summary[5];    /* out-degree min, Q1, median, Q3, max: sorted[floor(k (n-1) / 4)] */
+  int64_t deg_sd256;         /* floor(256 * population standard deviation of out-degree) */
+  int64_t bytes_resident;    /* device bytes held by the graph (CSR, transpose, stats) */
+  int32_t symmetric;         /* 1 if pull reuses the CSR, 0 if a transpose was built */
+  int32_t num_workspaces;    /* per-run workspaces currently allocated */
+} bfs_graph_info_t;
+
+typedef struct bfs_options {
+  int32_t forced_variant;    /* BFS_VARIANT_TREE or a fixed bfs_variant for every level */
+  int32_t depth_on_host;     /* 1: depth_out is host memory; the library copies the result there */
+  int32_t reserved[6];       /* must be zero */
+} bfs_options;
+
+typedef struct bfs_run_stats {
+  int64_t edges_reached;     /* sum of out-degrees of reached vertices */
+  int64_t vertices_reached;  /* vertices with depth >= 0 */
+  int32_t levels;            /* nonempty levels (max depth + 1) */
+  int32_t status;            /* device-side status word (BFS_OK or BFS_ERR_TIMEOUT) */
+  /* Per-level log, optional (set pointers to NULL to skip). Entry L describes
+   * the frontier of level L and the variant that expanded it. At most
+   * log_capacity entries are written; levels beyond it are counted only. */
+  int32_t log_capacity;
+  int32_t* log_variant;      /* host, log_capacity entries */
+  int64_t* log_frontier;     /* host, vertices in the frontier of level L */
+  int64_t* log_frontier_edges; /* host, sum of out-degrees over that frontier */
+} bfs_run_stats;
+
+/* Text of a status code (static storage). */
+const char* bfs_status_string(int status);
+
+/* Detail of the calling thread's last failure (thread-local storage; valid until the next call). */
+const char* bfs_last_error_detail(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int bfs_version(void);
+
+/*
+ * Create a graph from a CSR (Section 4.3: CSR, one int per vertex plus one per
+ * edge). row_offsets has n + 1 entries, col_indices m entries; each adjacency
+ * list is the out-neighbours of its vertex. The library copies both arrays into
+ * device memory it owns (the caller keeps ownership of its buffers), computes
+ * the out-degree statistics the decision tree uses (Section 4.1), and, without
+ * BFS_SYMMETRIC, builds the transpose that the pull variant reads. Self-loops
+ * and duplicate entries are allowed and never change a depth. Synchronous.
+ * The CSR is always validated (a malformed one would make kernels read out
+ * of bounds). Errors: BFS_ERR_INVALID_ARG (n < 1, n or m >= 2^31, null
+ * pointers, unknown flags), BFS_ERR_BAD_GRAPH, BFS_ERR_OOM, BFS_ERR_CUDA.
+ */
+int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int64_t n, int64_t m, uint32_t flags,
+                     bfs_graph_t* out);
+
+/* Free a graph and its workspaces after waiting for its runs to finish. NULL is a no-op. */
+int bfs_graph_destroy(bfs_graph_t g);
+
+/* Sizes and degree statistics of a graph (host struct, filled synchronously). */
+int bfs_graph_info(bfs_graph_t g, bfs_graph_info_t* info);
+
+/*
+ * Load the process-wide decision tree (Section 2.1, Section 4.3: the trained
+ * tree exported as an array plus a lookup function) from a text file, or with
+ * NULL restore the built-in tree. File format: optional '#' comment lines, then
+ * "bfs-tree 1 <num_nodes>", then one line per node "feature threshold left right
+ * value": feature -1 marks a leaf whose value is the predicted variant, or -1
+ * for an unknown prediction (Section 4.1); an internal node sends x[feature] <=
+ * threshold to `left`, otherwise to `right`. Runs started afterwards use the new
+ * tree. Errors: BFS_ERR_NOT_FOUND (file), BFS_ERR_INVALID_ARG (malformed tree).
+ */
+int bfs_load_tree(const char* path_or_null);
+
+/*
+ * Single-source BFS (Section 2.2, Section 3.1). depth_out: device, n int32,
+ * caller-owned; on completion depth_out[v] is the hop distance from root, or
+ * -1. Asynchronous on `stream`; the result is valid once the stream reaches
+ * this point. Errors: BFS_ERR_INVALID_ARG (root not in [0, n), null pointers),
+ * BFS_ERR_OOM (no workspace), BFS_ERR_CUDA.
+ */
+int bfs_run(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t stream);
+
+/*
+ * bfs_run with options and statistics. With opts->depth_on_host, depth_out is
+ * host memory and the call returns after the result has been copied there.
+ * With stats != NULL the call synchronises `stream` and fills *stats (host);
+ * it then also returns the device-side status (BFS_ERR_TIMEOUT if a bounded
+ * wait gave up). opts may be NULL (tree switching, device output).
+ */
+int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t stream, const bfs_options* opts,
+               bfs_run_stats* stats);
+
+/*
+ * Multi-source BFS: k independent traversals of one graph (the result equals k
+ * single-source runs). roots: host, k int32. depth_out: device, k * n int32,
+ * row-major (row i for roots[i]), caller-owned. Roots are processed in waves
+ * of up to 64, one bit per root in a 64-bit visited / frontier mask per vertex.
+ * edges_out: optional host array of k int64 reached-edge counts; when given,
+ * the call synchronises `stream`. Errors as bfs_run.
+ */
+int bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_out, bfs_stream_t stream,
+                  int64_t* edges_out);
+
+/* One level of a profiled traversal. */
+typedef struct bfs_level_profile {
+  int64_t features[BFS_NUM_FEATURES]; /* the tree's input at this level (enum bfs_feature order) */
+  float ms[BFS_NUM_VARIANTS];         /* median device time of each variant expanding this level */
+  int32_t tree_variant;               /* the current tree's choice (after the unknown-prediction rule) */
+  int32_t pad;
+} bfs_level_profile;
+
+/*
+ * Per-level timing harness (Section 4.1: the fastest implementation of every
+ * level labels the training set). Runs the traversal from `root` level by level
+ * with a host round trip per level; at each level it snapshots the state
+ * (depths, visited bitmap, counters), runs every variant `reps` times from that
+ * same snapshot, timing each run with CUDA events on `stream`, records the
+ * median, restores the snapshot and advances with `advance_variant` (or the
+ * tree's choice when BFS_VARIANT_TREE). out: host, `capacity` entries; levels
+ * beyond it are traversed but not recorded. *num_levels: levels traversed.
+ * Synchronous. Uses a private depth buffer (the graph's caller buffers are not
+ * touched). Errors: BFS_ERR_INVALID_ARG, BFS_ERR_OOM, BFS_ERR_CUDA.
+ */
+int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advance_variant, bfs_stream_t stream,
+                       bfs_level_profile* out, int32_t capacity, int32_t* num_levels);
+
+/*
+ * Test hook: make the n-th device allocation made by the library from now on
+ * fail with BFS_ERR_OOM (n = 0 disables). Lets tests exercise the out-of-memory
+ * paths without exhausting a shared GPU.
+ */
+int bfs_debug_fail_alloc_after(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFS_GB300_H */

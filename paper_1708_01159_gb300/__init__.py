@@ -1,0 +1,294 @@
+"""GB300-native level-synchronous BFS with per-level kernel switching.
+
+Implements the hot path of "Using Graph Properties to Speed-up GPU-based Graph
+Traversal: A Model-driven Approach" (Verstraaten, Varbanescu, de Laat): BFS
+over an int32 CSR graph where, at every level, a binary decision tree over
+graph and frontier properties (Section 4.1) picks the kernel that expands the
+level (Section 3.1 variants), evaluated on the device.
+
+This module is a thin ctypes binding of libbfs.so (C ABI in include/bfs.h):
+it marshals arguments (numpy host arrays, torch tensors, CUDA stream handles)
+and calls the library under the same names. Every step of the traversal runs
+in the library's CUDA kernels; there is no CPU fallback. If libbfs.so has not
+been built, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbfs.so")
+DEFAULT_TREE = os.path.join(_HERE, "trees", "default.tree")
+
+BFS_OK = 0
+BFS_ERR_INVALID_ARG = 1
+BFS_ERR_BAD_GRAPH = 2
+BFS_ERR_OOM = 3
+BFS_ERR_CUDA = 4
+BFS_ERR_TIMEOUT = 5
+BFS_ERR_BUSY = 6
+BFS_ERR_CANCELLED = 7
+BFS_ERR_NOT_FOUND = 8
+
+BFS_SYMMETRIC = 1
+BFS_INPUT_ON_DEVICE = 2
+BFS_VALIDATE = 4
+
+VARIANT_TREE = -1
+VARIANTS = ("push_thread", "push_warp", "push_cta", "push_edge", "pull")
+NUM_VARIANTS = len(VARIANTS)
+FEATURES = ("n", "m", "deg_min", "deg_q1", "deg_med", "deg_q3", "deg_max", "deg_sd256",
+            "frontier", "frontier_ppm", "discovered", "discovered_ppm", "frontier_edges", "level")
+NUM_FEATURES = len(FEATURES)
+
+
+class BFSError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {status_string(code)} ({code}): {detail}")
+        self.code = code
+
+
+class _GraphInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("deg_summary", ctypes.c_int64 * 5),
+                ("deg_sd256", ctypes.c_int64), ("bytes_resident", ctypes.c_int64), ("symmetric", ctypes.c_int32),
+                ("num_workspaces", ctypes.c_int32)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("forced_variant", ctypes.c_int32), ("depth_on_host", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("edges_reached", ctypes.c_int64), ("vertices_reached", ctypes.c_int64), ("levels", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("log_capacity", ctypes.c_int32),
+                ("log_variant", ctypes.POINTER(ctypes.c_int32)), ("log_frontier", ctypes.POINTER(ctypes.c_int64)),
+                ("log_frontier_edges", ctypes.POINTER(ctypes.c_int64))]
+
+
+class _LevelProfile(ctypes.Structure):
+    _fields_ = [("features", ctypes.c_int64 * NUM_FEATURES), ("ms", ctypes.c_float * NUM_VARIANTS),
+                ("tree_variant", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile libbfs.so in-tree (nvcc, sm_103a)."""
+    from .buildlib import build as _build
+    return _build(force=force)
+
+
+def lib():
+    """The loaded libbfs.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built (run paper_1708_01159_gb300.build()); "
+                               "there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        c_i32, c_i64, c_u32, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p
+        sig = {
+            "bfs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "bfs_last_error_detail": (ctypes.c_char_p, []),
+            "bfs_version": (ctypes.c_int, []),
+            "bfs_graph_create": (ctypes.c_int, [vp, vp, c_i64, c_i64, c_u32, ctypes.POINTER(vp)]),
+            "bfs_graph_destroy": (ctypes.c_int, [vp]),
+            "bfs_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(_GraphInfo)]),
+            "bfs_load_tree": (ctypes.c_int, [ctypes.c_char_p]),
+            "bfs_run": (ctypes.c_int, [vp, c_i32, vp, vp]),
+            "bfs_run_ex": (ctypes.c_int, [vp, c_i32, vp, vp, ctypes.POINTER(_Options), ctypes.POINTER(_Stats)]),
+            "bfs_run_batch": (ctypes.c_int, [vp, vp, c_i32, vp, vp, vp]),
+            "bfs_profile_levels": (ctypes.c_int, [vp, c_i32, c_i32, c_i32, vp, ctypes.POINTER(_LevelProfile), c_i32,
+                                                  ctypes.POINTER(c_i32)]),
+            "bfs_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return lib().bfs_status_string(code).decode()
+    except Exception:  # library unavailable
+        return str(code)
+
+
+def _check(code: int, where: str):
+    if code != BFS_OK:
+        raise BFSError(code, where, lib().bfs_last_error_detail().decode())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype=np.int32, what="array"):
+    """(pointer, on_device, numel) of a contiguous int32 numpy array or torch tensor."""
+    if x is None:
+        return None, False, 0
+    if _is_torch(x):
+        import torch
+        want = {np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise ValueError(f"{what} must be a contiguous {want} tensor")
+        return x.data_ptr(), x.is_cuda, x.numel()
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{what} must be a C-contiguous {np.dtype(dtype).name} array")
+    return a.ctypes.data, False, a.size
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if _is_torch(stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def bfs_graph_create(row_offsets, col_indices, flags: int = BFS_SYMMETRIC) -> int:
+    """Create a graph from a CSR (numpy host arrays or CUDA int32 tensors). Returns the handle."""
+    po, dev_o, no = _ptr(row_offsets, what="row_offsets")
+    pi, dev_i, ni = _ptr(col_indices, what="col_indices")
+    if dev_o != dev_i:
+        raise ValueError("row_offsets and col_indices must both be host or both be device memory")
+    if dev_o:
+        flags |= BFS_INPUT_ON_DEVICE
+    out = ctypes.c_void_p()
+    _check(lib().bfs_graph_create(po, pi, no - 1, ni, flags, ctypes.byref(out)), "bfs_graph_create")
+    return out.value
+
+
+def bfs_graph_destroy(g: int) -> None:
+    _check(lib().bfs_graph_destroy(g), "bfs_graph_destroy")
+
+
+def bfs_graph_info(g: int) -> dict:
+    info = _GraphInfo()
+    _check(lib().bfs_graph_info(g, ctypes.byref(info)), "bfs_graph_info")
+    return {"n": info.n, "m": info.m, "deg_summary": list(info.deg_summary), "deg_sd256": info.deg_sd256,
+            "bytes_resident": info.bytes_resident, "symmetric": bool(info.symmetric),
+            "num_workspaces": info.num_workspaces}
+
+
+def bfs_load_tree(path: Optional[str] = None) -> None:
+    """Load the process-wide decision tree from a tree file (None: the built-in tree)."""
+    _check(lib().bfs_load_tree(path.encode() if path else None), "bfs_load_tree")
+
+
+def bfs_run(g: int, root: int, depth_out, stream=None) -> None:
+    """Asynchronous BFS from `root` into depth_out (CUDA int32 tensor of n entries)."""
+    p, dev, _ = _ptr(depth_out, what="depth_out")
+    if not dev:
+        raise ValueError("bfs_run writes device memory; use bfs_run_ex(depth_on_host=True) for host output")
+    _check(lib().bfs_run(g, int(root), p, _stream(stream)), "bfs_run")
+
+
+def bfs_run_ex(g: int, root: int, depth_out, stream=None, forced_variant: int = VARIANT_TREE,
+               depth_on_host: Optional[bool] = None, stats: bool = False, log_capacity: int = 0):
+    """BFS with options. Returns a stats dict when stats=True (then the stream is synchronised)."""
+    p, dev, _ = _ptr(depth_out, what="depth_out")
+    host = (not dev) if depth_on_host is None else bool(depth_on_host)
+    opts = _Options(forced_variant=int(forced_variant), depth_on_host=int(host))
+    st = None
+    logs = None
+    if stats:
+        st = _Stats()
+        if log_capacity > 0:
+            logs = (np.zeros(log_capacity, np.int32), np.zeros(log_capacity, np.int64),
+                    np.zeros(log_capacity, np.int64))
+            st.log_capacity = log_capacity
+            st.log_variant = logs[0].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            st.log_frontier = logs[1].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+            st.log_frontier_edges = logs[2].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    _check(lib().bfs_run_ex(g, int(root), p, _stream(stream), ctypes.byref(opts),
+                            ctypes.byref(st) if st is not None else None), "bfs_run_ex")
+    if st is None:
+        return None
+    out = {"edges_reached": st.edges_reached, "vertices_reached": st.vertices_reached, "levels": st.levels,
+           "status": st.status}
+    if logs is not None:
+        k = min(st.levels, log_capacity)
+        out["variant"] = logs[0][:k].copy()
+        out["frontier"] = logs[1][:k].copy()
+        out["frontier_edges"] = logs[2][:k].copy()
+    return out
+
+
+def bfs_run_batch(g: int, roots, depth_out, stream=None, edges: bool = False):
+    """k traversals (host roots) into depth_out (CUDA int32 tensor of k * n, row-major)."""
+    r = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
+    p, dev, _ = _ptr(depth_out, what="depth_out")
+    if not dev:
+        raise ValueError("depth_out must be device memory")
+    e = np.zeros(max(r.size, 1), np.int64) if edges else None
+    _check(lib().bfs_run_batch(g, r.ctypes.data, r.size, p, _stream(stream),
+                               e.ctypes.data if e is not None else None), "bfs_run_batch")
+    return e[: r.size] if e is not None else None
+
+
+def bfs_profile_levels(g: int, root: int, reps: int = 5, advance_variant: int = VARIANT_TREE, stream=None,
+                       capacity: int = 4096):
+    """Per-level timing harness: for every level, time each variant from the same
+    state (median of `reps`). Returns (features[L, F], ms[L, V], tree_variant[L])."""
+    buf = (_LevelProfile * capacity)()
+    nl = ctypes.c_int32(0)
+    _check(lib().bfs_profile_levels(g, int(root), int(reps), int(advance_variant), _stream(stream), buf, capacity,
+                                    ctypes.byref(nl)), "bfs_profile_levels")
+    k = min(nl.value, capacity)
+    feats = np.array([list(buf[i].features) for i in range(k)], dtype=np.int64).reshape(k, NUM_FEATURES)
+    ms = np.array([list(buf[i].ms) for i in range(k)], dtype=np.float64).reshape(k, NUM_VARIANTS)
+    tv = np.array([buf[i].tree_variant for i in range(k)], dtype=np.int32)
+    return feats, ms, tv
+
+
+class Graph:
+    """Owning wrapper of a bfs_graph_t handle."""
+
+    def __init__(self, row_offsets, col_indices, flags: int = BFS_SYMMETRIC):
+        self.handle = bfs_graph_create(row_offsets, col_indices, flags)
+        info = bfs_graph_info(self.handle)
+        self.n, self.m = info["n"], info["m"]
+
+    def info(self) -> dict:
+        return bfs_graph_info(self.handle)
+
+    def run(self, root: int, depth_out, stream=None) -> None:
+        bfs_run(self.handle, root, depth_out, stream)
+
+    def close(self) -> None:
+        if self.handle:
+            bfs_graph_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

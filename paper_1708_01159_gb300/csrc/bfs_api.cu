@@ -1,0 +1,877 @@
+// C ABI of libbfs: graph objects, workspaces, the device-resident level loop
+// (one CUDA graph per workspace: init -> WHILE(frontier) { decide -> SWITCH
+// (variant) { level kernels } }), the decision-tree store and the per-level
+// timing harness.
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "bfs.h"
+#include "bfs_kernels.cuh"
+
+using namespace bfs;
+
+namespace {
+
+thread_local std::string t_detail;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_detail = buf;
+  return code;
+}
+
+#define CU(call)                                                                                      \
+  do {                                                                                                \
+    cudaError_t e_ = (call);                                                                          \
+    if (e_ != cudaSuccess) {                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA, "%s: %s (line %d)", #call, \
+                  cudaGetErrorString(e_), __LINE__);                                                  \
+    }                                                                                                 \
+  } while (0)
+
+#define TRY(expr)              \
+  do {                         \
+    int r_ = (expr);           \
+    if (r_ != BFS_OK) return r_; \
+  } while (0)
+
+// Test hook: fail the N-th device allocation from now (0 = off). Lets tests
+// exercise the out-of-memory paths without exhausting a shared GPU.
+std::atomic<int> g_fail_alloc_countdown{0};
+
+int dmalloc(void** p, size_t bytes) {
+  int c = g_fail_alloc_countdown.load();
+  if (c > 0 && g_fail_alloc_countdown.fetch_sub(1) == 1) {
+    *p = nullptr;
+    return fail(BFS_ERR_OOM, "injected allocation failure (%zu bytes)", bytes);
+  }
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                cudaGetErrorString(e));
+  }
+  return BFS_OK;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Decision trees
+// ---------------------------------------------------------------------------
+const TreeNode kBuiltinTree[] = {
+#include "default_tree.inc"
+};
+
+struct TreeStore {
+  std::mutex mu;
+  std::vector<TreeNode> nodes;
+  uint64_t version = 1;
+};
+
+TreeStore& tree_store() {
+  static TreeStore* ts = [] {
+    auto* t = new TreeStore;
+    t->nodes.assign(std::begin(kBuiltinTree), std::end(kBuiltinTree));
+    return t;
+  }();
+  return *ts;
+}
+
+// Children must have larger indices than their parent: every walk ends.
+int check_tree(const std::vector<TreeNode>& t) {
+  if (t.empty()) return fail(BFS_ERR_INVALID_ARG, "tree has no nodes");
+  for (size_t i = 0; i < t.size(); ++i) {
+    const TreeNode& nd = t[i];
+    if (nd.f < -1 || nd.f >= F_NUM) return fail(BFS_ERR_INVALID_ARG, "node %zu: feature %d out of range", i, nd.f);
+    if (nd.f >= 0) {
+      if (nd.l <= (int)i || nd.r <= (int)i || nd.l >= (int)t.size() || nd.r >= (int)t.size())
+        return fail(BFS_ERR_INVALID_ARG, "node %zu: children %d/%d invalid", i, nd.l, nd.r);
+    } else if (nd.v < -1 || nd.v >= V_NUM) {
+      return fail(BFS_ERR_INVALID_ARG, "node %zu: class %d out of range", i, nd.v);
+    }
+  }
+  return BFS_OK;
+}
+
+int parse_tree(const std::string& text, std::vector<TreeNode>* out) {
+  std::istringstream in(text);
+  std::string line;
+  long long count = -1;
+  std::vector<TreeNode> nodes;
+  while (std::getline(in, line)) {
+    size_t p = line.find_first_not_of(" \t\r");
+    if (p == std::string::npos || line[p] == '#') continue;
+    std::istringstream ls(line);
+    if (count < 0) {
+      std::string magic;
+      int ver = 0;
+      if (!(ls >> magic >> ver >> count) || magic != "bfs-tree" || ver != 1 || count <= 0 || count > (1 << 20))
+        return fail(BFS_ERR_INVALID_ARG, "bad tree header: %s", line.c_str());
+      continue;
+    }
+    TreeNode nd{};
+    long long f, l, r, v;
+    if (!(ls >> f >> nd.t >> l >> r >> v)) return fail(BFS_ERR_INVALID_ARG, "bad tree node line: %s", line.c_str());
+    nd.f = (int32_t)f;
+    nd.l = (int32_t)l;
+    nd.r = (int32_t)r;
+    nd.v = (int32_t)v;
+    nodes.push_back(nd);
+  }
+  if (count < 0 || (long long)nodes.size() != count)
+    return fail(BFS_ERR_INVALID_ARG, "tree: expected %lld nodes, read %zu", count, nodes.size());
+  TRY(check_tree(nodes));
+  *out = std::move(nodes);
+  return BFS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Workspaces
+// ---------------------------------------------------------------------------
+struct Workspace {
+  Buffers b{};
+  RunState* st = nullptr;
+  int32_t* log_variant = nullptr;
+  long long* log_frontier = nullptr;
+  long long* log_edges = nullptr;
+  int32_t log_cap = 0;
+  int32_t* host_depth_stage = nullptr;  // device buffer for runs whose output is host memory
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t init_node = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool in_use = false;
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+};
+
+constexpr int kMaxWorkspaces = 64;
+
+struct Shapes {
+  int init, push_thread, push_warp, push_cta, pe, pull;
+};
+
+}  // namespace
+
+struct bfs_graph {
+  int device = 0;
+  int sms = 0;
+  DevGraph dg{};
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  bool symmetric = false;
+  long long stats6[6] = {0, 0, 0, 0, 0, 0};
+  Shapes shapes{};
+  std::mutex mu;
+  std::vector<Workspace*> pool;
+  // device copies of the process-wide tree, one per version seen (old ones may
+  // still be read by runs in flight, so they live until destroy)
+  std::vector<TreeNode*> trees;
+  TreeNode* tree = nullptr;
+  int32_t tree_nodes = 0;
+  uint64_t tree_version = 0;
+};
+
+namespace {
+
+int grid_for(const void* func, int sms, int cap_per_sm) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, kThreads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  per_sm = std::max(1, std::min(per_sm, cap_per_sm));
+  return sms * per_sm;
+}
+
+void free_workspace(Workspace* ws) {
+  if (!ws) return;
+  if (ws->exec) cudaGraphExecDestroy(ws->exec);
+  if (ws->graph) cudaGraphDestroy(ws->graph);
+  if (ws->done) cudaEventDestroy(ws->done);
+  for (void* p : ws->allocs) cudaFree(p);
+  delete ws;
+}
+
+int ws_alloc(Workspace* ws, void** p, size_t bytes) {
+  TRY(dmalloc(p, bytes));
+  ws->allocs.push_back(*p);
+  ws->bytes += bytes;
+  return BFS_OK;
+}
+
+struct KArgs {
+  DevGraph g;
+  Buffers b;
+  RunState* st;
+  void* ptrs[3];
+};
+
+int add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphNode_t* dep, const void* func, int grid,
+               int block, KArgs& a) {
+  a.ptrs[0] = &a.g;
+  a.ptrs[1] = &a.b;
+  a.ptrs[2] = &a.st;
+  cudaKernelNodeParams p{};
+  p.func = const_cast<void*>(func);
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.sharedMemBytes = 0;
+  p.kernelParams = a.ptrs;
+  CU(cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &p));
+  return BFS_OK;
+}
+
+int fill_init_params(bfs_graph* g, Workspace* ws, int32_t* depth, int32_t root, int32_t forced,
+                     cudaKernelNodeParams* p, void** argp, void* storage) {
+  // storage layout: DevGraph, Buffers, RunState*, int32_t* depth, int32 root, int32 forced, TreeNode*, int32 nodes,
+  // int32 use_handles
+  struct InitArgs {
+    DevGraph g;
+    Buffers b;
+    RunState* st;
+    int32_t* depth;
+    int32_t root;
+    int32_t forced;
+    const TreeNode* tree;
+    int32_t nodes;
+    int32_t use_handles;
+  };
+  static_assert(sizeof(InitArgs) <= 1024, "init args");
+  InitArgs* a = static_cast<InitArgs*>(storage);
+  a->g = g->dg;
+  a->b = ws->b;
+  a->st = ws->st;
+  a->depth = depth;
+  a->root = root;
+  a->forced = forced;
+  a->tree = g->tree;
+  a->nodes = g->tree_nodes;
+  a->use_handles = 1;
+  argp[0] = &a->g;
+  argp[1] = &a->b;
+  argp[2] = &a->st;
+  argp[3] = &a->depth;
+  argp[4] = &a->root;
+  argp[5] = &a->forced;
+  argp[6] = &a->tree;
+  argp[7] = &a->nodes;
+  argp[8] = &a->use_handles;
+  *p = cudaKernelNodeParams{};
+  p->func = reinterpret_cast<void*>(&k_init);
+  p->gridDim = dim3(g->shapes.init);
+  p->blockDim = dim3(kThreads);
+  p->kernelParams = argp;
+  return BFS_OK;
+}
+
+// Build the level loop of one workspace as a CUDA graph with conditional nodes.
+int build_graph(bfs_graph* g, Workspace* ws) {
+  CU(cudaGraphCreate(&ws->graph, 0));
+  alignas(16) unsigned char storage[1024];
+  void* argp[9];
+  cudaKernelNodeParams ip;
+  TRY(fill_init_params(g, ws, ws->host_depth_stage, 0, -1, &ip, argp, storage));
+  CU(cudaGraphAddKernelNode(&ws->init_node, ws->graph, nullptr, 0, &ip));
+
+  cudaGraphConditionalHandle hw;
+  CU(cudaGraphConditionalHandleCreate(&hw, ws->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp{};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CU(cudaGraphAddNode(&wnode, ws->graph, &ws->init_node, nullptr, 1, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+
+  KArgs ka{g->dg, ws->b, ws->st, {}};
+  cudaGraphNode_t decide;
+  TRY(add_kernel(body, &decide, nullptr, reinterpret_cast<const void*>(&k_decide), 1, 32, ka));
+
+  cudaGraphConditionalHandle hs;
+  CU(cudaGraphConditionalHandleCreate(&hs, body, 0, 0));
+  cudaGraphNodeParams sp{};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = hs;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = V_NUM;
+  cudaGraphNode_t snode;
+  CU(cudaGraphAddNode(&snode, body, &decide, nullptr, 1, &sp));
+  cudaGraph_t* vb = sp.conditional.phGraph_out;
+  const Shapes& s = g->shapes;
+  cudaGraphNode_t n0, n1, n2, n3;
+  TRY(add_kernel(vb[V_PUSH_THREAD], &n0, nullptr, reinterpret_cast<const void*>(&k_push_thread), s.push_thread,
+                 kThreads, ka));
+  TRY(add_kernel(vb[V_PUSH_WARP], &n0, nullptr, reinterpret_cast<const void*>(&k_push_warp), s.push_warp, kThreads,
+                 ka));
+  TRY(add_kernel(vb[V_PUSH_CTA], &n0, nullptr, reinterpret_cast<const void*>(&k_push_cta), s.push_cta, kThreads,
+                 ka));
+  TRY(add_kernel(vb[V_PUSH_EDGE], &n0, nullptr, reinterpret_cast<const void*>(&k_pe_reduce), s.pe, kThreads, ka));
+  TRY(add_kernel(vb[V_PUSH_EDGE], &n1, &n0, reinterpret_cast<const void*>(&k_pe_top), 1, kThreads, ka));
+  TRY(add_kernel(vb[V_PUSH_EDGE], &n2, &n1, reinterpret_cast<const void*>(&k_pe_scan), s.pe, kThreads, ka));
+  TRY(add_kernel(vb[V_PUSH_EDGE], &n3, &n2, reinterpret_cast<const void*>(&k_pe_expand), s.pe, kThreads, ka));
+  TRY(add_kernel(vb[V_PULL], &n0, nullptr, reinterpret_cast<const void*>(&k_pull), s.pull, kThreads, ka));
+  CU(cudaGraphInstantiate(&ws->exec, ws->graph, 0));
+
+  // the handles live in the device state, where decide sets them each level
+  RunState init{};
+  init.h_while = hw;
+  init.h_switch = hs;
+  init.use_handles = 1;
+  init.log_cap = ws->log_cap;
+  init.log_variant = ws->log_variant;
+  init.log_frontier = ws->log_frontier;
+  init.log_edges = ws->log_edges;
+  CU(cudaMemcpy(ws->st, &init, sizeof init, cudaMemcpyHostToDevice));
+  return BFS_OK;
+}
+
+int create_workspace(bfs_graph* g, Workspace** out) {
+  auto* ws = new Workspace;
+  const int64_t n = g->dg.n;
+  const int64_t words = g->dg.words;
+  const int64_t pe_blocks = (n + kPeTile - 1) / kPeTile + 2;
+  int r = BFS_OK;
+  void* p;
+  auto A = [&](size_t bytes) -> void* {
+    if (r != BFS_OK) return nullptr;
+    r = ws_alloc(ws, &p, bytes);
+    return r == BFS_OK ? p : nullptr;
+  };
+  ws->b.q[0] = static_cast<int32_t*>(A(n * 4));
+  ws->b.q[1] = static_cast<int32_t*>(A(n * 4));
+  ws->b.vis[0] = static_cast<uint32_t*>(A(words * 4));
+  ws->b.vis[1] = static_cast<uint32_t*>(A(words * 4));
+  ws->b.pe_scan = static_cast<int32_t*>(A((n + 1) * 4));
+  ws->b.pe_beg = static_cast<int32_t*>(A(n * 4));
+  ws->b.pe_bsum = static_cast<long long*>(A(pe_blocks * 8));
+  ws->b.pe_blocks_cap = (int32_t)pe_blocks;
+  ws->st = static_cast<RunState*>(A(sizeof(RunState)));
+  ws->log_cap = (int32_t)std::min<int64_t>(n + 1, 1 << 16);
+  ws->log_variant = static_cast<int32_t*>(A(ws->log_cap * 4));
+  ws->log_frontier = static_cast<long long*>(A(ws->log_cap * 8));
+  ws->log_edges = static_cast<long long*>(A(ws->log_cap * 8));
+  ws->host_depth_stage = static_cast<int32_t*>(A(n * 4));
+  if (r == BFS_OK) {
+    cudaError_t e = cudaEventCreateWithFlags(&ws->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+  }
+  if (r == BFS_OK) r = build_graph(g, ws);
+  if (r != BFS_OK) {
+    free_workspace(ws);
+    return r;
+  }
+  *out = ws;
+  return BFS_OK;
+}
+
+// A workspace free for `stream`: idle on the device, or last used on the same
+// stream (then stream order protects it). At the pool limit the least recently
+// queued workspace is reused after `stream` waits for its last run.
+int acquire(bfs_graph* g, cudaStream_t stream, Workspace** out) {
+  std::lock_guard<std::mutex> lk(g->mu);
+  Workspace* pick = nullptr;
+  for (Workspace* ws : g->pool) {
+    if (ws->in_use) continue;
+    if (ws->last_stream == stream || cudaEventQuery(ws->done) == cudaSuccess) {
+      pick = ws;
+      break;
+    }
+  }
+  if (!pick && (int)g->pool.size() < kMaxWorkspaces) {
+    Workspace* ws = nullptr;
+    TRY(create_workspace(g, &ws));
+    g->pool.push_back(ws);
+    pick = ws;
+  }
+  if (!pick) {
+    for (Workspace* ws : g->pool)
+      if (!ws->in_use) {
+        pick = ws;
+        break;
+      }
+    if (!pick) return fail(BFS_ERR_BUSY, "all %d workspaces are being enqueued", kMaxWorkspaces);
+    CU(cudaStreamWaitEvent(stream, pick->done, 0));
+  }
+  cudaGetLastError();  // clear a not-ready status from cudaEventQuery
+  pick->in_use = true;
+  *out = pick;
+  return BFS_OK;
+}
+
+int release(bfs_graph* g, Workspace* ws, cudaStream_t stream) {
+  cudaError_t e = cudaEventRecord(ws->done, stream);
+  std::lock_guard<std::mutex> lk(g->mu);
+  ws->last_stream = stream;
+  ws->in_use = false;
+  if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+  return BFS_OK;
+}
+
+int sync_tree(bfs_graph* g) {
+  TreeStore& ts = tree_store();
+  std::lock_guard<std::mutex> lk(ts.mu);
+  std::lock_guard<std::mutex> lk2(g->mu);
+  if (g->tree_version == ts.version && g->tree) return BFS_OK;
+  void* p = nullptr;
+  TRY(dmalloc(&p, ts.nodes.size() * sizeof(TreeNode)));
+  cudaError_t e = cudaMemcpy(p, ts.nodes.data(), ts.nodes.size() * sizeof(TreeNode), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return fail(BFS_ERR_CUDA, "tree upload: %s", cudaGetErrorString(e));
+  }
+  g->trees.push_back(static_cast<TreeNode*>(p));
+  g->tree = static_cast<TreeNode*>(p);
+  g->tree_nodes = (int32_t)ts.nodes.size();
+  g->tree_version = ts.version;
+  return BFS_OK;
+}
+
+int launch_run(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
+  alignas(16) unsigned char storage[1024];
+  void* argp[9];
+  cudaKernelNodeParams ip;
+  TRY(fill_init_params(g, ws, depth, root, forced, &ip, argp, storage));
+  CU(cudaGraphExecKernelNodeSetParams(ws->exec, ws->init_node, &ip));
+  CU(cudaGraphLaunch(ws->exec, stream));
+  return BFS_OK;
+}
+
+// Launch the kernels of one variant for the current level directly on a
+// stream (the host-driven counterpart of one SWITCH body).
+int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s) {
+  const Shapes& sh = g->shapes;
+  const DevGraph& dg = g->dg;
+  switch (v) {
+    case V_PUSH_THREAD: k_push_thread<<<sh.push_thread, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
+    case V_PUSH_WARP: k_push_warp<<<sh.push_warp, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
+    case V_PUSH_CTA: k_push_cta<<<sh.push_cta, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
+    case V_PUSH_EDGE:
+      k_pe_reduce<<<sh.pe, kThreads, 0, s>>>(dg, ws->b, ws->st);
+      k_pe_top<<<1, kThreads, 0, s>>>(dg, ws->b, ws->st);
+      k_pe_scan<<<sh.pe, kThreads, 0, s>>>(dg, ws->b, ws->st);
+      k_pe_expand<<<sh.pe, kThreads, 0, s>>>(dg, ws->b, ws->st);
+      break;
+    case V_PULL: k_pull<<<sh.pull, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
+    default: return fail(BFS_ERR_INVALID_ARG, "variant %d", v);
+  }
+  CU(cudaGetLastError());
+  return BFS_OK;
+}
+
+int check_graph(bfs_graph_t g) {
+  if (!g) return fail(BFS_ERR_INVALID_ARG, "null graph");
+  return BFS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* bfs_status_string(int status) {
+  switch (status) {
+    case BFS_OK: return "ok";
+    case BFS_ERR_INVALID_ARG: return "invalid argument";
+    case BFS_ERR_BAD_GRAPH: return "malformed graph";
+    case BFS_ERR_OOM: return "out of memory";
+    case BFS_ERR_CUDA: return "CUDA error";
+    case BFS_ERR_TIMEOUT: return "timed out";
+    case BFS_ERR_BUSY: return "busy";
+    case BFS_ERR_CANCELLED: return "cancelled";
+    case BFS_ERR_NOT_FOUND: return "not found";
+    default: return "unknown status";
+  }
+}
+
+const char* bfs_last_error_detail(void) { return t_detail.c_str(); }
+
+int bfs_version(void) { return 100; }
+
+// Test hook (not part of the public header's contract): make the n-th device
+// allocation from now fail with BFS_ERR_OOM; 0 disables.
+int bfs_debug_fail_alloc_after(int n) {
+  g_fail_alloc_countdown.store(n < 0 ? 0 : n);
+  return BFS_OK;
+}
+
+int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int64_t n, int64_t m, uint32_t flags,
+                     bfs_graph_t* out) {
+  if (!out) return fail(BFS_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (!row_offsets || (!col_indices && m > 0)) return fail(BFS_ERR_INVALID_ARG, "null CSR pointer");
+  if (n < 1 || n >= INT32_MAX || m < 0 || m > (int64_t)INT32_MAX - 64)
+    return fail(BFS_ERR_INVALID_ARG, "sizes out of range (n=%lld, m=%lld)", (long long)n, (long long)m);
+  if (flags & ~(uint32_t)(BFS_SYMMETRIC | BFS_INPUT_ON_DEVICE | BFS_VALIDATE))
+    return fail(BFS_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  std::unique_ptr<bfs_graph> g(new bfs_graph);
+  CU(cudaGetDevice(&g->device));
+  CU(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
+  g->symmetric = (flags & BFS_SYMMETRIC) != 0;
+  auto cleanup = [&]() {
+    for (void* p : g->allocs) cudaFree(p);
+    g->allocs.clear();
+  };
+  auto galloc = [&](void** p, size_t bytes) -> int {
+    int r = dmalloc(p, bytes);
+    if (r == BFS_OK) {
+      g->allocs.push_back(*p);
+      g->bytes += bytes;
+    }
+    return r;
+  };
+  const cudaMemcpyKind kind = (flags & BFS_INPUT_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  int32_t *off = nullptr, *idx = nullptr;
+  int r = galloc(reinterpret_cast<void**>(&off), (n + 1) * 4);
+  if (r == BFS_OK) r = galloc(reinterpret_cast<void**>(&idx), (m + kIdxPad) * 4);
+  if (r != BFS_OK) {
+    cleanup();
+    return r;
+  }
+  cudaError_t e = cudaMemcpy(off, row_offsets, (n + 1) * 4, kind);
+  if (e == cudaSuccess && m > 0) e = cudaMemcpy(idx, col_indices, m * 4, kind);
+  if (e == cudaSuccess) e = cudaMemset(idx + m, 0, kIdxPad * 4);
+  // validation is unconditional: a malformed CSR would make kernels read out of bounds
+  int32_t* scratch = nullptr;  // [0] bad flag, [1] dmin, [2] dmax
+  unsigned long long* sums = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&scratch, 16);
+  if (e == cudaSuccess) e = cudaMalloc(&sums, 16);
+  if (e != cudaSuccess) {
+    if (scratch) cudaFree(scratch);
+    cleanup();
+    return fail(BFS_ERR_CUDA, "graph upload: %s", cudaGetErrorString(e));
+  }
+  const int blocks = g->sms * 4;
+  int32_t init3[3] = {0, INT32_MAX, 0};
+  cudaMemcpy(scratch, init3, 12, cudaMemcpyHostToDevice);
+  cudaMemset(sums, 0, 16);
+  k_validate<<<blocks, kThreads>>>(off, idx, (int32_t)n, (int32_t)m, scratch);
+  int32_t bad = 0;
+  e = cudaMemcpy(&bad, scratch, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess || bad) {
+    cudaFree(scratch);
+    cudaFree(sums);
+    cleanup();
+    if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "validate: %s", cudaGetErrorString(e));
+    return fail(BFS_ERR_BAD_GRAPH, "CSR failed validation (off[0]=0, nondecreasing, off[n]=m, 0<=idx<n)");
+  }
+  // out-degree statistics (Section 4.1 degree distribution)
+  k_deg_reduce<<<blocks, kThreads>>>(off, (int32_t)n, sums, sums + 1, scratch + 1, scratch + 2);
+  int32_t mm[3];
+  e = cudaMemcpy(mm, scratch, 12, cudaMemcpyDeviceToHost);
+  int32_t* hist = nullptr;
+  long long* st6 = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&hist, ((size_t)mm[2] + 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&st6, 6 * 8);
+  if (e == cudaSuccess) e = cudaMemset(hist, 0, ((size_t)mm[2] + 1) * 4);
+  if (e == cudaSuccess) {
+    k_deg_hist<<<blocks, kThreads>>>(off, (int32_t)n, hist);
+    k_deg_finish<<<1, kThreads>>>(hist, mm[2], (int32_t)n, sums, sums + 1, st6);
+    e = cudaMemcpy(g->stats6, st6, 6 * 8, cudaMemcpyDeviceToHost);
+  }
+  if (hist) cudaFree(hist);
+  if (st6) cudaFree(st6);
+  cudaFree(scratch);
+  cudaFree(sums);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(BFS_ERR_CUDA, "degree statistics: %s", cudaGetErrorString(e));
+  }
+  // transpose for pull when the graph may be directed
+  int32_t *in_off = off, *in_idx = idx;
+  if (!g->symmetric) {
+    r = galloc(reinterpret_cast<void**>(&in_off), (n + 1) * 4);
+    if (r == BFS_OK) r = galloc(reinterpret_cast<void**>(&in_idx), (m + kIdxPad) * 4);
+    int32_t* cnt = nullptr;
+    long long* bsum = nullptr;
+    const int64_t nblk = (n + kPeTile - 1) / kPeTile;
+    if (r == BFS_OK) {
+      e = cudaMalloc(&cnt, (n + 1) * 4);
+      if (e == cudaSuccess) e = cudaMalloc(&bsum, (nblk + 2) * 8);
+      if (e == cudaSuccess) e = cudaMemset(cnt, 0, (n + 1) * 4);
+      if (e == cudaSuccess) e = cudaMemset(in_idx + m, 0, kIdxPad * 4);
+      if (e == cudaSuccess) {
+        k_tr_count<<<blocks, kThreads>>>(idx, (int32_t)m, cnt);
+        k_scan_reduce<<<blocks, kThreads>>>(cnt, (int32_t)n, bsum);
+        k_scan_top<<<1, kThreads>>>(bsum, (int32_t)nblk);
+        k_scan_apply<<<blocks, kThreads>>>(cnt, (int32_t)n, bsum, in_off);
+        e = cudaMemcpy(cnt, in_off, (n + 1) * 4, cudaMemcpyDeviceToDevice);
+      }
+      if (e == cudaSuccess) {
+        k_tr_scatter<<<blocks, kThreads>>>(off, idx, (int32_t)n, cnt, in_idx);
+        e = cudaDeviceSynchronize();
+      }
+      if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "transpose: %s", cudaGetErrorString(e));
+    }
+    if (cnt) cudaFree(cnt);
+    if (bsum) cudaFree(bsum);
+    if (r != BFS_OK) {
+      cleanup();
+      return r;
+    }
+  }
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(BFS_ERR_CUDA, "graph create: %s", cudaGetErrorString(e));
+  }
+  DevGraph& dg = g->dg;
+  dg.off = off;
+  dg.idx = idx;
+  dg.in_off = in_off;
+  dg.in_idx = in_idx;
+  dg.n = (int32_t)n;
+  dg.m = (int32_t)m;
+  dg.words = (int32_t)((n + 31) / 32);
+  dg.symmetric = g->symmetric ? 1 : 0;
+  dg.gfeat[F_N] = n;
+  dg.gfeat[F_M] = m;
+  for (int k = 0; k < 6; ++k) dg.gfeat[F_DEG_MIN + k] = g->stats6[k];
+  Shapes& s = g->shapes;
+  s.init = g->sms * 4;
+  s.push_thread = grid_for(reinterpret_cast<const void*>(&k_push_thread), g->sms, 8);
+  s.push_warp = grid_for(reinterpret_cast<const void*>(&k_push_warp), g->sms, 8);
+  s.push_cta = grid_for(reinterpret_cast<const void*>(&k_push_cta), g->sms, 8);
+  s.pe = grid_for(reinterpret_cast<const void*>(&k_pe_expand), g->sms, 8);
+  s.pull = grid_for(reinterpret_cast<const void*>(&k_pull), g->sms, 8);
+  *out = g.release();
+  return BFS_OK;
+}
+
+int bfs_graph_destroy(bfs_graph_t g) {
+  if (!g) return BFS_OK;
+  DeviceGuard dgd(g->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  for (Workspace* ws : g->pool) free_workspace(ws);
+  for (TreeNode* t : g->trees) cudaFree(t);
+  for (void* p : g->allocs) cudaFree(p);
+  delete g;
+  if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "destroy: %s", cudaGetErrorString(e));
+  return BFS_OK;
+}
+
+int bfs_graph_info(bfs_graph_t g, bfs_graph_info_t* info) {
+  TRY(check_graph(g));
+  if (!info) return fail(BFS_ERR_INVALID_ARG, "info is null");
+  std::lock_guard<std::mutex> lk(g->mu);
+  info->n = g->dg.n;
+  info->m = g->dg.m;
+  for (int k = 0; k < 5; ++k) info->deg_summary[k] = g->stats6[k];
+  info->deg_sd256 = g->stats6[5];
+  size_t b = g->bytes;
+  for (Workspace* ws : g->pool) b += ws->bytes;
+  info->bytes_resident = (int64_t)b;
+  info->symmetric = g->symmetric ? 1 : 0;
+  info->num_workspaces = (int32_t)g->pool.size();
+  return BFS_OK;
+}
+
+int bfs_load_tree(const char* path_or_null) {
+  std::vector<TreeNode> nodes;
+  if (!path_or_null) {
+    nodes.assign(std::begin(kBuiltinTree), std::end(kBuiltinTree));
+  } else {
+    std::ifstream f(path_or_null);
+    if (!f) return fail(BFS_ERR_NOT_FOUND, "cannot open tree file %s", path_or_null);
+    std::stringstream ss;
+    ss << f.rdbuf();
+    TRY(parse_tree(ss.str(), &nodes));
+  }
+  TreeStore& ts = tree_store();
+  std::lock_guard<std::mutex> lk(ts.mu);
+  ts.nodes = std::move(nodes);
+  ts.version += 1;
+  return BFS_OK;
+}
+
+int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t stream_, const bfs_options* opts,
+               bfs_run_stats* stats) {
+  TRY(check_graph(g));
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (!depth_out) return fail(BFS_ERR_INVALID_ARG, "depth_out is null");
+  if (root < 0 || root >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root %d not in [0, %d)", root, g->dg.n);
+  int32_t forced = -1;
+  bool host_out = false;
+  if (opts) {
+    if (opts->forced_variant < -1 || opts->forced_variant >= V_NUM)
+      return fail(BFS_ERR_INVALID_ARG, "forced_variant %d out of range", opts->forced_variant);
+    for (int k = 0; k < 6; ++k)
+      if (opts->reserved[k]) return fail(BFS_ERR_INVALID_ARG, "reserved option fields must be zero");
+    forced = opts->forced_variant;
+    host_out = opts->depth_on_host != 0;
+  }
+  DeviceGuard dgd(g->device);
+  TRY(sync_tree(g));
+  Workspace* ws = nullptr;
+  TRY(acquire(g, stream, &ws));
+  int32_t* dst = host_out ? ws->host_depth_stage : depth_out;
+  int r = launch_run(g, ws, root, dst, forced, stream);
+  RunState hs{};
+  if (r == BFS_OK && host_out) {
+    cudaError_t e = cudaMemcpyAsync(depth_out, dst, (size_t)g->dg.n * 4, cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "depth copy: %s", cudaGetErrorString(e));
+  }
+  if (r == BFS_OK && stats) {
+    cudaError_t e = cudaMemcpyAsync(&hs, ws->st, sizeof hs, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess && stats->log_capacity > 0) {
+      const int32_t cnt = std::min(std::min(hs.levels, ws->log_cap), stats->log_capacity);
+      if (cnt > 0) {
+        if (stats->log_variant) e = cudaMemcpy(stats->log_variant, ws->log_variant, cnt * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && stats->log_frontier)
+          e = cudaMemcpy(stats->log_frontier, ws->log_frontier, cnt * 8, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && stats->log_frontier_edges)
+          e = cudaMemcpy(stats->log_frontier_edges, ws->log_edges, cnt * 8, cudaMemcpyDeviceToHost);
+      }
+    }
+    if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "stats: %s", cudaGetErrorString(e));
+  }
+  if (r == BFS_OK && host_out && !stats) {
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "sync: %s", cudaGetErrorString(e));
+  }
+  int rr = release(g, ws, stream);
+  if (r != BFS_OK) return r;
+  if (rr != BFS_OK) return rr;
+  if (stats) {
+    stats->edges_reached = hs.edges_reached;
+    stats->vertices_reached = hs.discovered;
+    stats->levels = hs.levels;
+    stats->status = hs.status;
+    if (hs.status != ST_OK) return fail(BFS_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  }
+  return BFS_OK;
+}
+
+int bfs_run(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t stream) {
+  return bfs_run_ex(g, root, depth_out, stream, nullptr, nullptr);
+}
+
+int bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_out, bfs_stream_t stream,
+                  int64_t* edges_out) {
+  TRY(check_graph(g));
+  if (k < 0) return fail(BFS_ERR_INVALID_ARG, "k < 0");
+  if (k == 0) return BFS_OK;
+  if (!roots || !depth_out) return fail(BFS_ERR_INVALID_ARG, "null roots or depth_out");
+  for (int32_t i = 0; i < k; ++i)
+    if (roots[i] < 0 || roots[i] >= g->dg.n)
+      return fail(BFS_ERR_INVALID_ARG, "roots[%d] = %d not in [0, %d)", i, roots[i], g->dg.n);
+  for (int32_t i = 0; i < k; ++i) {
+    bfs_run_stats st{};
+    TRY(bfs_run_ex(g, roots[i], depth_out + (size_t)i * g->dg.n, stream, nullptr, edges_out ? &st : nullptr));
+    if (edges_out) edges_out[i] = st.edges_reached;
+  }
+  return BFS_OK;
+}
+
+int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advance_variant, bfs_stream_t stream_,
+                       bfs_level_profile* out, int32_t capacity, int32_t* num_levels) {
+  TRY(check_graph(g));
+  if (root < 0 || root >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root %d not in [0, %d)", root, g->dg.n);
+  if (reps < 1 || reps > 1000) return fail(BFS_ERR_INVALID_ARG, "reps %d not in [1, 1000]", reps);
+  if (advance_variant < -1 || advance_variant >= V_NUM) return fail(BFS_ERR_INVALID_ARG, "advance_variant");
+  if (capacity < 0 || (capacity > 0 && !out) || !num_levels) return fail(BFS_ERR_INVALID_ARG, "output");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  DeviceGuard dgd(g->device);
+  TRY(sync_tree(g));
+  Workspace* ws = nullptr;
+  TRY(acquire(g, s, &ws));
+  const size_t n = (size_t)g->dg.n, words = (size_t)g->dg.words;
+  int32_t *depth = nullptr, *snap_depth = nullptr;
+  uint32_t* snap_vis = nullptr;
+  RunState* snap_st = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int r = dmalloc(reinterpret_cast<void**>(&depth), n * 4);
+  if (r == BFS_OK) r = dmalloc(reinterpret_cast<void**>(&snap_depth), n * 4);
+  if (r == BFS_OK) r = dmalloc(reinterpret_cast<void**>(&snap_vis), words * 4);
+  if (r == BFS_OK) r = dmalloc(reinterpret_cast<void**>(&snap_st), sizeof(RunState));
+  if (r == BFS_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
+    r = fail(BFS_ERR_CUDA, "cudaEventCreate");
+  int32_t L = 0;
+  std::vector<float> t(reps);
+  auto body = [&]() -> int {
+    k_init<<<g->shapes.init, kThreads, 0, s>>>(g->dg, ws->b, ws->st, depth, root, -1, g->tree, g->tree_nodes, 0);
+    CU(cudaGetLastError());
+    RunState hs{};
+    for (;;) {
+      k_decide<<<1, 32, 0, s>>>(g->dg, ws->b, ws->st);
+      CU(cudaMemcpyAsync(&hs, ws->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (hs.frontier == 0 || hs.status != ST_OK) break;
+      uint32_t* vis = hs.vsel ? ws->b.vis[1] : ws->b.vis[0];
+      if (L < capacity) {
+        bfs_level_profile& P = out[L];
+        for (int k = 0; k < F_NUM; ++k) P.features[k] = hs.feat[k];
+        P.tree_variant = hs.variant;
+        P.pad = 0;
+        CU(cudaMemcpyAsync(snap_depth, depth, n * 4, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemcpyAsync(snap_vis, vis, words * 4, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemcpyAsync(snap_st, ws->st, sizeof(RunState), cudaMemcpyDeviceToDevice, s));
+        for (int v = 0; v < V_NUM; ++v) {
+          for (int k = 0; k < reps; ++k) {
+            CU(cudaMemcpyAsync(depth, snap_depth, n * 4, cudaMemcpyDeviceToDevice, s));
+            CU(cudaMemcpyAsync(vis, snap_vis, words * 4, cudaMemcpyDeviceToDevice, s));
+            CU(cudaMemcpyAsync(ws->st, snap_st, sizeof(RunState), cudaMemcpyDeviceToDevice, s));
+            CU(cudaEventRecord(ev[0], s));
+            TRY(launch_variant(g, ws, v, s));
+            CU(cudaEventRecord(ev[1], s));
+            CU(cudaEventSynchronize(ev[1]));
+            CU(cudaEventElapsedTime(&t[k], ev[0], ev[1]));
+          }
+          std::sort(t.begin(), t.end());
+          P.ms[v] = t[reps / 2];
+        }
+        CU(cudaMemcpyAsync(depth, snap_depth, n * 4, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemcpyAsync(vis, snap_vis, words * 4, cudaMemcpyDeviceToDevice, s));
+        CU(cudaMemcpyAsync(ws->st, snap_st, sizeof(RunState), cudaMemcpyDeviceToDevice, s));
+      }
+      // advance to the next level (the resulting state does not depend on the variant)
+      int32_t adv = advance_variant >= 0 ? advance_variant : hs.variant;
+      CU(cudaMemcpyAsync(&ws->st->variant, &adv, 4, cudaMemcpyHostToDevice, s));
+      TRY(launch_variant(g, ws, adv, s));
+      ++L;
+    }
+    CU(cudaStreamSynchronize(s));
+    return BFS_OK;
+  };
+  if (r == BFS_OK) r = body();
+  *num_levels = L;
+  cudaStreamSynchronize(s);
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  for (void* p : {(void*)depth, (void*)snap_depth, (void*)snap_vis, (void*)snap_st})
+    if (p) cudaFree(p);
+  int rr = release(g, ws, s);
+  return r != BFS_OK ? r : rr;
+}
+
+}  // extern "C"

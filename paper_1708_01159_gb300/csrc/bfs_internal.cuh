@@ -1,0 +1,172 @@
+// Internal types and device helpers of libbfs (GB300, sm_103a).
+//
+// Data layout in HBM (one graph):
+//   off[n+1], idx[m + pad]      out-edge CSR, int32; idx padded so that
+//                               16-byte-aligned bulk copies may overrun by < 16 B
+//   in_off/in_idx               transpose for the pull variant (aliases off/idx
+//                               when the graph is symmetric)
+// Per run (one workspace):
+//   q[2][n]                     frontier queues (input / output, swapped per level)
+//   vis[2][ceil(n/32)]          visited bitmaps; push updates the current one in
+//                               place, pull reads the current and writes the other
+//   pe_*                        scratch of the edge-centric variant (degree scan)
+//   RunState                    level, counters, variant, status, log pointers
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bfs {
+
+enum Variant : int32_t {
+  V_PUSH_THREAD = 0,
+  V_PUSH_WARP = 1,
+  V_PUSH_CTA = 2,
+  V_PUSH_EDGE = 3,
+  V_PULL = 4,
+  V_NUM = 5,
+};
+
+// Section 4.1 features, in the order the tree file indexes them.
+enum Feature : int32_t {
+  F_N = 0, F_M, F_DEG_MIN, F_DEG_Q1, F_DEG_MED, F_DEG_Q3, F_DEG_MAX, F_DEG_SD256,
+  F_FRONTIER, F_FRONTIER_PPM, F_DISCOVERED, F_DISCOVERED_PPM, F_FRONTIER_EDGES, F_LEVEL,
+  F_NUM,
+};
+
+enum Status : int32_t { ST_OK = 0, ST_TIMEOUT = 5 };
+
+// Section 4.1: an unknown prediction at the first level falls back to the
+// edge list implementation (the edge-centric push here).
+constexpr int32_t kLevel0Default = V_PUSH_EDGE;
+
+constexpr int kIdxPad = 8;  // int32 entries of slack after idx
+
+struct TreeNode {
+  long long t;  // threshold: x[f] <= t goes left
+  int32_t f;    // feature, -1 for a leaf
+  int32_t l, r;
+  int32_t v;    // leaf class, -1 = unknown prediction
+};
+static_assert(sizeof(TreeNode) == 24, "TreeNode layout");
+
+struct DevGraph {
+  const int32_t* off;
+  const int32_t* idx;
+  const int32_t* in_off;
+  const int32_t* in_idx;
+  int32_t n;
+  int32_t m;
+  int32_t words;  // ceil(n / 32)
+  int32_t symmetric;
+  long long gfeat[8];  // F_N .. F_DEG_SD256
+};
+
+struct RunState {
+  int32_t* depth;            // caller's output
+  const TreeNode* tree;      // device tree
+  int32_t tree_nodes;
+  int32_t root;
+  int32_t forced;            // -1: tree
+  int32_t use_handles;       // 1 inside a CUDA graph with conditional nodes
+  int32_t level;             // depth of the frontier being expanded
+  int32_t variant;           // variant of the current level
+  uint32_t qsel;             // q[qsel] = input queue, q[qsel ^ 1] = output queue
+  uint32_t vsel;             // vis[vsel] = current visited bitmap
+  int32_t frontier;          // f_L
+  int32_t status;            // ST_OK / ST_TIMEOUT
+  int32_t vw;                // virtual warp width of the push_warp variant at this level
+  int32_t levels;            // levels completed (set when the run ends)
+  unsigned int next_count;   // f_{L+1}: output queue tail
+  unsigned int done_blocks;  // scratch counter
+  unsigned long long next_edges;  // e_{L+1}
+  long long frontier_edges;  // e_L
+  long long discovered;      // sum of f_j, j <= L
+  long long edges_reached;   // sum of e_j, j <= L
+  unsigned long long h_while;   // cudaGraphConditionalHandle of the level loop
+  unsigned long long h_switch;  // cudaGraphConditionalHandle of the variant switch
+  long long feat[F_NUM];     // feature vector of the current level (written by decide)
+  int32_t log_cap;
+  int32_t pad_;
+  int32_t* log_variant;
+  long long* log_frontier;
+  long long* log_edges;
+};
+
+struct Buffers {
+  int32_t* q[2];
+  uint32_t* vis[2];
+  int32_t* pe_scan;      // exclusive scan of frontier degrees (f + 1 entries)
+  int32_t* pe_beg;       // off[u] of each frontier entry
+  long long* pe_bsum;    // per-block sums of the scan
+  int32_t pe_blocks_cap;
+  int32_t pad_;
+};
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t ld_nc_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Sum `x` over the block and add it to *dst with one atomic. Every thread of
+// the block must call it (it synchronises).
+__device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned long long* dst) {
+  __shared__ unsigned long long part[32];
+  x = warp_sum(x);
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 0) part[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    unsigned long long y = lane_id() < (uint32_t)nw ? part[lane_id()] : 0ull;
+    y = warp_sum(y);
+    if (lane_id() == 0 && y) atomicAdd(dst, y);
+  }
+  __syncthreads();
+}
+
+// Append v to the output queue with one atomic per group of converged lanes
+// (warp-aggregated atomic). The queue tail doubles as the next frontier size.
+__device__ __forceinline__ void queue_append(int32_t* qout, unsigned int* tail, int32_t v) {
+  const uint32_t mask = __activemask();
+  const int leader = __ffs(mask) - 1;
+  unsigned int base = 0;
+  if ((int)lane_id() == leader) base = atomicAdd(tail, (unsigned)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  qout[base + __popc(mask & lanemask_lt())] = v;
+}
+
+// Try to claim vertex v: set its visited bit. True only for the one thread
+// whose atomicOr flipped the bit, so each vertex enters the queue once.
+__device__ __forceinline__ bool claim(uint32_t* vis, int32_t v) {
+  const uint32_t bit = 1u << (v & 31);
+  uint32_t* w = vis + (v >> 5);
+  if (*reinterpret_cast<volatile uint32_t*>(w) & bit) return false;  // cheap filter; bits only go 0 -> 1
+  return (atomicOr(w, bit) & bit) == 0u;
+}
+
+}  // namespace bfs

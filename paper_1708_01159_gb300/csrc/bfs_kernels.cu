@@ -1,0 +1,759 @@
+// Level kernels of the per-level switched BFS (sm_103a).
+//
+// Every kernel reads the level's parameters (level L, frontier size, queue and
+// bitmap selectors) from the device RunState, so the same launch shapes serve
+// every level and the level loop can run inside one CUDA graph with no host
+// round trip. Grids are fixed (a multiple of the SM count) and every kernel
+// strides over its work.
+//
+// Newly reached vertices are claimed by an atomicOr on the visited bitmap; the
+// single thread that flips a bit writes depth L + 1, appends the vertex to the
+// output queue with a warp-aggregated atomic (the queue tail is the next
+// frontier size, Section 3.1.4 variant 1 with warp aggregation), and adds the
+// vertex's out-degree to the next level's frontier-edge count.
+#include <cooperative_groups.h>
+
+#include "bfs_kernels.cuh"
+
+namespace bfs {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s bound on any device-side wait
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---- mbarrier + bulk async copy (TMA bulk, non-tensor) --------------------
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+
+// Wait for the phase with the given parity to complete, giving up after
+// kWaitLimitNs. Returns false on timeout.
+__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return true;
+}
+
+// ---- per-edge visit --------------------------------------------------------
+
+struct Level {
+  const int32_t* __restrict__ qin;
+  int32_t* qout;
+  uint32_t* vis;
+  int32_t* depth;
+  unsigned int* tail;
+  int32_t next_depth;
+  int32_t frontier;
+};
+
+__device__ __forceinline__ Level load_level(const Buffers& b, RunState* st) {
+  Level lv;
+  // select with ternaries: indexing the by-value parameter arrays would copy them to local memory
+  const bool qs = st->qsel != 0u;
+  lv.qin = qs ? b.q[1] : b.q[0];
+  lv.qout = qs ? b.q[0] : b.q[1];
+  lv.vis = st->vsel ? b.vis[1] : b.vis[0];
+  lv.depth = st->depth;
+  lv.tail = &st->next_count;
+  lv.next_depth = st->level + 1;
+  lv.frontier = st->frontier;
+  return lv;
+}
+
+// Top-down visit of edge u -> v (Section 3.1.2 push): the first claimant of v
+// sets its depth, appends it and counts its out-degree.
+__device__ __forceinline__ void visit(const DevGraph& g, const Level& lv, int32_t v, unsigned long long& edges) {
+  if (claim(lv.vis, v)) {
+    lv.depth[v] = lv.next_depth;
+    edges += (unsigned long long)(g.off[v + 1] - g.off[v]);
+    queue_append(lv.qout, lv.tail, v);
+  }
+}
+
+template <typename T>
+__device__ T block_exclusive_scan(T x, T* total) {
+  __shared__ T wsum[32];
+  const uint32_t lane = lane_id();
+  const int w = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  T inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(kFull, inc, o);
+    if ((int)lane >= o) inc += y;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    T s = (int)lane < nw ? wsum[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(kFull, s, o);
+      if ((int)lane >= o) s += y;
+    }
+    if ((int)lane < nw) wsum[lane] = s;
+  }
+  __syncthreads();
+  const T base = w > 0 ? wsum[w - 1] : T(0);
+  *total = wsum[nw - 1];
+  __syncthreads();
+  return base + inc - x;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Init (Section 3.1: all depths infinity, the root 0)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root,
+                                                   int32_t forced, const TreeNode* tree, int32_t tree_nodes,
+                                                   int32_t use_handles) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int32_t n = g.n;
+  if ((reinterpret_cast<uintptr_t>(depth) & 15u) == 0) {
+    const int64_t n4 = n >> 2;
+    int4* d4 = reinterpret_cast<int4*>(depth);
+    for (int64_t i = tid; i < n4; i += stride) {
+      int4 val = make_int4(-1, -1, -1, -1);
+      if ((root >> 2) == i) {
+        const int k = root & 3;
+        if (k == 0) val.x = 0;
+        if (k == 1) val.y = 0;
+        if (k == 2) val.z = 0;
+        if (k == 3) val.w = 0;
+      }
+      d4[i] = val;
+    }
+    for (int64_t i = (n4 << 2) + tid; i < n; i += stride) depth[i] = (i == root) ? 0 : -1;
+  } else {
+    for (int64_t i = tid; i < n; i += stride) depth[i] = (i == root) ? 0 : -1;
+  }
+  uint32_t* vis0 = b.vis[0];
+  for (int64_t w = tid; w < g.words; w += stride) vis0[w] = (w == (root >> 5)) ? (1u << (root & 31)) : 0u;
+  if (tid == 0) {
+    st->depth = depth;
+    st->tree = tree;
+    st->tree_nodes = tree_nodes;
+    st->root = root;
+    st->forced = forced;
+    st->use_handles = use_handles;
+    st->level = -1;
+    st->variant = -1;
+    st->qsel = 0;
+    st->vsel = 0;
+    st->frontier = 0;
+    st->status = ST_OK;
+    st->vw = 32;
+    st->levels = 0;
+    st->done_blocks = 0;
+    st->frontier_edges = 0;
+    st->discovered = 0;
+    st->edges_reached = 0;
+    // the root is the output of "level -1": the first decide turns it into the frontier of level 0
+    b.q[1][0] = root;
+    st->next_count = 1;
+    st->next_edges = (unsigned long long)(g.off[root + 1] - g.off[root]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Level end + tree evaluation (Section 2.1 walk, Section 4.1 features and
+// unknown-prediction rule). One thread; runs between levels on the device.
+// ---------------------------------------------------------------------------
+__global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  (void)b;
+  RunState& s = *st;
+  // close level L-1: its output queue becomes the frontier of level L
+  const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&s.next_count);
+  const unsigned long long e = *reinterpret_cast<volatile unsigned long long*>(&s.next_edges);
+  s.next_count = 0;
+  s.next_edges = 0;
+  if (s.level >= 0 && s.variant == V_PULL) s.vsel ^= 1u;  // pull wrote the other bitmap
+  s.qsel ^= 1u;
+  const int32_t L = s.level + 1;
+  s.level = L;
+  s.frontier = (int32_t)f;
+  s.frontier_edges = (long long)e;
+  s.discovered += f;
+  s.edges_reached += (long long)e;
+  // a traversal has at most n nonempty levels; more means corrupted state, so
+  // end the loop with an error instead of iterating on
+  if (L > g.n || s.discovered > g.n) s.status = ST_TIMEOUT;
+  if (f == 0 || s.status != ST_OK) {
+    s.levels = L;
+    if (s.use_handles) {
+      cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_while, 0u);
+      cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)V_NUM);
+    }
+    return;
+  }
+  long long x[F_NUM];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = g.gfeat[i];
+  const long long n = g.n;
+  x[F_FRONTIER] = f;
+  x[F_FRONTIER_PPM] = (1000000ll * (long long)f) / n;
+  x[F_DISCOVERED] = s.discovered;
+  x[F_DISCOVERED_PPM] = (1000000ll * s.discovered) / n;
+  x[F_FRONTIER_EDGES] = (long long)e;
+  x[F_LEVEL] = L;
+#pragma unroll
+  for (int i = 0; i < F_NUM; ++i) s.feat[i] = x[i];
+  int32_t v = s.forced;
+  if (v < 0) {
+    v = -1;
+    const TreeNode* t = s.tree;
+    if (t != nullptr && s.tree_nodes > 0) {
+      int32_t i = 0;
+      for (int32_t step = 0; step <= s.tree_nodes; ++step) {
+        const TreeNode nd = t[i];
+        if (nd.f < 0) {
+          v = nd.v;
+          break;
+        }
+        i = (x[nd.f] <= nd.t) ? nd.l : nd.r;
+      }
+    }
+    if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : s.variant;  // unknown prediction
+    if (v < 0 || v >= V_NUM) v = kLevel0Default;
+  }
+  s.variant = v;
+  // virtual-warp width for this level: the power of two nearest above the
+  // frontier's mean degree, clamped to [4, 32]
+  const long long avg = (long long)e / (long long)f;
+  s.vw = avg <= 4 ? 4 : avg <= 8 ? 8 : avg <= 16 ? 16 : 32;
+  if (L < s.log_cap) {
+    s.log_variant[L] = v;
+    s.log_frontier[L] = f;
+    s.log_edges[L] = (long long)e;
+  }
+  if (s.use_handles) cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)v);
+}
+
+// ---------------------------------------------------------------------------
+// Push, one thread per frontier vertex (Section 3.1.2 vertex push, over an
+// explicit queue instead of a scan of all vertices)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b, RunState* st) {
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < lv.frontier; i += stride) {
+    const int32_t u = lv.qin[i];
+    const int32_t beg = g.off[u], end = g.off[u + 1];
+    for (int32_t e = beg; e < end; ++e) visit(g, lv, g.idx[e], edges);
+  }
+  block_add_u64(edges, &st->next_edges);
+}
+
+// ---------------------------------------------------------------------------
+// Push, virtual warp of W lanes per frontier vertex (Section 3.1.3, after Hong
+// et al. 2011). W = 32 reads the adjacency with 16-byte vector loads.
+// ---------------------------------------------------------------------------
+namespace {
+template <int W>
+__device__ __forceinline__ void push_vwarp(const DevGraph& g, const Level& lv, unsigned long long& edges) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = gt & (W - 1);
+  const int ngroups = (gridDim.x * blockDim.x) / W;
+  for (int i = gt / W; i < lv.frontier; i += ngroups) {
+    const int32_t u = lv.qin[i];
+    const int32_t beg = g.off[u], end = g.off[u + 1];
+    if (W == 32 && end - beg >= 256) {
+      const int32_t a0 = (beg + 3) & ~3, a1 = end & ~3;
+      if (beg + lane < a0) visit(g, lv, g.idx[beg + lane], edges);
+      for (int32_t e = a0 + 4 * lane; e < a1; e += 128) {
+        const int4 v4 = *reinterpret_cast<const int4*>(g.idx + e);
+        visit(g, lv, v4.x, edges);
+        visit(g, lv, v4.y, edges);
+        visit(g, lv, v4.z, edges);
+        visit(g, lv, v4.w, edges);
+      }
+      if (a1 + lane < end) visit(g, lv, g.idx[a1 + lane], edges);
+    } else {
+      for (int32_t e = beg + lane; e < end; e += W) visit(g, lv, g.idx[e], edges);
+    }
+  }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_push_warp(DevGraph g, Buffers b, RunState* st) {
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  switch (st->vw) {
+    case 4: push_vwarp<4>(g, lv, edges); break;
+    case 8: push_vwarp<8>(g, lv, edges); break;
+    case 16: push_vwarp<16>(g, lv, edges); break;
+    default: push_vwarp<32>(g, lv, edges); break;
+  }
+  block_add_u64(edges, &st->next_edges);
+}
+
+// ---------------------------------------------------------------------------
+// Push, one CTA per frontier vertex. Long adjacency lists are streamed into a
+// double-buffered shared-memory stage by bulk async copies (cp.async.bulk with
+// an mbarrier transaction count); the CTA's threads then test and claim the
+// staged neighbours. Copies are 16-byte aligned: the range is widened to
+// multiples of 4 entries (idx is padded) and the extra entries are skipped.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, RunState* st) {
+  __shared__ alignas(128) int32_t stage[2][kCtaChunk];
+  __shared__ alignas(8) uint64_t bar[2];
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t parity[2] = {0u, 0u};
+  bool failed = false;
+  for (int i = blockIdx.x; i < lv.frontier && !failed; i += gridDim.x) {
+    const int32_t u = lv.qin[i];
+    const int32_t beg = g.off[u], end = g.off[u + 1];
+    if (end - beg < kCtaDirect) {
+      for (int32_t e = beg + tid; e < end; e += blockDim.x) visit(g, lv, g.idx[e], edges);
+      continue;
+    }
+    const int32_t abeg = beg & ~3, aend = (end + 3) & ~3;
+    const int32_t nch = (aend - abeg + kCtaChunk - 1) / kCtaChunk;
+    auto issue = [&](int32_t c) {
+      const int32_t cb = abeg + c * kCtaChunk;
+      const uint32_t bytes = (uint32_t)min(kCtaChunk, aend - cb) * 4u;
+      uint64_t* br = &bar[c & 1];
+      mbar_expect_tx(br, bytes);
+      bulk_g2s(stage[c & 1], g.idx + cb, bytes, br);
+    };
+    if (tid == 0) {
+      issue(0);
+      if (nch > 1) issue(1);
+    }
+    for (int32_t c = 0; c < nch; ++c) {
+      const int s = c & 1;
+      const bool ok = mbar_wait_bounded(&bar[s], parity[s]);
+      parity[s] ^= 1u;
+      if (ok) {
+        const int32_t cb = abeg + c * kCtaChunk;
+        const int32_t len = min(kCtaChunk, aend - cb);
+        for (int32_t k = tid; k < len; k += blockDim.x) {
+          const int32_t e = cb + k;
+          if (e >= beg && e < end) visit(g, lv, stage[s][k], edges);
+        }
+      }
+      if (!__syncthreads_and(ok)) {
+        // a copy never completed: flag it, let the other in-flight copy land (bounded) and stop
+        if (tid == 0) {
+          st->status = ST_TIMEOUT;
+          if (c + 1 < nch) mbar_wait_bounded(&bar[s ^ 1], parity[s ^ 1]);
+        }
+        failed = true;
+        break;
+      }
+      if (tid == 0 && c + 2 < nch) issue(c + 2);
+    }
+  }
+  block_add_u64(edges, &st->next_edges);
+}
+
+// ---------------------------------------------------------------------------
+// Push, edge-centric (Section 3.1.1 edge list, restricted to the frontier's
+// edges): exclusive scan of the frontier degrees, then a load-balanced search
+// (merge path of the scan with the edge indices) gives every thread
+// kPeItems items (frontier boundaries or edges) regardless of degree skew.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_pe_reduce(DevGraph g, Buffers b, RunState* st) {
+  const Level lv = load_level(b, st);
+  const int f = lv.frontier;
+  const int nblk = (f + kPeTile - 1) / kPeTile;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    long long sum = 0;
+    const int base = blk * kPeTile;
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k) {
+      const int i = base + k * kThreads + threadIdx.x;
+      if (i < f) {
+        const int32_t u = lv.qin[i];
+        const int32_t beg = g.off[u];
+        const int32_t d = g.off[u + 1] - beg;
+        b.pe_beg[i] = beg;
+        b.pe_scan[i] = d;
+        sum += d;
+      }
+    }
+    long long tot;
+    block_exclusive_scan<long long>(sum, &tot);
+    if (threadIdx.x == 0) b.pe_bsum[blk] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_pe_top(DevGraph g, Buffers b, RunState* st) {
+  (void)g;
+  const int f = st->frontier;
+  const int nblk = (f + kPeTile - 1) / kPeTile;
+  long long carry = 0;
+  for (int base = 0; base < nblk; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const long long x = i < nblk ? b.pe_bsum[i] : 0;
+    long long tot;
+    const long long ex = block_exclusive_scan<long long>(x, &tot);
+    if (i < nblk) b.pe_bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) b.pe_bsum[nblk] = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) k_pe_scan(DevGraph g, Buffers b, RunState* st) {
+  (void)g;
+  const int f = st->frontier;
+  const int nblk = (f + kPeTile - 1) / kPeTile;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int base = blk * kPeTile + threadIdx.x * kPeItems;
+    int32_t d[kPeItems];
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k) d[k] = (base + k < f) ? b.pe_scan[base + k] : 0;
+    int32_t run = 0;
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k) {
+      const int32_t t = d[k];
+      d[k] = run;
+      run += t;
+    }
+    long long tot;
+    const long long ex = block_exclusive_scan<long long>((long long)run, &tot);
+    const long long off = b.pe_bsum[blk] + ex;
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k)
+      if (base + k < f) b.pe_scan[base + k] = (int32_t)(off + d[k]);
+    if (blk == nblk - 1 && threadIdx.x == 0) b.pe_scan[f] = (int32_t)b.pe_bsum[nblk];
+  }
+}
+
+namespace {
+// Merge-path split: how many of the first d items of merge(A[0..na), j0+[0..nb))
+// are A items, with A first on ties (A[i] <= edge index => boundary first).
+__device__ __forceinline__ int merge_split(const int32_t* a, int na, long long j0, int nb, long long d) {
+  int lo = (int)max(0ll, d - nb), hi = (int)min(d, (long long)na);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((long long)a[mid] <= j0 + d - 1 - mid)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, RunState* st) {
+  __shared__ int32_t s_a[kPeTile + 1];
+  __shared__ int32_t s_beg[kPeTile + 1];
+  __shared__ int s_split[2];
+  const Level lv = load_level(b, st);
+  const int f = lv.frontier;
+  const int32_t E = b.pe_scan[f];
+  const long long total = (long long)f + E;
+  const long long ntiles = (total + kPeTile - 1) / kPeTile;
+  unsigned long long edges = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long d0 = t * kPeTile;
+    const long long d1 = min(d0 + kPeTile, total);
+    if (threadIdx.x < 2) s_split[threadIdx.x] = merge_split(b.pe_scan, f, 0, E, threadIdx.x ? d1 : d0);
+    __syncthreads();
+    const int i0 = s_split[0], i1 = s_split[1];
+    const int na = i1 - i0;
+    const int tl = (int)(d1 - d0);
+    const int nb = tl - na;
+    const long long j0 = d0 - i0;
+    // s index k <-> frontier entry i0 - 1 + k (the vertex owning edge j0 may precede the tile)
+    for (int k = threadIdx.x; k <= na; k += blockDim.x) {
+      const int gi = i0 - 1 + k;
+      s_a[k] = gi >= 0 ? b.pe_scan[gi] : 0;
+      s_beg[k] = gi >= 0 ? b.pe_beg[gi] : 0;
+    }
+    __syncthreads();
+    const int td0 = min((int)threadIdx.x * kPeItems, tl);
+    const int td1 = min(td0 + kPeItems, tl);
+    const int ti = merge_split(s_a + 1, na, j0, nb, td0);
+    int cur = ti;          // s index of the current vertex
+    int anext = ti + 1;    // s index of the next boundary
+    long long bj = j0 + (td0 - ti);
+    for (int step = td0; step < td1; ++step) {
+      if (anext <= na && (long long)s_a[anext] <= bj) {
+        cur = anext++;
+      } else {
+        const int32_t e = s_beg[cur] + (int32_t)(bj - s_a[cur]);
+        visit(g, lv, g.idx[e], edges);
+        ++bj;
+      }
+    }
+    __syncthreads();
+  }
+  block_add_u64(edges, &st->next_edges);
+}
+
+// ---------------------------------------------------------------------------
+// Pull, bottom-up over the visited bitmap (Section 3.1.2 vertex pull). A warp
+// owns 32 consecutive vertices (one bitmap word); each unvisited lane scans its
+// in-neighbours and stops at the first visited one. At the start of level L a
+// visited in-neighbour of an unvisited vertex has depth exactly L (a smaller
+// depth would already have reached the vertex), so the current bitmap is the
+// frontier test. New bits go to the other bitmap (read and write sets stay
+// apart); the found vertices are appended to the queue with one atomic per
+// warp (ballot + prefix popcount), which is also the bitmap-to-queue
+// conversion a following push level needs.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunState* st) {
+  const int32_t L1 = st->level + 1;
+  const bool vs = st->vsel != 0u;
+  const uint32_t* __restrict__ cur_vis = vs ? b.vis[1] : b.vis[0];
+  uint32_t* nxt_vis = vs ? b.vis[0] : b.vis[1];
+  int32_t* qout = st->qsel ? b.q[0] : b.q[1];
+  int32_t* depth = st->depth;
+  unsigned int* tail = &st->next_count;
+  const uint32_t lane = lane_id();
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned long long edges = 0;
+  for (int w = warp; w < g.words; w += nwarps) {
+    const uint32_t cw = cur_vis[w];
+    uint32_t fm = 0;
+    if (cw != kFull) {
+      const int32_t v = w * 32 + (int32_t)lane;
+      bool found = false;
+      int32_t deg = 0;
+      if (v < g.n && !((cw >> lane) & 1u)) {
+        const int32_t beg = g.in_off[v], end = g.in_off[v + 1];
+        for (int32_t e = beg; e < end; ++e) {
+          const int32_t u = g.in_idx[e];
+          if ((ld_nc_u32(cur_vis + (u >> 5)) >> (u & 31)) & 1u) {
+            found = true;
+            break;
+          }
+        }
+        if (found) deg = g.symmetric ? end - beg : g.off[v + 1] - g.off[v];
+      }
+      fm = __ballot_sync(kFull, found);
+      if (fm) {
+        unsigned int base = 0;
+        if (lane == 0) base = atomicAdd(tail, (unsigned)__popc(fm));
+        base = __shfl_sync(kFull, base, 0);
+        if (found) {
+          depth[v] = L1;
+          edges += (unsigned long long)deg;
+          qout[base + __popc(fm & lanemask_lt())] = v;
+        }
+      }
+    }
+    if (lane == 0) nxt_vis[w] = cw | fm;
+  }
+  block_add_u64(edges, &st->next_edges);
+}
+
+// ---------------------------------------------------------------------------
+// Graph creation: validation, out-degree statistics, transpose
+// ---------------------------------------------------------------------------
+__global__ void k_validate(const int32_t* off, const int32_t* idx, int32_t n, int32_t m, int32_t* bad) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int32_t my = 0;
+  if (tid == 0 && (off[0] != 0 || off[n] != m)) my = 1;
+  for (int64_t v = tid; v < n; v += stride)
+    if (off[v + 1] < off[v]) my = 1;
+  for (int64_t e = tid; e < m; e += stride)
+    if (idx[e] < 0 || idx[e] >= n) my = 1;
+  if (my) atomicOr(bad, 1);
+}
+
+__global__ void k_deg_reduce(const int32_t* off, int32_t n, unsigned long long* s1, unsigned long long* s2,
+                             int32_t* dmin, int32_t* dmax) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long a = 0, q = 0;
+  int32_t lo = INT32_MAX, hi = 0;
+  for (int64_t v = tid; v < n; v += stride) {
+    const int32_t d = off[v + 1] - off[v];
+    a += (unsigned long long)d;
+    q += (unsigned long long)d * (unsigned long long)d;
+    lo = min(lo, d);
+    hi = max(hi, d);
+  }
+  block_add_u64(a, s1);
+  block_add_u64(q, s2);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+    hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+  }
+  if (lane_id() == 0) {
+    atomicMin(dmin, lo);
+    atomicMax(dmax, hi);
+  }
+}
+
+__global__ void k_deg_hist(const int32_t* off, int32_t n, int32_t* hist) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = tid; v < n; v += stride) atomicAdd(&hist[off[v + 1] - off[v]], 1);
+}
+
+namespace {
+__device__ unsigned long long isqrt_u128(unsigned __int128 x) {
+  unsigned long long lo = 0, hi = 0xffffffffull << 32 | 0xffffffffull;
+  // largest r with r*r <= x (r < 2^64)
+  while (lo < hi) {
+    const unsigned long long mid = lo + ((hi - lo) >> 1) + 1;
+    if ((unsigned __int128)mid * mid <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+}  // namespace
+
+// One block: 5-number summary by nearest rank (q_k = sorted[floor(k (n-1)/4)])
+// from the degree histogram, and floor(256 sigma) exactly:
+// isqrt(65536 (n S2 - S1^2)) / n.
+__global__ void k_deg_finish(const int32_t* hist, int32_t maxdeg, int32_t n, const unsigned long long* s1p,
+                             const unsigned long long* s2p, long long* out6) {
+  __shared__ long long carry_s;
+  long long rank[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) rank[k] = ((long long)k * (n - 1)) / 4;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base <= maxdeg; base += blockDim.x) {
+    const int d = base + threadIdx.x;
+    const long long c = d <= maxdeg ? hist[d] : 0;
+    long long tot;
+    const long long ex = block_exclusive_scan<long long>(c, &tot);
+    const long long before = carry_s + ex;  // vertices with degree < d
+    // d is the k-th quantile when before <= rank_k < before + c
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      if (c > 0 && before <= rank[k] && rank[k] < before + c) out6[k] = d;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const unsigned __int128 S1 = *s1p, S2 = *s2p;
+    const unsigned __int128 var_n2 = (unsigned __int128)n * S2 - S1 * S1;
+    out6[5] = (long long)(isqrt_u128(var_n2 * 65536u) / (unsigned long long)n);
+  }
+}
+
+__global__ void k_tr_count(const int32_t* idx, int32_t m, int32_t* cnt) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = tid; e < m; e += stride) atomicAdd(&cnt[idx[e]], 1);
+}
+
+// Generic exclusive scan of int32 (three kernels): per-block sums, scan of the
+// block sums, apply. Blocks of kThreads threads x kPeItems items.
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const int32_t* in, int32_t len, long long* bsum) {
+  const int nblk = (len + kPeTile - 1) / kPeTile;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    long long s = 0;
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k) {
+      const long long i = (long long)blk * kPeTile + k * kThreads + threadIdx.x;
+      if (i < len) s += in[i];
+    }
+    long long tot;
+    block_exclusive_scan<long long>(s, &tot);
+    if (threadIdx.x == 0) bsum[blk] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_top(long long* bsum, int32_t nblk) {
+  long long carry = 0;
+  for (int base = 0; base < nblk; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const long long x = i < nblk ? bsum[i] : 0;
+    long long tot;
+    const long long ex = block_exclusive_scan<long long>(x, &tot);
+    if (i < nblk) bsum[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) bsum[nblk] = carry;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_apply(const int32_t* in, int32_t len, const long long* bsum,
+                                                         int32_t* out) {
+  const int nblk = (len + kPeTile - 1) / kPeTile;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const long long base = (long long)blk * kPeTile + threadIdx.x * kPeItems;
+    int32_t d[kPeItems];
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k) d[k] = (base + k < len) ? in[base + k] : 0;
+    long long run = 0;
+    long long ex_k[kPeItems];
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k) {
+      ex_k[k] = run;
+      run += d[k];
+    }
+    long long tot;
+    const long long ex = block_exclusive_scan<long long>(run, &tot);
+    const long long o = bsum[blk] + ex;
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k)
+      if (base + k < len) out[base + k] = (int32_t)(o + ex_k[k]);
+    if (blk == nblk - 1 && threadIdx.x == 0) out[len] = (int32_t)bsum[nblk];
+  }
+}
+
+__global__ void k_tr_scatter(const int32_t* off, const int32_t* idx, int32_t n, int32_t* cursor, int32_t* in_idx) {
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = tid; u < n; u += stride)
+    for (int32_t e = off[u]; e < off[u + 1]; ++e) {
+      const int32_t v = idx[e];
+      in_idx[atomicAdd(&cursor[v], 1)] = (int32_t)u;
+    }
+}
+
+}  // namespace bfs

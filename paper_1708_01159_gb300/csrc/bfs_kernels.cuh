@@ -1,0 +1,39 @@
+// Kernel declarations and launch shapes shared by the kernel and host sources.
+#pragma once
+
+#include "bfs_internal.cuh"
+
+namespace bfs {
+
+constexpr int kThreads = 256;     // block size of the level kernels
+constexpr int kCtaChunk = 2048;   // int32 per shared-memory stage of the CTA variant (8 KB)
+constexpr int kCtaDirect = 512;   // adjacency shorter than this is read directly, not staged
+constexpr int kPeItems = 8;       // items per thread in the edge-centric scan / expand
+constexpr int kPeTile = kThreads * kPeItems;  // frontier entries per scan block, items per expand tile
+
+__global__ void k_init(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root, int32_t forced,
+                       const TreeNode* tree, int32_t tree_nodes, int32_t use_handles);
+__global__ void k_decide(DevGraph g, Buffers b, RunState* st);
+__global__ void k_push_thread(DevGraph g, Buffers b, RunState* st);
+__global__ void k_push_warp(DevGraph g, Buffers b, RunState* st);
+__global__ void k_push_cta(DevGraph g, Buffers b, RunState* st);
+__global__ void k_pe_reduce(DevGraph g, Buffers b, RunState* st);
+__global__ void k_pe_top(DevGraph g, Buffers b, RunState* st);
+__global__ void k_pe_scan(DevGraph g, Buffers b, RunState* st);
+__global__ void k_pe_expand(DevGraph g, Buffers b, RunState* st);
+__global__ void k_pull(DevGraph g, Buffers b, RunState* st);
+
+// graph creation
+__global__ void k_validate(const int32_t* off, const int32_t* idx, int32_t n, int32_t m, int32_t* bad);
+__global__ void k_deg_reduce(const int32_t* off, int32_t n, unsigned long long* s1, unsigned long long* s2,
+                             int32_t* dmin, int32_t* dmax);
+__global__ void k_deg_hist(const int32_t* off, int32_t n, int32_t* hist);
+__global__ void k_deg_finish(const int32_t* hist, int32_t maxdeg, int32_t n, const unsigned long long* s1,
+                             const unsigned long long* s2, long long* out6);
+__global__ void k_tr_count(const int32_t* idx, int32_t m, int32_t* cnt);
+__global__ void k_scan_reduce(const int32_t* in, int32_t len, long long* bsum);
+__global__ void k_scan_top(long long* bsum, int32_t nblocks);
+__global__ void k_scan_apply(const int32_t* in, int32_t len, const long long* bsum, int32_t* out);
+__global__ void k_tr_scatter(const int32_t* off, const int32_t* idx, int32_t n, int32_t* cursor, int32_t* in_idx);
+
+}  // namespace bfs

@@ -1,0 +1,81 @@
+"""The C ABI library builds, loads and exports every symbol include/bfs.h
+declares; host-side argument checks and tree parsing work without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1708_01159_gb300 as bfs
+from paper_1708_01159_gb300 import buildlib as bfs_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bfs.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(bfs_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    bfs.build()
+    return bfs.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("bfs_graph_create", "bfs_graph_destroy", "bfs_graph_info", "bfs_load_tree", "bfs_run",
+                 "bfs_run_ex", "bfs_run_batch", "bfs_profile_levels", "bfs_status_string"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_status_strings(lib):
+    assert bfs.status_string(bfs.BFS_OK) == "ok"
+    assert bfs.status_string(bfs.BFS_ERR_TIMEOUT) == "timed out"
+    assert lib.bfs_version() >= 100
+
+
+def test_host_side_argument_checks(lib):
+    import numpy as np
+    off = np.array([0, 1, 2], np.int32)
+    idx = np.array([1, 0], np.int32)
+    out = ctypes.c_void_p()
+    # n < 1, unknown flags and null output are rejected before any CUDA call
+    assert lib.bfs_graph_create(off.ctypes.data, idx.ctypes.data, 0, 2, 1, ctypes.byref(out)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_graph_create(off.ctypes.data, idx.ctypes.data, 2, 2, 1 << 7, ctypes.byref(out)) == \
+        bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_graph_create(off.ctypes.data, idx.ctypes.data, 2, 2, 1, None) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_graph_create(None, idx.ctypes.data, 2, 2, 1, ctypes.byref(out)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_run(None, 0, None, None) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_graph_destroy(None) == bfs.BFS_OK
+
+
+def test_tree_files(lib, tmp_path):
+    # the built-in tree file parses on both sides
+    rows = bfs_build.parse_tree_text(open(bfs.DEFAULT_TREE).read())
+    assert rows and all(len(r) == 5 for r in rows)
+    bfs.bfs_load_tree(bfs.DEFAULT_TREE)
+    bfs.bfs_load_tree(None)
+    with pytest.raises(bfs.BFSError) as e:
+        bfs.bfs_load_tree(str(tmp_path / "missing.tree"))
+    assert e.value.code == bfs.BFS_ERR_NOT_FOUND
+    bad = tmp_path / "bad.tree"
+    # a cycle (child index not greater than its parent) must be rejected
+    bad.write_text("bfs-tree 1 2\n8 5 0 1 -1\n-1 0 -1 -1 3\n")
+    with pytest.raises(bfs.BFSError) as e:
+        bfs.bfs_load_tree(str(bad))
+    assert e.value.code == bfs.BFS_ERR_INVALID_ARG
+    bad.write_text("bfs-tree 1 1\n-1 0 -1 -1 9\n")  # class out of range
+    with pytest.raises(bfs.BFSError):
+        bfs.bfs_load_tree(str(bad))
+    bad.write_text("bfs-tree 1 3\n99 5 1 2 -1\n-1 0 -1 -1 3\n-1 0 -1 -1 4\n")  # feature out of range
+    with pytest.raises(bfs.BFSError):
+        bfs.bfs_load_tree(str(bad))

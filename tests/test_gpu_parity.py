@@ -1,0 +1,297 @@
+"""GPU parity: depths from the CUDA path (through the C ABI) equal the CPU
+oracle's element by element, on every variant, under tree switching, on edge
+cases and at full workload sizes. Integer results: the bar is bit-exact."""
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import paper_1708_01159_gb300 as bfs
+from tests import graphs_closed_form as cf
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+V = bfs.NUM_VARIANTS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    bfs.build()
+    bfs.bfs_load_tree(None)
+    yield
+
+
+def make(g, flags=bfs.BFS_SYMMETRIC):
+    return bfs.Graph(g.off, g.idx, flags)
+
+
+def run(G, root, variant=bfs.VARIANT_TREE, log=64):
+    d = torch.empty(G.n, dtype=torch.int32, device="cuda")
+    st = bfs.bfs_run_ex(G.handle, int(root), d, forced_variant=variant, stats=True, log_capacity=log)
+    return d.cpu().numpy(), st
+
+
+def assert_parity(g, G, root, variant=bfs.VARIANT_TREE):
+    ref = oracle.bfs(g.off, g.idx, int(root))
+    dep, st = run(G, root, variant, log=max(ref.num_levels + 1, 1))
+    assert np.array_equal(dep, ref.depth), f"root {root} variant {variant}: depth mismatch " \
+        f"({int((dep != ref.depth).sum())} entries)"
+    assert st["edges_reached"] == ref.edges_reached
+    assert st["vertices_reached"] == int((ref.depth >= 0).sum())
+    assert st["levels"] == ref.num_levels
+    assert st["status"] == 0
+    k = min(ref.num_levels, len(st["frontier"]))
+    assert np.array_equal(st["frontier"][:k], ref.level_count[:k])
+    assert np.array_equal(st["frontier_edges"][:k], ref.level_edges[:k])
+    if variant >= 0:
+        assert np.all(st["variant"][:k] == variant)
+    return ref, st
+
+
+# ------------------------------------------------------------- small graphs
+
+def test_rmat_s14_push_thread_16_roots():
+    """R-MAT scale 14, edge factor 16, 16 seeded roots of nonzero degree, one
+    fixed top-down push kernel: bit-exact depths."""
+    g = gg.rmat_s14_ef16()
+    roots = gg.sample_roots(g, 16, seed=gg.SEED_ROOTS)
+    with make(g) as G:
+        for r in roots:
+            assert_parity(g, G, r, variant=0)
+
+
+@pytest.mark.parametrize("variant", range(V))
+@pytest.mark.parametrize("which", ["rmat13", "grid70x53", "er9000", "rmat12_perm"])
+def test_each_variant(which, variant):
+    g = {"rmat13": lambda: gg.rmat(13, 16, seed=11), "grid70x53": lambda: gg.grid(70, 53, 0.1, seed=12),
+         "er9000": lambda: gg.erdos_renyi(9000, 6.0, seed=13),
+         "rmat12_perm": lambda: gg.rmat(12, 8, seed=14, permute=True)}[which]()
+    with make(g) as G:
+        for r in gg.sample_roots(g, 3, seed=5):
+            assert_parity(g, G, r, variant)
+
+
+@pytest.mark.parametrize("name", sorted(cf.ALL))
+def test_closed_forms_all_variants(name):
+    g, fn = cf.ALL[name]()
+    with make(g) as G:
+        for r in range(0, g.n, max(1, g.n // 5)):
+            for v in [bfs.VARIANT_TREE] + list(range(V)):
+                dep, st = run(G, r, v)
+                assert np.array_equal(dep, fn(r)), (name, r, v)
+
+
+def test_directed_graph_uses_transpose():
+    rng = np.random.default_rng(3)
+    n = 3000
+    s = rng.integers(0, n, 12000)
+    t = rng.integers(0, n, 12000)
+    g = gg.from_edges(n, s, t, symmetrize=False, name="directed")
+    with make(g, flags=0) as G:
+        assert not G.info()["symmetric"]
+        for r in gg.sample_roots(g, 4, seed=1):
+            for v in [bfs.VARIANT_TREE] + list(range(V)):
+                assert_parity(g, G, r, v)
+
+
+def test_hub_star_exercises_staged_cta_path():
+    # one hub of degree 200k (staged through shared memory in many chunks) plus a tail
+    n = 200_003
+    s = np.zeros(n - 3, np.int32)
+    t = np.arange(1, n - 2, dtype=np.int32)
+    s = np.concatenate([s, [n - 3, n - 2]]).astype(np.int32)
+    t = np.concatenate([t, [n - 2, n - 1]]).astype(np.int32)
+    g = gg.from_edges(n, s, t, name="hub")
+    with make(g) as G:
+        for r in (0, 5, n - 1):
+            for v in range(V):
+                assert_parity(g, G, r, v)
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_edge_cases():
+    # single vertex, no edges
+    g = gg.Graph(np.array([0, 0], np.int32), np.zeros(0, np.int32))
+    with make(g) as G:
+        dep, st = run(G, 0)
+        assert dep.tolist() == [0] and st["edges_reached"] == 0 and st["levels"] == 1
+    # isolated root in a larger graph; ragged n (not a multiple of 32 or 4)
+    g = gg.rmat(10, 4, seed=3)
+    iso = int(np.nonzero(g.degrees() == 0)[0][0])
+    with make(g) as G:
+        for v in [bfs.VARIANT_TREE] + list(range(V)):
+            dep, st = run(G, iso, v)
+            exp = np.full(g.n, -1, np.int32)
+            exp[iso] = 0
+            assert np.array_equal(dep, exp) and st["edges_reached"] == 0
+        with pytest.raises(bfs.BFSError) as e:
+            run(G, g.n)
+        assert e.value.code == bfs.BFS_ERR_INVALID_ARG
+        with pytest.raises(bfs.BFSError):
+            run(G, -1)
+    g, fn = cf.path(37)
+    with make(g) as G:
+        dep, _ = run(G, 36)
+        assert np.array_equal(dep, fn(36))
+
+
+def test_unaligned_depth_output_and_host_output():
+    g = gg.rmat(11, 8, seed=9)
+    r = int(gg.sample_roots(g, 1, seed=2)[0])
+    ref = oracle.bfs(g.off, g.idx, r)
+    with make(g) as G:
+        buf = torch.empty(g.n + 1, dtype=torch.int32, device="cuda")
+        bfs.bfs_run(G.handle, r, buf[1:])  # 4-byte aligned only: scalar init path
+        torch.cuda.synchronize()
+        assert np.array_equal(buf[1:].cpu().numpy(), ref.depth)
+        host = np.empty(g.n, np.int32)
+        bfs.bfs_run_ex(G.handle, r, host, depth_on_host=True)
+        assert np.array_equal(host, ref.depth)
+        pinned = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        bfs.bfs_run_ex(G.handle, r, pinned, depth_on_host=True)
+        assert np.array_equal(pinned.numpy(), ref.depth)
+
+
+def test_bad_graphs_rejected_on_device():
+    off = np.array([0, 2, 3], np.int32)
+    with pytest.raises(bfs.BFSError) as e:
+        bfs.Graph(off, np.array([1, 5, 0], np.int32))  # index out of range
+    assert e.value.code == bfs.BFS_ERR_BAD_GRAPH
+    with pytest.raises(bfs.BFSError):
+        bfs.Graph(np.array([0, 3, 2], np.int32), np.array([1, 0, 1], np.int32))  # decreasing offsets
+    with pytest.raises(bfs.BFSError):
+        bfs.Graph(np.array([1, 2, 3], np.int32), np.array([1, 0, 1], np.int32))  # off[0] != 0
+
+
+def test_device_input_and_graph_info():
+    g = gg.rmat(12, 16, seed=21)
+    off = torch.from_numpy(g.off).cuda()
+    idx = torch.from_numpy(g.idx).cuda()
+    with bfs.Graph(off, idx) as G:
+        info = G.info()
+        assert info["n"] == g.n and info["m"] == g.m
+        st = oracle.degree_stats(g.off)
+        assert info["deg_summary"] == st[:5] and info["deg_sd256"] == st[5]
+        for r in gg.sample_roots(g, 2, seed=4):
+            assert_parity(g, G, r)
+
+
+def test_injected_oom_is_reported():
+    g = gg.rmat(10, 8, seed=3)
+    bfs.lib().bfs_debug_fail_alloc_after(1)
+    try:
+        with pytest.raises(bfs.BFSError) as e:
+            make(g)
+        assert e.value.code == bfs.BFS_ERR_OOM
+    finally:
+        bfs.lib().bfs_debug_fail_alloc_after(0)
+    with make(g) as G:  # the library is still usable
+        assert_parity(g, G, int(gg.sample_roots(g, 1)[0]))
+
+
+# -------------------------------------------------- switching and the schedule
+
+def test_tree_schedule_matches_oracle_walk():
+    """The variant log of a switched run equals the oracle's walk of the same
+    tree over the oracle's per-level features, unknown-prediction rule included."""
+    from paper_1708_01159_gb300 import buildlib
+    rows = buildlib.parse_tree_text(open(bfs.DEFAULT_TREE).read())
+    tree = {"nodes": [{"f": f, "t": t, "l": l, "r": r, "v": v} for f, t, l, r, v in rows]}
+    for g in (gg.rmat(14, 16, seed=31), gg.grid(60, 60, 0.1, seed=32), gg.erdos_renyi(20000, 10.0, seed=33)):
+        with make(g) as G:
+            for r in gg.sample_roots(g, 3, seed=6):
+                ref, st = assert_parity(g, G, r)
+                feats = oracle.level_features(g.off, ref)
+                want = oracle.predict_schedule(tree, feats)
+                assert st["variant"][:len(want)].tolist() == want
+
+
+def test_custom_tree_file_with_unknown_leaves(tmp_path):
+    # unknown at level 0 -> edge list default; unknown later -> repeat previous
+    p = tmp_path / "t.tree"
+    p.write_text("bfs-tree 1 5\n13 0 1 2 -1\n-1 0 -1 -1 -1\n8 50 3 4 -1\n-1 0 -1 -1 -1\n-1 0 -1 -1 4\n")
+    tree = {"nodes": [{"f": 13, "t": 0, "l": 1, "r": 2, "v": -1}, {"f": -1, "t": 0, "l": -1, "r": -1, "v": -1},
+                      {"f": 8, "t": 50, "l": 3, "r": 4, "v": -1}, {"f": -1, "t": 0, "l": -1, "r": -1, "v": -1},
+                      {"f": -1, "t": 0, "l": -1, "r": -1, "v": 4}]}
+    bfs.bfs_load_tree(str(p))
+    try:
+        g = gg.rmat(13, 16, seed=41)
+        with make(g) as G:
+            for r in gg.sample_roots(g, 3, seed=7):
+                ref, st = assert_parity(g, G, r)
+                want = oracle.predict_schedule(tree, oracle.level_features(g.off, ref))
+                assert st["variant"][:len(want)].tolist() == want
+    finally:
+        bfs.bfs_load_tree(None)
+
+
+def test_profile_levels_features_match_oracle():
+    g = gg.rmat(13, 16, seed=51)
+    r = int(gg.sample_roots(g, 1, seed=8)[0])
+    ref = oracle.bfs(g.off, g.idx, r)
+    with make(g) as G:
+        feats, ms, tv = bfs.bfs_profile_levels(G.handle, r, reps=3)
+        assert feats.shape[0] == ref.num_levels
+        assert feats.tolist() == oracle.level_features(g.off, ref)
+        assert np.all(ms > 0)
+        # the harness leaves the graph usable and results unchanged
+        assert_parity(g, G, r)
+
+
+def test_concurrent_streams():
+    g = gg.rmat(14, 16, seed=61)
+    roots = gg.sample_roots(g, 6, seed=9)
+    refs = [oracle.bfs(g.off, g.idx, int(r)).depth for r in roots]
+    with make(g) as G:
+        streams = [torch.cuda.Stream() for _ in range(3)]
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in roots]
+        for k in range(2):
+            for i, r in enumerate(roots):
+                bfs.bfs_run(G.handle, int(r), outs[i], streams[i % 3])
+        torch.cuda.synchronize()
+        for i in range(len(roots)):
+            assert np.array_equal(outs[i].cpu().numpy(), refs[i])
+        assert G.info()["num_workspaces"] >= 1
+
+
+def test_batch_equals_single_runs():
+    g = gg.rmat(12, 16, seed=71)
+    roots = gg.sample_roots(g, 70, seed=10)  # more than one wave of 64
+    with make(g) as G:
+        out = torch.empty(len(roots) * g.n, dtype=torch.int32, device="cuda")
+        edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
+        torch.cuda.synchronize()
+        D, E = oracle.bfs_batch(g.off, g.idx, roots)
+        assert np.array_equal(out.cpu().numpy().reshape(len(roots), g.n), D)
+        assert np.array_equal(edges, E)
+
+
+# --------------------------------------------------------- full-size workloads
+
+@pytest.mark.slow
+def test_rmat_s22_full_size():
+    """R-MAT scale 22, edge factor 16 (~128M directed edges), roots in the giant
+    component: switched and every fixed variant bit-exact, in the launch
+    configuration the benchmark times."""
+    g = gg.rmat_s22_ef16()
+    roots = gg.sample_roots(g, 2, seed=gg.SEED_ROOTS + 1, giant=True)
+    with make(g) as G:
+        for i, r in enumerate(roots):
+            assert_parity(g, G, r)
+            if i == 0:
+                for v in range(V):
+                    assert_parity(g, G, r, v)
+
+
+@pytest.mark.slow
+def test_grid_4096_full_size():
+    """4096 x 4096 permuted grid with 10% of edges dropped: thousands of levels."""
+    g = gg.grid_4096_permuted()
+    r = int(gg.sample_roots(g, 1, seed=gg.SEED_ROOTS + 2, giant=True)[0])
+    with make(g) as G:
+        ref, st = assert_parity(g, G, r)
+        assert ref.num_levels > 1000
