@@ -1,0 +1,280 @@
+"""Training the per-level decision tree (Section 4.1, Section 4.2).
+
+  collect  -- on a GPU: run the per-level timing harness (bfs_profile_levels)
+              over a set of generated graphs and roots and write one CSV row
+              per (graph, root, level): the 14 integer features and the median
+              time of every variant expanding that level from the same state.
+  train    -- label every level with its fastest variant, fit a CART tree
+              (Gini impurity, scikit-learn) and export it in the integer text
+              format bfs_load_tree reads: thresholds become floor(t) (the
+              features are integers, so x <= t and x <= floor(t) agree), and a
+              leaf whose two largest class weights tie is marked unknown (-1),
+              the case Section 4.1 resolves by repeating the previous level's
+              choice.
+  evaluate -- per traversal, the time of the tree's schedule (unknown rule
+              applied), of the best fixed variant and of every variant, each
+              relative to the per-level optimum (the shape of Table 2).
+
+The benchmark's own graph (R-MAT scale 22, seed 1001) is never in the
+training set. Graphs are split into train and test sets by graph, since the
+levels of one traversal are correlated.
+
+  python -m paper_1708_01159_gb300.train collect --out levels.csv
+  python -m paper_1708_01159_gb300.train train --csv levels.csv --out trees/default.tree
+  python -m paper_1708_01159_gb300.train evaluate --csv levels.csv --tree trees/default.tree
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+from paper_1708_01159_gb300 import FEATURES, NUM_FEATURES, NUM_VARIANTS, VARIANTS  # noqa: E402
+
+LEVEL0_DEFAULT = 3  # Section 4.1: unknown at the first level -> edge list (edge-centric push)
+
+# Training graphs: (name, generator kwargs). Seeds start at 3000; the
+# benchmark graph uses seed 1001 and is excluded by construction.
+TRAIN_GRAPHS = [
+    ("rmat", dict(scale=16, edge_factor=16, seed=3001)),
+    ("rmat", dict(scale=18, edge_factor=8, seed=3002)),
+    ("rmat", dict(scale=18, edge_factor=32, seed=3003)),
+    ("rmat", dict(scale=20, edge_factor=16, seed=3004)),
+    ("rmat", dict(scale=20, edge_factor=4, seed=3005)),
+    ("rmat", dict(scale=21, edge_factor=16, seed=3006, permute=True)),
+    ("rmat", dict(scale=22, edge_factor=16, seed=3007)),
+    ("rmat", dict(scale=22, edge_factor=8, seed=3008)),
+    ("rmat", dict(scale=19, edge_factor=16, seed=3009, a=0.45, b=0.15, c=0.15)),
+    ("rmat", dict(scale=21, edge_factor=24, seed=3010, a=0.50, b=0.20, c=0.20)),
+    ("grid", dict(rows=512, cols=512, drop=0.1, seed=3011)),
+    ("grid", dict(rows=1024, cols=1024, drop=0.1, seed=3012)),
+    ("grid", dict(rows=2048, cols=2048, drop=0.2, seed=3013)),
+    ("grid", dict(rows=1500, cols=3000, drop=0.05, seed=3014)),
+    ("er", dict(n=1 << 20, avg_degree=4.0, seed=3015)),
+    ("er", dict(n=1 << 21, avg_degree=8.0, seed=3016)),
+    ("er", dict(n=1 << 22, avg_degree=16.0, seed=3017)),
+    ("er", dict(n=1 << 18, avg_degree=32.0, seed=3018)),
+]
+
+
+def make_graph(kind, kw):
+    import graphgen as gg
+    if kind == "rmat":
+        kw = dict(kw)
+        return gg.rmat(kw.pop("scale"), kw.pop("edge_factor"), **kw)
+    if kind == "grid":
+        return gg.grid(kw["rows"], kw["cols"], kw["drop"], seed=kw["seed"], permute=True)
+    if kind == "er":
+        return gg.erdos_renyi(kw["n"], kw["avg_degree"], seed=kw["seed"])
+    raise ValueError(kind)
+
+
+def collect(out: str, roots_per_graph: int = 4, reps: int = 3, max_levels: int = 4096, graphs=None):
+    import graphgen as gg
+    import torch
+    import paper_1708_01159_gb300 as bfs
+    bfs.build()
+    torch.cuda.set_device(0)
+    graphs = graphs or TRAIN_GRAPHS
+    cols = ["graph", "root", "level"] + list(FEATURES) + [f"ms_{v}" for v in VARIANTS] + ["tree_variant"]
+    with open(out, "w", newline="") as fh:
+        w = csv.writer(fh)
+        w.writerow(cols)
+        for kind, kw in graphs:
+            t0 = time.time()
+            g = make_graph(kind, kw)
+            name = g.name
+            roots = gg.sample_roots(g, roots_per_graph, seed=kw["seed"] + 500, giant=True)
+            with bfs.Graph(g.off, g.idx) as G:
+                for r in roots:
+                    feats, ms, tv = bfs.bfs_profile_levels(G.handle, int(r), reps=reps, capacity=max_levels)
+                    for L in range(feats.shape[0]):
+                        w.writerow([name, int(r), L] + [int(x) for x in feats[L]] + [f"{x:.5f}" for x in ms[L]]
+                                   + [int(tv[L])])
+            fh.flush()
+            print(f"{name}: {len(roots)} roots in {time.time() - t0:.1f}s", file=sys.stderr, flush=True)
+
+
+def load(csv_path: str):
+    rows = list(csv.DictReader(open(csv_path)))
+    graph = np.array([r["graph"] for r in rows])
+    root = np.array([int(r["root"]) for r in rows])
+    level = np.array([int(r["level"]) for r in rows])
+    X = np.array([[int(r[f]) for f in FEATURES] for r in rows], dtype=np.int64).reshape(-1, NUM_FEATURES)
+    T = np.array([[float(r[f"ms_{v}"]) for v in VARIANTS] for r in rows]).reshape(-1, NUM_VARIANTS)
+    return graph, root, level, X, T
+
+
+def split_by_graph(graph, test_frac=0.3, seed=0):
+    names = sorted(set(graph.tolist()))
+    rng = np.random.default_rng(seed)
+    rng.shuffle(names)
+    k = max(1, int(round(test_frac * len(names))))
+    test = set(names[:k])
+    return np.array([g not in test for g in graph]), sorted(test)
+
+
+def fit(X, T, feature_idx, max_depth=8, min_samples_leaf=8, weighting="regret"):
+    """CART with Gini impurity (Section 2.1). Labels: the fastest variant per
+    level. With weighting='regret' each level weighs its spread of times
+    (slowest minus fastest), so the tree spends its splits where a wrong choice
+    costs the most; 'uniform' is the paper's plain classification."""
+    from sklearn.tree import DecisionTreeClassifier
+    y = T.argmin(axis=1)
+    if weighting == "regret":
+        w = T.max(axis=1) - T.min(axis=1) + 1e-4
+    else:
+        w = np.ones(len(y))
+    clf = DecisionTreeClassifier(criterion="gini", max_depth=max_depth, min_samples_leaf=min_samples_leaf,
+                                 random_state=0)
+    clf.fit(X[:, feature_idx], y, sample_weight=w)
+    return clf
+
+
+def export(clf, feature_idx, path, meta=""):
+    """Integer tree text: 'feature threshold left right value' per node."""
+    t = clf.tree_
+    lines = []
+    for i in range(t.node_count):
+        if t.children_left[i] < 0:
+            v = t.value[i][0]
+            order = np.argsort(v)[::-1]
+            cls = clf.classes_
+            top = int(cls[order[0]])
+            tie = len(order) > 1 and math.isclose(float(v[order[0]]), float(v[order[1]]), rel_tol=1e-9)
+            lines.append(f"-1 0 -1 -1 {-1 if tie else top}")
+        else:
+            f = int(feature_idx[t.feature[i]])
+            lines.append(f"{f} {int(math.floor(t.threshold[i]))} {t.children_left[i]} {t.children_right[i]} -1")
+    with open(path, "w") as fh:
+        fh.write("# Decision tree trained on per-level GB300 timings (CART, Gini).\n")
+        for m in meta.splitlines():
+            fh.write(f"# {m}\n")
+        fh.write("# Features: " + ", ".join(f"{i} {f}" for i, f in enumerate(FEATURES)) + "\n")
+        fh.write("# Classes: " + ", ".join(f"{i} {v}" for i, v in enumerate(VARIANTS)) + "\n")
+        fh.write(f"bfs-tree 1 {t.node_count}\n")
+        fh.write("\n".join(lines) + "\n")
+
+
+def read_tree(path):
+    from paper_1708_01159_gb300.buildlib import parse_tree_text
+    rows = parse_tree_text(open(path).read())
+    return [{"f": f, "t": t, "l": l, "r": r, "v": v} for f, t, l, r, v in rows]
+
+
+def walk(nodes, x):
+    i = 0
+    while nodes[i]["f"] >= 0:
+        i = nodes[i]["l"] if x[nodes[i]["f"]] <= nodes[i]["t"] else nodes[i]["r"]
+    return nodes[i]["v"]
+
+
+def schedule_time(nodes, X, T, level):
+    """Per-level choice with the unknown rule; returns the chosen variants."""
+    out = np.empty(len(X), dtype=np.int64)
+    for i in range(len(X)):
+        v = walk(nodes, X[i])
+        if v < 0:
+            v = out[i - 1] if level[i] > 0 else LEVEL0_DEFAULT
+        out[i] = v
+    return out
+
+
+def evaluate(graph, root, level, X, T, nodes, mask=None):
+    """Table-2-shaped summary over traversals: slowdown vs the per-level optimum."""
+    if mask is None:
+        mask = np.ones(len(X), bool)
+    keys = sorted(set(zip(graph[mask].tolist(), root[mask].tolist())))
+    pred = schedule_time(nodes, X, T, level)
+    rows = {"predicted": [], "best_fixed": []}
+    for v in VARIANTS:
+        rows[v] = []
+    fixed_by_graph = {}
+    for gname in set(graph[mask].tolist()):
+        sel = mask & (graph == gname)
+        fixed_by_graph[gname] = int(T[sel].sum(axis=0).argmin())
+    acc_hits = 0
+    for gname, r in keys:
+        sel = np.nonzero(mask & (graph == gname) & (root == r))[0]
+        opt = T[sel].min(axis=1).sum()
+        rows["predicted"].append(T[sel, pred[sel]].sum() / opt)
+        rows["best_fixed"].append(T[sel, fixed_by_graph[gname]].sum() / opt)
+        for k, v in enumerate(VARIANTS):
+            rows[v].append(T[sel, k].sum() / opt)
+        acc_hits += int((pred[sel] == T[sel].argmin(axis=1)).sum())
+    summary = {}
+    for k, vals in rows.items():
+        a = np.array(vals)
+        summary[k] = {"optimal": float((a < 1.0 + 1e-9).mean()), "1-2x": float(((a >= 1) & (a <= 2)).mean()),
+                      ">5x": float((a > 5).mean()), ">20x": float((a > 20).mean()), "average": float(a.mean()),
+                      "worst": float(a.max())}
+    summary["level_accuracy"] = acc_hits / int(mask.sum())
+    summary["traversals"] = len(keys)
+    return summary
+
+
+def print_table(summary, file=sys.stdout):
+    print(f"traversals: {summary['traversals']}, per-level accuracy: {summary['level_accuracy']:.3f}", file=file)
+    print(f"{'algorithm':14s} {'optimal':>8s} {'1-2x':>7s} {'>5x':>6s} {'>20x':>6s} {'average':>8s} {'worst':>8s}",
+          file=file)
+    for k in ["predicted", "best_fixed"] + list(VARIANTS):
+        s = summary[k]
+        print(f"{k:14s} {s['optimal']:8.2%} {s['1-2x']:7.2%} {s['>5x']:6.2%} {s['>20x']:6.2%} "
+              f"{s['average']:7.2f}x {s['worst']:7.2f}x", file=file)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    sub = p.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("collect")
+    c.add_argument("--out", required=True)
+    c.add_argument("--roots", type=int, default=4)
+    c.add_argument("--reps", type=int, default=3)
+    t = sub.add_parser("train")
+    t.add_argument("--csv", required=True)
+    t.add_argument("--out", required=True)
+    t.add_argument("--features", default="paper", choices=["paper", "all"])
+    t.add_argument("--max-depth", type=int, default=8)
+    t.add_argument("--min-leaf", type=int, default=8)
+    t.add_argument("--weighting", default="regret", choices=["regret", "uniform"])
+    t.add_argument("--all-graphs", action="store_true", help="train on every graph (no held-out split)")
+    e = sub.add_parser("evaluate")
+    e.add_argument("--csv", required=True)
+    e.add_argument("--tree", required=True)
+    a = p.parse_args()
+    if a.cmd == "collect":
+        collect(a.out, a.roots, a.reps)
+        return
+    graph, root, level, X, T = load(a.csv)
+    if a.cmd == "train":
+        # Section 4.2's best set: graph size, % discovered, out-degree distribution, frontier vertex count
+        paper = [0, 1, 2, 3, 4, 5, 6, 7, 8, 11]
+        fidx = np.array(paper if a.features == "paper" else list(range(NUM_FEATURES)))
+        train_mask, test_graphs = split_by_graph(graph)
+        if a.all_graphs:
+            train_mask = np.ones(len(graph), bool)
+        clf = fit(X[train_mask], T[train_mask], fidx, a.max_depth, a.min_leaf, a.weighting)
+        meta = (f"features={a.features} max_depth={a.max_depth} min_samples_leaf={a.min_leaf} "
+                f"weighting={a.weighting}\nlevels={int(train_mask.sum())} "
+                f"held-out graphs={'none' if a.all_graphs else ','.join(test_graphs)}")
+        export(clf, fidx, a.out, meta)
+        nodes = read_tree(a.out)
+        print("train:")
+        print_table(evaluate(graph, root, level, X, T, nodes, train_mask))
+        if not a.all_graphs:
+            print("held-out graphs:", ", ".join(test_graphs))
+            print_table(evaluate(graph, root, level, X, T, nodes, ~train_mask))
+    else:
+        print_table(evaluate(graph, root, level, X, T, read_tree(a.tree)))
+
+
+if __name__ == "__main__":
+    main()
