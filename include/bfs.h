@@ -179,6 +179,32 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
 int bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_out, bfs_stream_t stream,
                   int64_t* edges_out);
 
+/*
+ * Single-source BFS that allocates nothing. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while they
+ * run (code working inside a memory arena it does not own, a plugin given
+ * fixed buffers by its host application, a real-time loop where cudaMalloc may
+ * stall or fail). It makes no cudaMalloc, cudaFree or other allocating call,
+ * and needs no bfs_graph_t: the caller passes the CSR (row_offsets, n + 1
+ * int32; col_indices, m int32) and depth_out (n int32) in device memory it
+ * owns, and gets the same depths as bfs_run.
+ *
+ * Limit: n <= 1,048,576 vertices; larger n returns BFS_ERR_INVALID_ARG. The
+ * traversal's scratch (two frontier queues, the visited bitmap, counters) is a
+ * fixed device array of about 8.1 MB inside the library, held by every GPU that
+ * loads the library until the process exits. The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture. All calls share
+ * the one array, which keeps the previous call's contents (each call clears
+ * what it reads first): calls whose work overlaps on the GPU, from any stream
+ * or thread, race and corrupt each other, so serialise them. The CSR is
+ * validated on every call (BFS_ERR_BAD_GRAPH). Synchronous: the level loop
+ * reads each level's frontier size back to the host. Uses a simple one thread
+ * per frontier vertex push for every level (no tree switching).
+ */
+int bfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int64_t n, int64_t m, int32_t root,
+                   int32_t* depth_out, bfs_stream_t stream);
+
 /* One level of a profiled traversal. */
 typedef struct bfs_level_profile {
   int64_t features[BFS_NUM_FEATURES]; /* the tree's input at this level (enum bfs_feature order) */

@@ -111,6 +111,7 @@ def lib():
             "bfs_profile_levels": (ctypes.c_int, [vp, c_i32, c_i32, c_i32, vp, ctypes.POINTER(_LevelProfile), c_i32,
                                                   ctypes.POINTER(c_i32)]),
             "bfs_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int]),
+            "bfs_run_static": (ctypes.c_int, [vp, vp, c_i64, c_i64, c_i32, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -260,6 +261,21 @@ def bfs_profile_levels(g: int, root: int, reps: int = 5, advance_variant: int = 
     ms = np.array([list(buf[i].ms) for i in range(k)], dtype=np.float64).reshape(k, NUM_VARIANTS)
     tv = np.array([buf[i].tree_variant for i in range(k)], dtype=np.int32)
     return feats, ms, tv
+
+
+def bfs_run_static(row_offsets, col_indices, root: int, depth_out, stream=None) -> None:
+    """BFS that allocates nothing, for callers that cannot allocate device memory
+    while they run. All three arrays are CUDA int32 tensors the caller owns; the
+    library's scratch is a fixed array inside libbfs.so, so n is limited to
+    1,048,576 vertices and calls must not overlap on the GPU. Synchronous."""
+    po, do, no = _ptr(row_offsets, what="row_offsets")
+    pi, di, ni = _ptr(col_indices, what="col_indices")
+    pd, dd, nd = _ptr(depth_out, what="depth_out")
+    if not (do and di and dd):
+        raise ValueError("bfs_run_static takes device arrays only")
+    if nd != no - 1:
+        raise ValueError("depth_out must have n = len(row_offsets) - 1 entries")
+    _check(lib().bfs_run_static(po, pi, no - 1, ni, int(root), pd, _stream(stream)), "bfs_run_static")
 
 
 class Graph:

@@ -493,6 +493,8 @@ int check_graph(bfs_graph_t g) {
 
 }  // namespace
 
+int bfs::set_error_detail(int code, const char* msg) { return fail(code, "%s", msg); }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -103,6 +103,9 @@ struct Buffers {
   int32_t pad_;
 };
 
+// Records `msg` as the calling thread's bfs_last_error_detail() and returns code.
+int set_error_detail(int code, const char* msg);
+
 // ---------------------------------------------------------------------------
 // Small device helpers
 // ---------------------------------------------------------------------------
