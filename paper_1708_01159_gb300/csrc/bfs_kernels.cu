@@ -7,10 +7,12 @@
 // strides over its work.
 //
 // Newly reached vertices are claimed by an atomicOr on the visited bitmap; the
-// single thread that flips a bit writes depth L + 1, appends the vertex to the
-// output queue with a warp-aggregated atomic (the queue tail is the next
-// frontier size, Section 3.1.4 variant 1 with warp aggregation), and adds the
-// vertex's out-degree to the next level's frontier-edge count.
+// single thread that flips a bit writes depth L + 1, stages the vertex in a
+// block-local shared-memory buffer that is flushed to the output queue with
+// one global atomic per block (the queue tail is the next frontier size:
+// Section 3.1.4's first variant, a global atomic counter, with warp and block
+// aggregation in front of it), and adds the vertex's out-degree to the next
+// level's frontier-edge count.
 #include <cooperative_groups.h>
 
 #include "bfs_kernels.cuh"
@@ -98,14 +100,86 @@ __device__ __forceinline__ Level load_level(const Buffers& b, RunState* st) {
   return lv;
 }
 
-// Top-down visit of edge u -> v (Section 3.1.2 push): the first claimant of v
-// sets its depth, appends it and counts its out-degree.
-__device__ __forceinline__ void visit(const DevGraph& g, const Level& lv, int32_t v, unsigned long long& edges) {
-  if (claim(lv.vis, v)) {
-    lv.depth[v] = lv.next_depth;
-    edges += (unsigned long long)(g.off[v + 1] - g.off[v]);
+// Block-local staging of newly reached vertices. Lanes reserve slots with one
+// shared-memory atomic per warp; a block-uniform flush reserves space in the
+// output queue with one global atomic per block and copies the slots out with
+// coalesced stores. (One global queue tail shared by every warp serialises
+// under dense levels; the block stage removes that.) Slots beyond the
+// capacity fall back to a warp-aggregated global append.
+constexpr int kStageCap = 2048;
+
+struct Stage {
+  int32_t* buf;
+  unsigned int* cnt;
+  unsigned int* base;
+};
+
+#define BFS_DECLARE_STAGE(name)                   \
+  __shared__ int32_t name##_buf[kStageCap];       \
+  __shared__ unsigned int name##_cnt, name##_base; \
+  if (threadIdx.x == 0) name##_cnt = 0;           \
+  __syncthreads();                                \
+  const Stage name { name##_buf, &name##_cnt, &name##_base }
+
+__device__ __forceinline__ void stage_push(const Stage& s, const Level& lv, int32_t v) {
+  const uint32_t mask = __activemask();
+  const int leader = __ffs(mask) - 1;
+  unsigned int pos = 0;
+  if ((int)lane_id() == leader) pos = atomicAdd(s.cnt, (unsigned)__popc(mask));
+  pos = __shfl_sync(mask, pos, leader) + (unsigned)__popc(mask & lanemask_lt());
+  if (pos < (unsigned)kStageCap)
+    s.buf[pos] = v;
+  else
     queue_append(lv.qout, lv.tail, v);
+}
+
+// Copies the staged entries out once at least `threshold` are waiting. Every
+// thread of the block must call it (it synchronises).
+__device__ __forceinline__ void stage_flush(const Stage& s, const Level& lv, unsigned int threshold) {
+  __syncthreads();
+  const unsigned int c = min(*s.cnt, (unsigned)kStageCap);
+  if (c == 0 || c < threshold) return;  // uniform: every thread read the same count
+  if (threadIdx.x == 0) *s.base = atomicAdd(lv.tail, c);
+  __syncthreads();
+  const unsigned int b = *s.base;
+  for (unsigned int i = threadIdx.x; i < c; i += blockDim.x) lv.qout[b + i] = s.buf[i];
+  __syncthreads();
+  if (threadIdx.x == 0) *s.cnt = 0;
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// Top-down visit of up to K edges u -> v[k] (Section 3.1.2 push). The bitmap
+// words of all K targets are read, then the claims (atomicOr) issued, then the
+// winners' degrees read, so the K edges' memory round trips overlap instead of
+// forming one dependent chain per edge. The one thread whose atomicOr flips a
+// vertex's bit writes its depth, counts its out-degree and stages it.
+template <int K>
+__device__ __forceinline__ void visit_k(const DevGraph& g, const Level& lv, const Stage& s, const int32_t (&v)[K],
+                                        int nv, unsigned long long& edges) {
+  uint32_t word[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) word[k] = k < nv ? ld_volatile_u32(lv.vis + (v[k] >> 5)) : 0xffffffffu;
+  bool won[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t bit = 1u << (v[k] & 31);
+    won[k] = false;
+    if (k < nv && !(word[k] & bit)) won[k] = (atomicOr(lv.vis + (v[k] >> 5), bit) & bit) == 0u;
   }
+  int32_t d[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) d[k] = won[k] ? g.off[v[k] + 1] - g.off[v[k]] : 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (won[k]) {
+      lv.depth[v[k]] = lv.next_depth;
+      edges += (unsigned long long)d[k];
+      stage_push(s, lv, v[k]);
+    }
 }
 
 template <typename T>
@@ -272,60 +346,94 @@ __global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
 
 // ---------------------------------------------------------------------------
 // Push, one thread per frontier vertex (Section 3.1.2 vertex push, over an
-// explicit queue instead of a scan of all vertices)
+// explicit queue instead of a scan of all vertices). Each thread walks its
+// vertex's adjacency four edges at a time.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(b, st);
   unsigned long long edges = 0;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < lv.frontier; i += stride) {
-    const int32_t u = lv.qin[i];
-    const int32_t beg = g.off[u], end = g.off[u + 1];
-    for (int32_t e = beg; e < end; ++e) visit(g, lv, g.idx[e], edges);
+  for (int base = blockIdx.x * blockDim.x; base < lv.frontier; base += stride) {
+    const int i = base + threadIdx.x;
+    if (i < lv.frontier) {
+      const int32_t u = lv.qin[i];
+      const int32_t end = g.off[u + 1];
+      for (int32_t e = g.off[u]; e < end; e += 4) {
+        const int nv = min(4, end - e);
+        int32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = k < nv ? g.idx[e + k] : 0;
+        visit_k<4>(g, lv, stage, v, nv, edges);
+      }
+    }
+    stage_flush(stage, lv, kStageCap / 2);
   }
+  stage_flush(stage, lv, 1);
   block_add_u64(edges, &st->next_edges);
 }
 
 // ---------------------------------------------------------------------------
 // Push, virtual warp of W lanes per frontier vertex (Section 3.1.3, after Hong
-// et al. 2011). W = 32 reads the adjacency with 16-byte vector loads.
+// et al. 2011). Lanes stride the adjacency; W = 32 reads long lists with
+// 16-byte vector loads.
 // ---------------------------------------------------------------------------
 namespace {
 template <int W>
-__device__ __forceinline__ void push_vwarp(const DevGraph& g, const Level& lv, unsigned long long& edges) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = gt & (W - 1);
-  const int ngroups = (gridDim.x * blockDim.x) / W;
-  for (int i = gt / W; i < lv.frontier; i += ngroups) {
-    const int32_t u = lv.qin[i];
-    const int32_t beg = g.off[u], end = g.off[u + 1];
-    if (W == 32 && end - beg >= 256) {
-      const int32_t a0 = (beg + 3) & ~3, a1 = end & ~3;
-      if (beg + lane < a0) visit(g, lv, g.idx[beg + lane], edges);
-      for (int32_t e = a0 + 4 * lane; e < a1; e += 128) {
-        const int4 v4 = *reinterpret_cast<const int4*>(g.idx + e);
-        visit(g, lv, v4.x, edges);
-        visit(g, lv, v4.y, edges);
-        visit(g, lv, v4.z, edges);
-        visit(g, lv, v4.w, edges);
+__device__ __forceinline__ void push_vwarp(const DevGraph& g, const Level& lv, const Stage& stage,
+                                           unsigned long long& edges) {
+  constexpr int G = kThreads / W;  // groups per block
+  const int lane = threadIdx.x & (W - 1);
+  for (int base = blockIdx.x * G; base < lv.frontier; base += gridDim.x * G) {
+    const int i = base + (int)threadIdx.x / W;
+    if (i < lv.frontier) {
+      const int32_t u = lv.qin[i];
+      const int32_t beg = g.off[u], end = g.off[u + 1];
+      if (W == 32 && end - beg >= 256) {
+        const int32_t a0 = (beg + 3) & ~3, a1 = end & ~3;
+        {
+          int32_t v[1] = {beg + lane < a0 ? g.idx[beg + lane] : 0};
+          visit_k<1>(g, lv, stage, v, beg + lane < a0 ? 1 : 0, edges);
+        }
+        for (int32_t e = a0 + 4 * lane; e < a1; e += 128) {
+          const int4 q = *reinterpret_cast<const int4*>(g.idx + e);
+          int32_t v[4] = {q.x, q.y, q.z, q.w};
+          visit_k<4>(g, lv, stage, v, 4, edges);
+        }
+        {
+          int32_t v[1] = {a1 + lane < end ? g.idx[a1 + lane] : 0};
+          visit_k<1>(g, lv, stage, v, a1 + lane < end ? 1 : 0, edges);
+        }
+      } else {
+        for (int32_t e = beg + lane; e < end; e += 4 * W) {
+          int32_t v[4];
+          int nv = 0;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int32_t ek = e + k * W;
+            v[k] = ek < end ? g.idx[ek] : 0;
+            nv += ek < end ? 1 : 0;
+          }
+          visit_k<4>(g, lv, stage, v, nv, edges);
+        }
       }
-      if (a1 + lane < end) visit(g, lv, g.idx[a1 + lane], edges);
-    } else {
-      for (int32_t e = beg + lane; e < end; e += W) visit(g, lv, g.idx[e], edges);
     }
+    stage_flush(stage, lv, kStageCap / 2);
   }
 }
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads) k_push_warp(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(b, st);
   unsigned long long edges = 0;
   switch (st->vw) {
-    case 4: push_vwarp<4>(g, lv, edges); break;
-    case 8: push_vwarp<8>(g, lv, edges); break;
-    case 16: push_vwarp<16>(g, lv, edges); break;
-    default: push_vwarp<32>(g, lv, edges); break;
+    case 4: push_vwarp<4>(g, lv, stage, edges); break;
+    case 8: push_vwarp<8>(g, lv, stage, edges); break;
+    case 16: push_vwarp<16>(g, lv, stage, edges); break;
+    default: push_vwarp<32>(g, lv, stage, edges); break;
   }
+  stage_flush(stage, lv, 1);
   block_add_u64(edges, &st->next_edges);
 }
 
@@ -337,8 +445,9 @@ __global__ void __launch_bounds__(kThreads) k_push_warp(DevGraph g, Buffers b, R
 // multiples of 4 entries (idx is padded) and the extra entries are skipped.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, RunState* st) {
-  __shared__ alignas(128) int32_t stage[2][kCtaChunk];
+  __shared__ alignas(128) int32_t chunk[2][kCtaChunk];
   __shared__ alignas(8) uint64_t bar[2];
+  BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(b, st);
   unsigned long long edges = 0;
   const int tid = threadIdx.x;
@@ -348,13 +457,25 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
     mbar_fence_init();
   }
   __syncthreads();
-  uint32_t parity[2] = {0u, 0u};
+  uint32_t parity0 = 0u, parity1 = 0u;
   bool failed = false;
+  constexpr int kPer = kCtaChunk / kThreads;  // staged entries per thread per chunk
   for (int i = blockIdx.x; i < lv.frontier && !failed; i += gridDim.x) {
     const int32_t u = lv.qin[i];
     const int32_t beg = g.off[u], end = g.off[u + 1];
     if (end - beg < kCtaDirect) {
-      for (int32_t e = beg + tid; e < end; e += blockDim.x) visit(g, lv, g.idx[e], edges);
+      for (int32_t e = beg + tid; e < end; e += 4 * kThreads) {
+        int32_t v[4];
+        int nv = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int32_t ek = e + k * kThreads;
+          v[k] = ek < end ? g.idx[ek] : 0;
+          nv += ek < end ? 1 : 0;
+        }
+        visit_k<4>(g, lv, stage, v, nv, edges);
+      }
+      stage_flush(stage, lv, kStageCap / 2);
       continue;
     }
     const int32_t abeg = beg & ~3, aend = (end + 3) & ~3;
@@ -364,7 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
       const uint32_t bytes = (uint32_t)min(kCtaChunk, aend - cb) * 4u;
       uint64_t* br = &bar[c & 1];
       mbar_expect_tx(br, bytes);
-      bulk_g2s(stage[c & 1], g.idx + cb, bytes, br);
+      bulk_g2s(chunk[c & 1], g.idx + cb, bytes, br);
     };
     if (tid == 0) {
       issue(0);
@@ -372,21 +493,39 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
     }
     for (int32_t c = 0; c < nch; ++c) {
       const int s = c & 1;
-      const bool ok = mbar_wait_bounded(&bar[s], parity[s]);
-      parity[s] ^= 1u;
+      const bool ok = mbar_wait_bounded(&bar[s], s ? parity1 : parity0);
+      if (s)
+        parity1 ^= 1u;
+      else
+        parity0 ^= 1u;
       if (ok) {
         const int32_t cb = abeg + c * kCtaChunk;
         const int32_t len = min(kCtaChunk, aend - cb);
-        for (int32_t k = tid; k < len; k += blockDim.x) {
-          const int32_t e = cb + k;
-          if (e >= beg && e < end) visit(g, lv, stage[s][k], edges);
+        int32_t v[kPer];
+        int nv = 0;
+        // entries tid, tid + 256, ... of the chunk; compacted to the valid ones
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          const int32_t kk = tid + k * kThreads;
+          const int32_t e = cb + kk;
+          const bool in = kk < len && e >= beg && e < end;
+          v[k] = in ? chunk[s][kk] : 0;
         }
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+          const int32_t kk = tid + k * kThreads;
+          const int32_t e = cb + kk;
+          const bool in = kk < len && e >= beg && e < end;
+          if (in) v[nv++] = v[k];
+        }
+        visit_k<kPer>(g, lv, stage, v, nv, edges);
       }
+      stage_flush(stage, lv, kStageCap / 2);
       if (!__syncthreads_and(ok)) {
         // a copy never completed: flag it, let the other in-flight copy land (bounded) and stop
         if (tid == 0) {
           st->status = ST_TIMEOUT;
-          if (c + 1 < nch) mbar_wait_bounded(&bar[s ^ 1], parity[s ^ 1]);
+          if (c + 1 < nch) mbar_wait_bounded(&bar[s ^ 1], s ? parity0 : parity1);
         }
         failed = true;
         break;
@@ -394,6 +533,7 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
       if (tid == 0 && c + 2 < nch) issue(c + 2);
     }
   }
+  stage_flush(stage, lv, 1);
   block_add_u64(edges, &st->next_edges);
 }
 
@@ -490,6 +630,7 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
   __shared__ int32_t s_a[kPeTile + 1];
   __shared__ int32_t s_beg[kPeTile + 1];
   __shared__ int s_split[2];
+  BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(b, st);
   const int f = lv.frontier;
   const int32_t E = b.pe_scan[f];
@@ -519,16 +660,21 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
     int cur = ti;          // s index of the current vertex
     int anext = ti + 1;    // s index of the next boundary
     long long bj = j0 + (td0 - ti);
+    int32_t epos[kPeItems];
+    int ne = 0;
     for (int step = td0; step < td1; ++step) {
       if (anext <= na && (long long)s_a[anext] <= bj) {
         cur = anext++;
       } else {
-        const int32_t e = s_beg[cur] + (int32_t)(bj - s_a[cur]);
-        visit(g, lv, g.idx[e], edges);
+        epos[ne++] = s_beg[cur] + (int32_t)(bj - s_a[cur]);
         ++bj;
       }
     }
-    __syncthreads();
+    int32_t v[kPeItems];
+#pragma unroll
+    for (int k = 0; k < kPeItems; ++k) v[k] = k < ne ? g.idx[epos[k]] : 0;
+    visit_k<kPeItems>(g, lv, stage, v, ne, edges);
+    stage_flush(stage, lv, 1);
   }
   block_add_u64(edges, &st->next_edges);
 }
@@ -536,58 +682,62 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
 // ---------------------------------------------------------------------------
 // Pull, bottom-up over the visited bitmap (Section 3.1.2 vertex pull). A warp
 // owns 32 consecutive vertices (one bitmap word); each unvisited lane scans its
-// in-neighbours and stops at the first visited one. At the start of level L a
-// visited in-neighbour of an unvisited vertex has depth exactly L (a smaller
-// depth would already have reached the vertex), so the current bitmap is the
-// frontier test. New bits go to the other bitmap (read and write sets stay
-// apart); the found vertices are appended to the queue with one atomic per
-// warp (ballot + prefix popcount), which is also the bitmap-to-queue
-// conversion a following push level needs.
+// in-neighbours, four at a time, and stops at the first visited one. At the
+// start of level L a visited in-neighbour of an unvisited vertex has depth
+// exactly L (a smaller depth would already have reached the vertex), so the
+// current bitmap is the frontier test. New bits go to the other bitmap (read
+// and write sets stay apart); the found vertices are staged and appended to
+// the queue, which is also the bitmap-to-queue conversion a following push
+// level needs.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunState* st) {
-  const int32_t L1 = st->level + 1;
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
   const bool vs = st->vsel != 0u;
   const uint32_t* __restrict__ cur_vis = vs ? b.vis[1] : b.vis[0];
   uint32_t* nxt_vis = vs ? b.vis[0] : b.vis[1];
-  int32_t* qout = st->qsel ? b.q[0] : b.q[1];
-  int32_t* depth = st->depth;
-  unsigned int* tail = &st->next_count;
   const uint32_t lane = lane_id();
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  constexpr int kWarps = kThreads / 32;
+  const int wib = threadIdx.x >> 5;
   unsigned long long edges = 0;
-  for (int w = warp; w < g.words; w += nwarps) {
-    const uint32_t cw = cur_vis[w];
-    uint32_t fm = 0;
-    if (cw != kFull) {
-      const int32_t v = w * 32 + (int32_t)lane;
-      bool found = false;
-      int32_t deg = 0;
-      if (v < g.n && !((cw >> lane) & 1u)) {
-        const int32_t beg = g.in_off[v], end = g.in_off[v + 1];
-        for (int32_t e = beg; e < end; ++e) {
-          const int32_t u = g.in_idx[e];
-          if ((ld_nc_u32(cur_vis + (u >> 5)) >> (u & 31)) & 1u) {
-            found = true;
-            break;
+  for (int wbase = blockIdx.x * kWarps; wbase < g.words; wbase += gridDim.x * kWarps) {
+    const int w = wbase + wib;
+    if (w < g.words) {
+      const uint32_t cw = cur_vis[w];
+      uint32_t fm = 0;
+      if (cw != kFull) {
+        const int32_t v = w * 32 + (int32_t)lane;
+        bool found = false;
+        int32_t deg = 0;
+        if (v < g.n && !((cw >> lane) & 1u)) {
+          const int32_t beg = g.in_off[v], end = g.in_off[v + 1];
+          for (int32_t e = beg; e < end; e += 4) {
+            const int nv = min(4, end - e);
+            int32_t u[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[k] = g.in_idx[k < nv ? e + k : e];
+            uint32_t hit = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) hit |= (ld_nc_u32(cur_vis + (u[k] >> 5)) >> (u[k] & 31)) & 1u;
+            if (hit) {
+              found = true;
+              break;
+            }
           }
+          if (found) deg = g.symmetric ? end - beg : g.off[v + 1] - g.off[v];
         }
-        if (found) deg = g.symmetric ? end - beg : g.off[v + 1] - g.off[v];
-      }
-      fm = __ballot_sync(kFull, found);
-      if (fm) {
-        unsigned int base = 0;
-        if (lane == 0) base = atomicAdd(tail, (unsigned)__popc(fm));
-        base = __shfl_sync(kFull, base, 0);
+        fm = __ballot_sync(kFull, found);
         if (found) {
-          depth[v] = L1;
+          lv.depth[v] = lv.next_depth;
           edges += (unsigned long long)deg;
-          qout[base + __popc(fm & lanemask_lt())] = v;
+          stage_push(stage, lv, v);
         }
       }
+      if (lane == 0) nxt_vis[w] = cw | fm;
     }
-    if (lane == 0) nxt_vis[w] = cw | fm;
+    stage_flush(stage, lv, kStageCap - kThreads);
   }
+  stage_flush(stage, lv, 1);
   block_add_u64(edges, &st->next_edges);
 }
 
