@@ -460,10 +460,13 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
   uint32_t parity0 = 0u, parity1 = 0u;
   bool failed = false;
   constexpr int kPer = kCtaChunk / kThreads;  // staged entries per thread per chunk
-  for (int i = blockIdx.x; i < lv.frontier && !failed; i += gridDim.x) {
+  int iter = 0;
+  for (int i = blockIdx.x; i < lv.frontier && !failed; i += gridDim.x, ++iter) {
     const int32_t u = lv.qin[i];
     const int32_t beg = g.off[u], end = g.off[u + 1];
     if (end - beg < kCtaDirect) {
+      // short lists: read directly; check the stage every 4th vertex (4 x 512
+      // entries fit it), not after each one, to keep barriers rare
       for (int32_t e = beg + tid; e < end; e += 4 * kThreads) {
         int32_t v[4];
         int nv = 0;
@@ -475,9 +478,10 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
         }
         visit_k<4>(g, lv, stage, v, nv, edges);
       }
-      stage_flush(stage, lv, kStageCap / 2);
+      if ((iter & 3) == 3) stage_flush(stage, lv, kStageCap / 2);
       continue;
     }
+    stage_flush(stage, lv, 1);  // empty the stage before a long list
     const int32_t abeg = beg & ~3, aend = (end + 3) & ~3;
     const int32_t nch = (aend - abeg + kCtaChunk - 1) / kCtaChunk;
     auto issue = [&](int32_t c) {

@@ -1,0 +1,41 @@
+"""Small fixed BFS workload for profiler captures.
+
+Builds one R-MAT graph (default scale 22, edge factor 16, seed 1001: the
+benchmark's graph), then runs the switched traversal (or one forced variant)
+from a few giant-component roots. Small and deterministic, so a profiler can
+capture a handful of kernel launches of interest.
+
+  python -m paper_1708_01159_gb300.profile_case [--scale 22] [--roots 2] [--variant -1]
+"""
+import argparse
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--scale", type=int, default=22)
+    p.add_argument("--edge-factor", type=int, default=16)
+    p.add_argument("--seed", type=int, default=1001)
+    p.add_argument("--roots", type=int, default=2)
+    p.add_argument("--variant", type=int, default=-1)
+    a = p.parse_args()
+    import torch
+
+    import graphgen as gg
+    import paper_1708_01159_gb300 as bfs
+    bfs.build()
+    g = gg.rmat(a.scale, a.edge_factor, seed=a.seed)
+    roots = gg.sample_roots(g, a.roots, seed=gg.SEED_ROOTS + 1, giant=True)
+    with bfs.Graph(g.off, g.idx) as G:
+        depth = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for r in roots:
+            st = bfs.bfs_run_ex(G.handle, int(r), depth, forced_variant=a.variant, stats=True, log_capacity=64)
+            names = [bfs.VARIANTS[v] for v in st["variant"]]
+            print(f"root {int(r)}: levels {st['levels']} edges {st['edges_reached']} schedule {names}")
+
+
+if __name__ == "__main__":
+    main()

@@ -41,6 +41,18 @@ from paper_1708_01159_gb300 import FEATURES, NUM_FEATURES, NUM_VARIANTS, VARIANT
 
 LEVEL0_DEFAULT = 3  # Section 4.1: unknown at the first level -> edge list (edge-centric push)
 
+# Feature sets (indices into FEATURES):
+#   paper -- Section 4.2's best model: graph size, % of vertices discovered,
+#            out-degree distribution, vertices in the frontier
+#   m1    -- every feature Section 4.1 lists (frontier and discovered both
+#            absolute and as a share of the vertices)
+#   ext   -- m1 plus the frontier's edge count and the level index
+FEATURE_SETS = {
+    "paper": [0, 1, 2, 3, 4, 5, 6, 7, 8, 11],
+    "m1": list(range(12)),
+    "ext": list(range(14)),
+}
+
 # Training graphs: (name, generator kwargs). Seeds start at 3000; the
 # benchmark graph uses seed 1001 and is excluded by construction.
 TRAIN_GRAPHS = [
@@ -122,17 +134,29 @@ def split_by_graph(graph, test_frac=0.3, seed=0):
     return np.array([g not in test for g in graph]), sorted(test)
 
 
-def fit(X, T, feature_idx, max_depth=8, min_samples_leaf=8, weighting="regret"):
-    """CART with Gini impurity (Section 2.1). Labels: the fastest variant per
-    level. With weighting='regret' each level weighs its spread of times
-    (slowest minus fastest), so the tree spends its splits where a wrong choice
-    costs the most; 'uniform' is the paper's plain classification."""
+def level_weights(T, trav, weighting):
+    """Sample weights. 'uniform': the paper's plain classification. 'regret':
+    a level weighs its spread of times (slowest minus fastest), so splits go
+    where a wrong choice costs most. 'relregret': that spread divided by the
+    traversal's per-level-optimal time, the level's share of the traversal
+    slowdown that Table 2 averages."""
+    if weighting == "uniform":
+        return np.ones(len(T))
+    spread = T.max(axis=1) - T.min(axis=1) + 1e-5
+    if weighting == "regret":
+        return spread
+    opt = T.min(axis=1)
+    tot = {}
+    for k, t in zip(trav, opt):
+        tot[k] = tot.get(k, 0.0) + t
+    return spread / np.array([tot[k] for k in trav])
+
+
+def fit(X, T, feature_idx, max_depth=8, min_samples_leaf=8, weighting="regret", trav=None):
+    """CART with Gini impurity (Section 2.1); labels: the fastest variant per level."""
     from sklearn.tree import DecisionTreeClassifier
     y = T.argmin(axis=1)
-    if weighting == "regret":
-        w = T.max(axis=1) - T.min(axis=1) + 1e-4
-    else:
-        w = np.ones(len(y))
+    w = level_weights(T, trav if trav is not None else np.zeros(len(T)), weighting)
     clf = DecisionTreeClassifier(criterion="gini", max_depth=max_depth, min_samples_leaf=min_samples_leaf,
                                  random_state=0)
     clf.fit(X[:, feature_idx], y, sample_weight=w)
@@ -221,6 +245,36 @@ def evaluate(graph, root, level, X, T, nodes, mask=None):
     return summary
 
 
+def cross_validate(graph, root, level, X, T, folds=6, depths=(6, 8, 10)):
+    """Mean held-out slowdown vs the per-level optimum, k folds split by graph."""
+    import tempfile
+    names = sorted(set(graph.tolist()))
+    rng = np.random.default_rng(1)
+    rng.shuffle(names)
+    fold_of = {nm: i % folds for i, nm in enumerate(names)}
+    fold = np.array([fold_of[g] for g in graph])
+    trav = np.array([f"{g}/{r}" for g, r in zip(graph, root)])
+    for fs in sorted(FEATURE_SETS):
+        for wt in ("uniform", "regret", "relregret"):
+            for depth in depths:
+                slow, worst, best_fixed = [], 0.0, []
+                for k in range(folds):
+                    tr, te = fold != k, fold == k
+                    fidx = np.array(FEATURE_SETS[fs])
+                    clf = fit(X[tr], T[tr], fidx, depth, 8, wt, trav[tr])
+                    with tempfile.NamedTemporaryFile("w", suffix=".tree", delete=False) as fh:
+                        path = fh.name
+                    export(clf, fidx, path)
+                    s = evaluate(graph, root, level, X, T, read_tree(path), te)
+                    os.unlink(path)
+                    slow.append(s["predicted"]["average"] * s["traversals"])
+                    best_fixed.append(s["best_fixed"]["average"] * s["traversals"])
+                    worst = max(worst, s["predicted"]["worst"])
+                n = len(set(trav.tolist()))
+                print(f"features={fs:5s} weighting={wt:9s} depth={depth:2d}: held-out mean {sum(slow) / n:.3f}x "
+                      f"worst {worst:.2f}x (best fixed {sum(best_fixed) / n:.3f}x)", flush=True)
+
+
 def print_table(summary, file=sys.stdout):
     print(f"traversals: {summary['traversals']}, per-level accuracy: {summary['level_accuracy']:.3f}", file=file)
     print(f"{'algorithm':14s} {'optimal':>8s} {'1-2x':>7s} {'>5x':>6s} {'>20x':>6s} {'average':>8s} {'worst':>8s}",
@@ -241,11 +295,14 @@ def main():
     t = sub.add_parser("train")
     t.add_argument("--csv", required=True)
     t.add_argument("--out", required=True)
-    t.add_argument("--features", default="paper", choices=["paper", "all"])
+    t.add_argument("--features", default="ext", choices=sorted(FEATURE_SETS))
     t.add_argument("--max-depth", type=int, default=8)
     t.add_argument("--min-leaf", type=int, default=8)
-    t.add_argument("--weighting", default="regret", choices=["regret", "uniform"])
+    t.add_argument("--weighting", default="relregret", choices=["regret", "uniform", "relregret"])
     t.add_argument("--all-graphs", action="store_true", help="train on every graph (no held-out split)")
+    v = sub.add_parser("cv", help="k-fold cross-validation by graph over feature sets and weightings")
+    v.add_argument("--csv", required=True)
+    v.add_argument("--folds", type=int, default=6)
     e = sub.add_parser("evaluate")
     e.add_argument("--csv", required=True)
     e.add_argument("--tree", required=True)
@@ -255,13 +312,12 @@ def main():
         return
     graph, root, level, X, T = load(a.csv)
     if a.cmd == "train":
-        # Section 4.2's best set: graph size, % discovered, out-degree distribution, frontier vertex count
-        paper = [0, 1, 2, 3, 4, 5, 6, 7, 8, 11]
-        fidx = np.array(paper if a.features == "paper" else list(range(NUM_FEATURES)))
+        fidx = np.array(FEATURE_SETS[a.features])
         train_mask, test_graphs = split_by_graph(graph)
         if a.all_graphs:
             train_mask = np.ones(len(graph), bool)
-        clf = fit(X[train_mask], T[train_mask], fidx, a.max_depth, a.min_leaf, a.weighting)
+        trav = np.array([f"{g}/{r}" for g, r in zip(graph, root)])
+        clf = fit(X[train_mask], T[train_mask], fidx, a.max_depth, a.min_leaf, a.weighting, trav[train_mask])
         meta = (f"features={a.features} max_depth={a.max_depth} min_samples_leaf={a.min_leaf} "
                 f"weighting={a.weighting}\nlevels={int(train_mask.sum())} "
                 f"held-out graphs={'none' if a.all_graphs else ','.join(test_graphs)}")
@@ -272,6 +328,8 @@ def main():
         if not a.all_graphs:
             print("held-out graphs:", ", ".join(test_graphs))
             print_table(evaluate(graph, root, level, X, T, nodes, ~train_mask))
+    elif a.cmd == "cv":
+        cross_validate(graph, root, level, X, T, a.folds)
     else:
         print_table(evaluate(graph, root, level, X, T, read_tree(a.tree)))
 
