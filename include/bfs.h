@@ -87,10 +87,19 @@ typedef struct bfs_graph_info {
   int32_t num_workspaces;    /* per-run workspaces currently allocated */
 } bfs_graph_info_t;
 
+/* How the level loop is driven (all run the same level code and give the same depths). */
+enum bfs_mode {
+  BFS_MODE_DEFAULT = 0,    /* persistent when the device supports cooperative launch, else graph */
+  BFS_MODE_PERSISTENT = 1, /* one cooperative kernel for the whole traversal; levels separated by a grid barrier */
+  BFS_MODE_GRAPH = 2,      /* one CUDA graph: WHILE node over levels, SWITCH node over variant kernels */
+  BFS_MODE_HOST_LOOP = 3,  /* the graph's kernels launched level by level from the host (for profilers) */
+};
+
 typedef struct bfs_options {
   int32_t forced_variant;    /* BFS_VARIANT_TREE or a fixed bfs_variant for every level */
   int32_t depth_on_host;     /* 1: depth_out is host memory; the library copies the result there */
-  int32_t reserved[6];       /* must be zero */
+  int32_t mode;              /* enum bfs_mode */
+  int32_t reserved[5];       /* must be zero */
 } bfs_options;
 
 typedef struct bfs_run_stats {

@@ -39,6 +39,12 @@ BFS_SYMMETRIC = 1
 BFS_INPUT_ON_DEVICE = 2
 BFS_VALIDATE = 4
 
+MODE_DEFAULT = 0
+MODE_PERSISTENT = 1
+MODE_GRAPH = 2
+MODE_HOST_LOOP = 3
+MODES = {"default": MODE_DEFAULT, "persistent": MODE_PERSISTENT, "graph": MODE_GRAPH, "host_loop": MODE_HOST_LOOP}
+
 VARIANT_TREE = -1
 VARIANTS = ("push_thread", "push_warp", "push_cta", "push_edge", "pull")
 NUM_VARIANTS = len(VARIANTS)
@@ -60,8 +66,8 @@ class _GraphInfo(ctypes.Structure):
 
 
 class _Options(ctypes.Structure):
-    _fields_ = [("forced_variant", ctypes.c_int32), ("depth_on_host", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("forced_variant", ctypes.c_int32), ("depth_on_host", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class _Stats(ctypes.Structure):
@@ -206,11 +212,12 @@ def bfs_run(g: int, root: int, depth_out, stream=None) -> None:
 
 
 def bfs_run_ex(g: int, root: int, depth_out, stream=None, forced_variant: int = VARIANT_TREE,
-               depth_on_host: Optional[bool] = None, stats: bool = False, log_capacity: int = 0):
+               depth_on_host: Optional[bool] = None, stats: bool = False, log_capacity: int = 0,
+               mode: int = MODE_DEFAULT):
     """BFS with options. Returns a stats dict when stats=True (then the stream is synchronised)."""
     p, dev, _ = _ptr(depth_out, what="depth_out")
     host = (not dev) if depth_on_host is None else bool(depth_on_host)
-    opts = _Options(forced_variant=int(forced_variant), depth_on_host=int(host))
+    opts = _Options(forced_variant=int(forced_variant), depth_on_host=int(host), mode=int(mode))
     st = None
     logs = None
     if stats:

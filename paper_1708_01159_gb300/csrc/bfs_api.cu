@@ -175,6 +175,7 @@ constexpr int kMaxWorkspaces = 64;
 
 struct Shapes {
   int init, push_thread, push_warp, push_cta, pe, pull;
+  int persist;  // cooperative grid of the persistent kernel (0: not supported)
 };
 
 }  // namespace
@@ -454,7 +455,9 @@ int sync_tree(bfs_graph* g) {
   return BFS_OK;
 }
 
-int launch_run(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
+int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s);
+
+int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
   alignas(16) unsigned char storage[1024];
   void* argp[9];
   cudaKernelNodeParams ip;
@@ -462,6 +465,51 @@ int launch_run(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_
   CU(cudaGraphExecKernelNodeSetParams(ws->exec, ws->init_node, &ip));
   CU(cudaGraphLaunch(ws->exec, stream));
   return BFS_OK;
+}
+
+// One cooperative launch runs the whole traversal (k_bfs_persistent).
+int launch_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced,
+                      cudaStream_t stream) {
+  k_persist_reset<<<1, 1, 0, stream>>>(ws->st);
+  CU(cudaGetLastError());
+  DevGraph dg = g->dg;
+  Buffers b = ws->b;
+  RunState* st = ws->st;
+  const TreeNode* tree = g->tree;
+  int32_t nodes = g->tree_nodes;
+  void* args[] = {&dg, &b, &st, &depth, &root, &forced, &tree, &nodes};
+  CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_bfs_persistent), dim3(g->shapes.persist),
+                                 dim3(kThreads), args, 0, stream));
+  return BFS_OK;
+}
+
+// The graph's kernels launched level by level from the host, reading each
+// level's decision back (synchronous). Profilers can see every kernel here.
+int launch_host_loop(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t s) {
+  k_init<<<g->shapes.init, kThreads, 0, s>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes, 0);
+  CU(cudaGetLastError());
+  RunState hs{};
+  for (;;) {
+    k_decide<<<1, 32, 0, s>>>(g->dg, ws->b, ws->st);
+    CU(cudaMemcpyAsync(&hs, ws->st, sizeof hs, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (hs.frontier == 0 || hs.status != ST_OK) break;
+    TRY(launch_variant(g, ws, hs.variant, s));
+  }
+  return BFS_OK;
+}
+
+int launch_run(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, int32_t mode,
+               cudaStream_t stream) {
+  if (mode == BFS_MODE_DEFAULT) mode = g->shapes.persist > 0 ? BFS_MODE_PERSISTENT : BFS_MODE_GRAPH;
+  switch (mode) {
+    case BFS_MODE_PERSISTENT:
+      if (g->shapes.persist <= 0) return fail(BFS_ERR_INVALID_ARG, "device lacks cooperative launch");
+      return launch_persistent(g, ws, root, depth, forced, stream);
+    case BFS_MODE_GRAPH: return launch_graph(g, ws, root, depth, forced, stream);
+    case BFS_MODE_HOST_LOOP: return launch_host_loop(g, ws, root, depth, forced, stream);
+    default: return fail(BFS_ERR_INVALID_ARG, "mode %d", mode);
+  }
 }
 
 // Launch the kernels of one variant for the current level directly on a
@@ -665,6 +713,15 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
   s.push_cta = grid_for(reinterpret_cast<const void*>(&k_push_cta), g->sms, 8);
   s.pe = grid_for(reinterpret_cast<const void*>(&k_pe_expand), g->sms, 8);
   s.pull = grid_for(reinterpret_cast<const void*>(&k_pull), g->sms, 8);
+  // the persistent kernel needs every block resident: one full occupancy wave
+  int coop = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
+  if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(&k_bfs_persistent),
+                                                            kThreads, 0) == cudaSuccess && per_sm > 0)
+    s.persist = g->sms * std::min(per_sm, 8);
+  else
+    s.persist = 0;
+  cudaGetLastError();
   *out = g.release();
   return BFS_OK;
 }
@@ -721,14 +778,17 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (!depth_out) return fail(BFS_ERR_INVALID_ARG, "depth_out is null");
   if (root < 0 || root >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root %d not in [0, %d)", root, g->dg.n);
-  int32_t forced = -1;
+  int32_t forced = -1, mode = BFS_MODE_DEFAULT;
   bool host_out = false;
   if (opts) {
     if (opts->forced_variant < -1 || opts->forced_variant >= V_NUM)
       return fail(BFS_ERR_INVALID_ARG, "forced_variant %d out of range", opts->forced_variant);
-    for (int k = 0; k < 6; ++k)
+    if (opts->mode < BFS_MODE_DEFAULT || opts->mode > BFS_MODE_HOST_LOOP)
+      return fail(BFS_ERR_INVALID_ARG, "mode %d out of range", opts->mode);
+    for (int k = 0; k < 5; ++k)
       if (opts->reserved[k]) return fail(BFS_ERR_INVALID_ARG, "reserved option fields must be zero");
     forced = opts->forced_variant;
+    mode = opts->mode;
     host_out = opts->depth_on_host != 0;
   }
   DeviceGuard dgd(g->device);
@@ -736,7 +796,7 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   Workspace* ws = nullptr;
   TRY(acquire(g, stream, &ws));
   int32_t* dst = host_out ? ws->host_depth_stage : depth_out;
-  int r = launch_run(g, ws, root, dst, forced, stream);
+  int r = launch_run(g, ws, root, dst, forced, mode, stream);
   RunState hs{};
   if (r == BFS_OK && host_out) {
     cudaError_t e = cudaMemcpyAsync(depth_out, dst, (size_t)g->dg.n * 4, cudaMemcpyDeviceToHost, stream);

@@ -86,6 +86,13 @@ struct RunState {
   unsigned long long h_while;   // cudaGraphConditionalHandle of the level loop
   unsigned long long h_switch;  // cudaGraphConditionalHandle of the variant switch
   long long feat[F_NUM];     // feature vector of the current level (written by decide)
+  // persistent driver: level counters indexed by level % 3 (level L reads slot
+  // L % 3, appends to (L + 1) % 3 and clears (L + 2) % 3) and the grid barrier
+  unsigned int cnt3[3];
+  unsigned int bar_count;
+  unsigned long long edg3[3];
+  unsigned int bar_gen;
+  int32_t pad2_;
   int32_t log_cap;
   int32_t pad_;
   int32_t* log_variant;

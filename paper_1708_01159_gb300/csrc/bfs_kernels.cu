@@ -1,10 +1,15 @@
 // Level kernels of the per-level switched BFS (sm_103a).
 //
-// Every kernel reads the level's parameters (level L, frontier size, queue and
-// bitmap selectors) from the device RunState, so the same launch shapes serve
-// every level and the level loop can run inside one CUDA graph with no host
-// round trip. Grids are fixed (a multiple of the SM count) and every kernel
-// strides over its work.
+// Each variant's level is a device function ("body") written with
+// block-uniform loops, so three drivers can share it:
+//   - graph path: one thin kernel per body, launched by a CUDA graph whose
+//     WHILE node runs the level loop and whose SWITCH node picks the variant
+//     set on the device by k_decide;
+//   - persistent path: k_bfs_persistent, one cooperative launch per traversal;
+//     levels are separated by a grid barrier and every block evaluates the
+//     decision tree itself from counters indexed by level % 3;
+//   - host loop: the graph path's kernels launched from the host level by
+//     level (for profilers and the per-level timing harness).
 //
 // Newly reached vertices are claimed by an atomicOr on the visited bitmap; the
 // single thread that flips a bit writes depth L + 1, stages the vertex in a
@@ -13,8 +18,6 @@
 // Section 3.1.4's first variant, a global atomic counter, with warp and block
 // aggregation in front of it), and adds the vertex's out-degree to the next
 // level's frontier-edge count.
-#include <cooperative_groups.h>
-
 #include "bfs_kernels.cuh"
 
 namespace bfs {
@@ -74,12 +77,57 @@ __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
-// ---- per-edge visit --------------------------------------------------------
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+  return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// Grid-wide barrier for the persistent driver (cooperative launch, so every
+// block is resident). Arrival counter plus generation word; waiting is bounded
+// by kWaitLimitNs, after which the status word is set and false returned.
+__device__ bool grid_sync(RunState* st) {
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    const unsigned int gen = ld_acquire_u32(&st->bar_gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&st->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      st->bar_count = 0;
+      __threadfence();
+      st_release_u32(&st->bar_gen, gen + 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(&st->bar_gen) == gen) {
+        if (*reinterpret_cast<volatile int32_t*>(&st->status) != ST_OK || global_ns() - t0 > kWaitLimitNs) {
+          st->status = ST_TIMEOUT;
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// ---- output staging and per-edge visit --------------------------------------
 
 struct Level {
   const int32_t* __restrict__ qin;
   int32_t* qout;
-  uint32_t* vis;
+  uint32_t* vis;       // current visited bitmap (push updates it in place; pull reads it)
+  uint32_t* vis_next;  // the other bitmap (pull writes it)
   int32_t* depth;
   unsigned int* tail;
   int32_t next_depth;
@@ -90,9 +138,11 @@ __device__ __forceinline__ Level load_level(const Buffers& b, RunState* st) {
   Level lv;
   // select with ternaries: indexing the by-value parameter arrays would copy them to local memory
   const bool qs = st->qsel != 0u;
+  const bool vs = st->vsel != 0u;
   lv.qin = qs ? b.q[1] : b.q[0];
   lv.qout = qs ? b.q[0] : b.q[1];
-  lv.vis = st->vsel ? b.vis[1] : b.vis[0];
+  lv.vis = vs ? b.vis[1] : b.vis[0];
+  lv.vis_next = vs ? b.vis[0] : b.vis[1];
   lv.depth = st->depth;
   lv.tail = &st->next_count;
   lv.next_depth = st->level + 1;
@@ -146,10 +196,6 @@ __device__ __forceinline__ void stage_flush(const Stage& s, const Level& lv, uns
   __syncthreads();
   if (threadIdx.x == 0) *s.cnt = 0;
   __syncthreads();
-}
-
-__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
-  return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
 // Top-down visit of up to K edges u -> v[k] (Section 3.1.2 push). The bitmap
@@ -212,14 +258,10 @@ __device__ T block_exclusive_scan(T x, T* total) {
   return base + inc - x;
 }
 
-}  // namespace
-
 // ---------------------------------------------------------------------------
-// Init (Section 3.1: all depths infinity, the root 0)
+// Init (Section 3.1: all depths infinity, the root 0): depth and bitmap fill
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root,
-                                                   int32_t forced, const TreeNode* tree, int32_t tree_nodes,
-                                                   int32_t use_handles) {
+__device__ __forceinline__ void init_fill(const DevGraph& g, uint32_t* vis0, int32_t* depth, int32_t root) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int32_t n = g.n;
@@ -241,86 +283,32 @@ __global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunSta
   } else {
     for (int64_t i = tid; i < n; i += stride) depth[i] = (i == root) ? 0 : -1;
   }
-  uint32_t* vis0 = b.vis[0];
   for (int64_t w = tid; w < g.words; w += stride) vis0[w] = (w == (root >> 5)) ? (1u << (root & 31)) : 0u;
-  if (tid == 0) {
-    st->depth = depth;
-    st->tree = tree;
-    st->tree_nodes = tree_nodes;
-    st->root = root;
-    st->forced = forced;
-    st->use_handles = use_handles;
-    st->level = -1;
-    st->variant = -1;
-    st->qsel = 0;
-    st->vsel = 0;
-    st->frontier = 0;
-    st->status = ST_OK;
-    st->vw = 32;
-    st->levels = 0;
-    st->done_blocks = 0;
-    st->frontier_edges = 0;
-    st->discovered = 0;
-    st->edges_reached = 0;
-    // the root is the output of "level -1": the first decide turns it into the frontier of level 0
-    b.q[1][0] = root;
-    st->next_count = 1;
-    st->next_edges = (unsigned long long)(g.off[root + 1] - g.off[root]);
-  }
 }
 
 // ---------------------------------------------------------------------------
-// Level end + tree evaluation (Section 2.1 walk, Section 4.1 features and
-// unknown-prediction rule). One thread; runs between levels on the device.
+// Tree evaluation (Section 2.1 walk over the Section 4.1 features, with the
+// Section 4.1 unknown-prediction rule). Returns the variant; fills feat[].
 // ---------------------------------------------------------------------------
-__global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  (void)b;
-  RunState& s = *st;
-  // close level L-1: its output queue becomes the frontier of level L
-  const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&s.next_count);
-  const unsigned long long e = *reinterpret_cast<volatile unsigned long long*>(&s.next_edges);
-  s.next_count = 0;
-  s.next_edges = 0;
-  if (s.level >= 0 && s.variant == V_PULL) s.vsel ^= 1u;  // pull wrote the other bitmap
-  s.qsel ^= 1u;
-  const int32_t L = s.level + 1;
-  s.level = L;
-  s.frontier = (int32_t)f;
-  s.frontier_edges = (long long)e;
-  s.discovered += f;
-  s.edges_reached += (long long)e;
-  // a traversal has at most n nonempty levels; more means corrupted state, so
-  // end the loop with an error instead of iterating on
-  if (L > g.n || s.discovered > g.n) s.status = ST_TIMEOUT;
-  if (f == 0 || s.status != ST_OK) {
-    s.levels = L;
-    if (s.use_handles) {
-      cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_while, 0u);
-      cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)V_NUM);
-    }
-    return;
-  }
-  long long x[F_NUM];
+__device__ int32_t decide_variant(const DevGraph& g, const TreeNode* tree, int32_t nodes, int32_t forced, int32_t L,
+                                  long long f, long long e, long long discovered, int32_t prev, long long* x,
+                                  int32_t* vw) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) x[i] = g.gfeat[i];
   const long long n = g.n;
   x[F_FRONTIER] = f;
-  x[F_FRONTIER_PPM] = (1000000ll * (long long)f) / n;
-  x[F_DISCOVERED] = s.discovered;
-  x[F_DISCOVERED_PPM] = (1000000ll * s.discovered) / n;
-  x[F_FRONTIER_EDGES] = (long long)e;
+  x[F_FRONTIER_PPM] = (1000000ll * f) / n;
+  x[F_DISCOVERED] = discovered;
+  x[F_DISCOVERED_PPM] = (1000000ll * discovered) / n;
+  x[F_FRONTIER_EDGES] = e;
   x[F_LEVEL] = L;
-#pragma unroll
-  for (int i = 0; i < F_NUM; ++i) s.feat[i] = x[i];
-  int32_t v = s.forced;
+  int32_t v = forced;
   if (v < 0) {
     v = -1;
-    const TreeNode* t = s.tree;
-    if (t != nullptr && s.tree_nodes > 0) {
+    if (tree != nullptr && nodes > 0) {
       int32_t i = 0;
-      for (int32_t step = 0; step <= s.tree_nodes; ++step) {
-        const TreeNode nd = t[i];
+      for (int32_t step = 0; step <= nodes; ++step) {
+        const TreeNode nd = tree[i];
         if (nd.f < 0) {
           v = nd.v;
           break;
@@ -328,20 +316,14 @@ __global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
         i = (x[nd.f] <= nd.t) ? nd.l : nd.r;
       }
     }
-    if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : s.variant;  // unknown prediction
+    if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : prev;  // unknown prediction
     if (v < 0 || v >= V_NUM) v = kLevel0Default;
   }
-  s.variant = v;
-  // virtual-warp width for this level: the power of two nearest above the
-  // frontier's mean degree, clamped to [4, 32]
-  const long long avg = (long long)e / (long long)f;
-  s.vw = avg <= 4 ? 4 : avg <= 8 ? 8 : avg <= 16 ? 16 : 32;
-  if (L < s.log_cap) {
-    s.log_variant[L] = v;
-    s.log_frontier[L] = f;
-    s.log_edges[L] = (long long)e;
-  }
-  if (s.use_handles) cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)v);
+  // virtual-warp width: the power of two nearest above the frontier's mean
+  // degree, clamped to [4, 32]
+  const long long avg = f > 0 ? e / f : 0;
+  *vw = avg <= 4 ? 4 : avg <= 8 ? 8 : avg <= 16 ? 16 : 32;
+  return v;
 }
 
 // ---------------------------------------------------------------------------
@@ -349,10 +331,7 @@ __global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
 // explicit queue instead of a scan of all vertices). Each thread walks its
 // vertex's adjacency four edges at a time.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b, RunState* st) {
-  BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
-  unsigned long long edges = 0;
+__device__ void body_push_thread(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < lv.frontier; base += stride) {
     const int i = base + threadIdx.x;
@@ -369,8 +348,6 @@ __global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b,
     }
     stage_flush(stage, lv, kStageCap / 2);
   }
-  stage_flush(stage, lv, 1);
-  block_add_u64(edges, &st->next_edges);
 }
 
 // ---------------------------------------------------------------------------
@@ -378,7 +355,6 @@ __global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b,
 // et al. 2011). Lanes stride the adjacency; W = 32 reads long lists with
 // 16-byte vector loads.
 // ---------------------------------------------------------------------------
-namespace {
 template <int W>
 __device__ __forceinline__ void push_vwarp(const DevGraph& g, const Level& lv, const Stage& stage,
                                            unsigned long long& edges) {
@@ -421,20 +397,15 @@ __device__ __forceinline__ void push_vwarp(const DevGraph& g, const Level& lv, c
     stage_flush(stage, lv, kStageCap / 2);
   }
 }
-}  // namespace
 
-__global__ void __launch_bounds__(kThreads) k_push_warp(DevGraph g, Buffers b, RunState* st) {
-  BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
-  unsigned long long edges = 0;
-  switch (st->vw) {
+__device__ void body_push_warp(const DevGraph& g, const Level& lv, const Stage& stage, int32_t vw,
+                               unsigned long long& edges) {
+  switch (vw) {
     case 4: push_vwarp<4>(g, lv, stage, edges); break;
     case 8: push_vwarp<8>(g, lv, stage, edges); break;
     case 16: push_vwarp<16>(g, lv, stage, edges); break;
     default: push_vwarp<32>(g, lv, stage, edges); break;
   }
-  stage_flush(stage, lv, 1);
-  block_add_u64(edges, &st->next_edges);
 }
 
 // ---------------------------------------------------------------------------
@@ -444,24 +415,28 @@ __global__ void __launch_bounds__(kThreads) k_push_warp(DevGraph g, Buffers b, R
 // staged neighbours. Copies are 16-byte aligned: the range is widened to
 // multiples of 4 entries (idx is padded) and the extra entries are skipped.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, RunState* st) {
-  __shared__ alignas(128) int32_t chunk[2][kCtaChunk];
-  __shared__ alignas(8) uint64_t bar[2];
-  BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
-  unsigned long long edges = 0;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
+struct CtaPipe {
+  int32_t* chunk;  // 2 x kCtaChunk entries of shared memory
+  uint64_t* bar;   // 2 mbarriers, initialised once per block
+  uint32_t parity0, parity1;
+};
+
+__device__ __forceinline__ void cta_pipe_init(uint64_t* bar) {
+  if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  uint32_t parity0 = 0u, parity1 = 0u;
-  bool failed = false;
+}
+
+// Returns false if a copy never completed (status set; block stopped early).
+__device__ bool body_push_cta(const DevGraph& g, const Level& lv, const Stage& stage, CtaPipe& pp, int32_t* status,
+                              unsigned long long& edges) {
+  const int tid = threadIdx.x;
   constexpr int kPer = kCtaChunk / kThreads;  // staged entries per thread per chunk
   int iter = 0;
-  for (int i = blockIdx.x; i < lv.frontier && !failed; i += gridDim.x, ++iter) {
+  for (int i = blockIdx.x; i < lv.frontier; i += gridDim.x, ++iter) {
     const int32_t u = lv.qin[i];
     const int32_t beg = g.off[u], end = g.off[u + 1];
     if (end - beg < kCtaDirect) {
@@ -487,9 +462,9 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
     auto issue = [&](int32_t c) {
       const int32_t cb = abeg + c * kCtaChunk;
       const uint32_t bytes = (uint32_t)min(kCtaChunk, aend - cb) * 4u;
-      uint64_t* br = &bar[c & 1];
+      uint64_t* br = &pp.bar[c & 1];
       mbar_expect_tx(br, bytes);
-      bulk_g2s(chunk[c & 1], g.idx + cb, bytes, br);
+      bulk_g2s(pp.chunk + (c & 1) * kCtaChunk, g.idx + cb, bytes, br);
     };
     if (tid == 0) {
       issue(0);
@@ -497,30 +472,23 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
     }
     for (int32_t c = 0; c < nch; ++c) {
       const int s = c & 1;
-      const bool ok = mbar_wait_bounded(&bar[s], s ? parity1 : parity0);
+      const bool ok = mbar_wait_bounded(&pp.bar[s], s ? pp.parity1 : pp.parity0);
       if (s)
-        parity1 ^= 1u;
+        pp.parity1 ^= 1u;
       else
-        parity0 ^= 1u;
+        pp.parity0 ^= 1u;
       if (ok) {
         const int32_t cb = abeg + c * kCtaChunk;
         const int32_t len = min(kCtaChunk, aend - cb);
+        const int32_t* buf = pp.chunk + s * kCtaChunk;
         int32_t v[kPer];
         int nv = 0;
-        // entries tid, tid + 256, ... of the chunk; compacted to the valid ones
+        // entries tid, tid + 256, ... of the chunk, compacted to the valid ones
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
           const int32_t kk = tid + k * kThreads;
           const int32_t e = cb + kk;
-          const bool in = kk < len && e >= beg && e < end;
-          v[k] = in ? chunk[s][kk] : 0;
-        }
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-          const int32_t kk = tid + k * kThreads;
-          const int32_t e = cb + kk;
-          const bool in = kk < len && e >= beg && e < end;
-          if (in) v[nv++] = v[k];
+          if (kk < len && e >= beg && e < end) v[nv++] = buf[kk];
         }
         visit_k<kPer>(g, lv, stage, v, nv, edges);
       }
@@ -528,17 +496,15 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
       if (!__syncthreads_and(ok)) {
         // a copy never completed: flag it, let the other in-flight copy land (bounded) and stop
         if (tid == 0) {
-          st->status = ST_TIMEOUT;
-          if (c + 1 < nch) mbar_wait_bounded(&bar[s ^ 1], s ? parity0 : parity1);
+          *status = ST_TIMEOUT;
+          if (c + 1 < nch) mbar_wait_bounded(&pp.bar[s ^ 1], s ? pp.parity0 : pp.parity1);
         }
-        failed = true;
-        break;
+        return false;
       }
       if (tid == 0 && c + 2 < nch) issue(c + 2);
     }
   }
-  stage_flush(stage, lv, 1);
-  block_add_u64(edges, &st->next_edges);
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -547,8 +513,7 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
 // (merge path of the scan with the edge indices) gives every thread
 // kPeItems items (frontier boundaries or edges) regardless of degree skew.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_pe_reduce(DevGraph g, Buffers b, RunState* st) {
-  const Level lv = load_level(b, st);
+__device__ void body_pe_reduce(const DevGraph& g, const Level& lv, const Buffers& b) {
   const int f = lv.frontier;
   const int nblk = (f + kPeTile - 1) / kPeTile;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
@@ -572,9 +537,8 @@ __global__ void __launch_bounds__(kThreads) k_pe_reduce(DevGraph g, Buffers b, R
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_pe_top(DevGraph g, Buffers b, RunState* st) {
-  (void)g;
-  const int f = st->frontier;
+// One block.
+__device__ void body_pe_top(const Buffers& b, int f) {
   const int nblk = (f + kPeTile - 1) / kPeTile;
   long long carry = 0;
   for (int base = 0; base < nblk; base += blockDim.x) {
@@ -588,9 +552,7 @@ __global__ void __launch_bounds__(kThreads) k_pe_top(DevGraph g, Buffers b, RunS
   if (threadIdx.x == 0) b.pe_bsum[nblk] = carry;
 }
 
-__global__ void __launch_bounds__(kThreads) k_pe_scan(DevGraph g, Buffers b, RunState* st) {
-  (void)g;
-  const int f = st->frontier;
+__device__ void body_pe_scan(const Buffers& b, int f) {
   const int nblk = (f + kPeTile - 1) / kPeTile;
   for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
     const int base = blk * kPeTile + threadIdx.x * kPeItems;
@@ -614,7 +576,6 @@ __global__ void __launch_bounds__(kThreads) k_pe_scan(DevGraph g, Buffers b, Run
   }
 }
 
-namespace {
 // Merge-path split: how many of the first d items of merge(A[0..na), j0+[0..nb))
 // are A items, with A first on ties (A[i] <= edge index => boundary first).
 __device__ __forceinline__ int merge_split(const int32_t* a, int na, long long j0, int nb, long long d) {
@@ -628,19 +589,14 @@ __device__ __forceinline__ int merge_split(const int32_t* a, int na, long long j
   }
   return lo;
 }
-}  // namespace
 
-__global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, RunState* st) {
-  __shared__ int32_t s_a[kPeTile + 1];
-  __shared__ int32_t s_beg[kPeTile + 1];
-  __shared__ int s_split[2];
-  BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+// s_a, s_beg: kPeTile + 1 entries of shared memory each; s_split: 2 ints.
+__device__ void body_pe_expand(const DevGraph& g, const Level& lv, const Buffers& b, const Stage& stage, int32_t* s_a,
+                               int32_t* s_beg, int* s_split, unsigned long long& edges) {
   const int f = lv.frontier;
   const int32_t E = b.pe_scan[f];
   const long long total = (long long)f + E;
   const long long ntiles = (total + kPeTile - 1) / kPeTile;
-  unsigned long long edges = 0;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const long long d0 = t * kPeTile;
     const long long d1 = min(d0 + kPeTile, total);
@@ -680,7 +636,6 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
     visit_k<kPeItems>(g, lv, stage, v, ne, edges);
     stage_flush(stage, lv, 1);
   }
-  block_add_u64(edges, &st->next_edges);
 }
 
 // ---------------------------------------------------------------------------
@@ -694,16 +649,12 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
 // the queue, which is also the bitmap-to-queue conversion a following push
 // level needs.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunState* st) {
-  BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
-  const bool vs = st->vsel != 0u;
-  const uint32_t* __restrict__ cur_vis = vs ? b.vis[1] : b.vis[0];
-  uint32_t* nxt_vis = vs ? b.vis[0] : b.vis[1];
+__device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
+  const uint32_t* __restrict__ cur_vis = lv.vis;
+  uint32_t* nxt_vis = lv.vis_next;
   const uint32_t lane = lane_id();
   constexpr int kWarps = kThreads / 32;
   const int wib = threadIdx.x >> 5;
-  unsigned long long edges = 0;
   for (int wbase = blockIdx.x * kWarps; wbase < g.words; wbase += gridDim.x * kWarps) {
     const int w = wbase + wib;
     if (w < g.words) {
@@ -741,8 +692,252 @@ __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunSta
     }
     stage_flush(stage, lv, kStageCap - kThreads);
   }
+}
+
+}  // namespace
+
+// ===========================================================================
+// Graph path: init, decide, and one kernel per body
+// ===========================================================================
+__global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root,
+                                                   int32_t forced, const TreeNode* tree, int32_t tree_nodes,
+                                                   int32_t use_handles) {
+  init_fill(g, b.vis[0], depth, root);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->depth = depth;
+    st->tree = tree;
+    st->tree_nodes = tree_nodes;
+    st->root = root;
+    st->forced = forced;
+    st->use_handles = use_handles;
+    st->level = -1;
+    st->variant = -1;
+    st->qsel = 0;
+    st->vsel = 0;
+    st->frontier = 0;
+    st->status = ST_OK;
+    st->vw = 32;
+    st->levels = 0;
+    st->done_blocks = 0;
+    st->frontier_edges = 0;
+    st->discovered = 0;
+    st->edges_reached = 0;
+    // the root is the output of "level -1": the first decide turns it into the frontier of level 0
+    b.q[1][0] = root;
+    st->next_count = 1;
+    st->next_edges = (unsigned long long)(g.off[root + 1] - g.off[root]);
+  }
+}
+
+// Level end + tree evaluation, between levels on the device (one thread).
+__global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  (void)b;
+  RunState& s = *st;
+  // close level L-1: its output queue becomes the frontier of level L
+  const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&s.next_count);
+  const unsigned long long e = *reinterpret_cast<volatile unsigned long long*>(&s.next_edges);
+  s.next_count = 0;
+  s.next_edges = 0;
+  if (s.level >= 0 && s.variant == V_PULL) s.vsel ^= 1u;  // pull wrote the other bitmap
+  s.qsel ^= 1u;
+  const int32_t L = s.level + 1;
+  s.level = L;
+  s.frontier = (int32_t)f;
+  s.frontier_edges = (long long)e;
+  s.discovered += f;
+  s.edges_reached += (long long)e;
+  // a traversal has at most n nonempty levels; more means corrupted state, so
+  // end the loop with an error instead of iterating on
+  if (L > g.n || s.discovered > g.n) s.status = ST_TIMEOUT;
+  if (f == 0 || s.status != ST_OK) {
+    s.levels = L;
+    if (s.use_handles) {
+      cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_while, 0u);
+      cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)V_NUM);
+    }
+    return;
+  }
+  long long x[F_NUM];
+  int32_t vw = 32;
+  const int32_t v = decide_variant(g, s.tree, s.tree_nodes, s.forced, L, f, (long long)e, s.discovered, s.variant, x,
+                                   &vw);
+#pragma unroll
+  for (int i = 0; i < F_NUM; ++i) s.feat[i] = x[i];
+  s.variant = v;
+  s.vw = vw;
+  if (L < s.log_cap) {
+    s.log_variant[L] = v;
+    s.log_frontier[L] = f;
+    s.log_edges[L] = (long long)e;
+  }
+  if (s.use_handles) cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)v);
+}
+
+__global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  body_push_thread(g, lv, stage, edges);
   stage_flush(stage, lv, 1);
   block_add_u64(edges, &st->next_edges);
+}
+
+__global__ void __launch_bounds__(kThreads) k_push_warp(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  body_push_warp(g, lv, stage, st->vw, edges);
+  stage_flush(stage, lv, 1);
+  block_add_u64(edges, &st->next_edges);
+}
+
+__global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, RunState* st) {
+  __shared__ alignas(128) int32_t chunk[2 * kCtaChunk];
+  __shared__ alignas(8) uint64_t bar[2];
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  cta_pipe_init(bar);
+  CtaPipe pp{chunk, bar, 0u, 0u};
+  unsigned long long edges = 0;
+  body_push_cta(g, lv, stage, pp, &st->status, edges);
+  stage_flush(stage, lv, 1);
+  block_add_u64(edges, &st->next_edges);
+}
+
+__global__ void __launch_bounds__(kThreads) k_pe_reduce(DevGraph g, Buffers b, RunState* st) {
+  body_pe_reduce(g, load_level(b, st), b);
+}
+
+__global__ void __launch_bounds__(kThreads) k_pe_top(DevGraph g, Buffers b, RunState* st) {
+  (void)g;
+  body_pe_top(b, st->frontier);
+}
+
+__global__ void __launch_bounds__(kThreads) k_pe_scan(DevGraph g, Buffers b, RunState* st) {
+  (void)g;
+  body_pe_scan(b, st->frontier);
+}
+
+__global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, RunState* st) {
+  __shared__ int32_t s_a[kPeTile + 1];
+  __shared__ int32_t s_beg[kPeTile + 1];
+  __shared__ int s_split[2];
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  body_pe_expand(g, lv, b, stage, s_a, s_beg, s_split, edges);
+  block_add_u64(edges, &st->next_edges);
+}
+
+__global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  body_pull(g, lv, stage, edges);
+  stage_flush(stage, lv, 1);
+  block_add_u64(edges, &st->next_edges);
+}
+
+// ===========================================================================
+// Persistent path: the whole traversal in one cooperative launch
+// ===========================================================================
+// Clears the words the persistent kernel's blocks read before block 0 could
+// reset them (a previous run may have stopped with an error).
+__global__ void k_persist_reset(RunState* st) {
+  st->status = ST_OK;
+  st->bar_count = 0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth,
+                                                             int32_t root, int32_t forced, const TreeNode* tree,
+                                                             int32_t tree_nodes) {
+  // one shared buffer serves the CTA variant's copy stage or the edge-centric tile
+  constexpr int kPeSlot = kPeTile + 32;
+  static_assert(2 * kCtaChunk <= 2 * kPeSlot, "union sizing");
+  __shared__ alignas(128) int32_t ubuf[2 * kPeSlot];
+  __shared__ alignas(8) uint64_t bar[2];
+  __shared__ int s_split[2];
+  BFS_DECLARE_STAGE(stage);
+  init_fill(g, b.vis[0], depth, root);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->depth = depth;
+    st->root = root;
+    st->forced = forced;
+    st->status = ST_OK;
+    st->cnt3[0] = 1;
+    st->cnt3[1] = 0;
+    st->cnt3[2] = 0;
+    st->edg3[0] = (unsigned long long)(g.off[root + 1] - g.off[root]);
+    st->edg3[1] = 0;
+    st->edg3[2] = 0;
+    b.q[0][0] = root;
+  }
+  cta_pipe_init(bar);
+  CtaPipe pp{ubuf, bar, 0u, 0u};
+  int32_t L = 0;
+  long long discovered = 0, reached = 0;
+  int32_t prev = -1;
+  uint32_t vsel = 0;
+  bool ok = grid_sync(st);
+  for (; ok; ++L) {
+    const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&st->cnt3[L % 3]);
+    const unsigned long long e = *reinterpret_cast<volatile unsigned long long*>(&st->edg3[L % 3]);
+    discovered += f;
+    reached += (long long)e;
+    if (f == 0) break;
+    if (L > g.n || discovered > g.n) {  // corrupted state: stop with an error
+      if (blockIdx.x == 0 && threadIdx.x == 0) st->status = ST_TIMEOUT;
+      break;
+    }
+    long long x[F_NUM];
+    int32_t vw = 32;
+    const int32_t v = decide_variant(g, tree, tree_nodes, forced, L, f, (long long)e, discovered, prev, x, &vw);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->cnt3[(L + 2) % 3] = 0;  // last read by level L - 1, which every block has finished
+      st->edg3[(L + 2) % 3] = 0;
+      if (L < st->log_cap) {
+        st->log_variant[L] = v;
+        st->log_frontier[L] = f;
+        st->log_edges[L] = (long long)e;
+      }
+    }
+    Level lv;
+    lv.qin = (L & 1) ? b.q[1] : b.q[0];
+    lv.qout = (L & 1) ? b.q[0] : b.q[1];
+    lv.vis = vsel ? b.vis[1] : b.vis[0];
+    lv.vis_next = vsel ? b.vis[0] : b.vis[1];
+    lv.depth = depth;
+    lv.tail = &st->cnt3[(L + 1) % 3];
+    lv.next_depth = L + 1;
+    lv.frontier = (int32_t)f;
+    unsigned long long edges = 0;
+    switch (v) {
+      case V_PUSH_THREAD: body_push_thread(g, lv, stage, edges); break;
+      case V_PUSH_WARP: body_push_warp(g, lv, stage, vw, edges); break;
+      case V_PUSH_CTA: body_push_cta(g, lv, stage, pp, &st->status, edges); break;
+      case V_PUSH_EDGE:
+        body_pe_reduce(g, lv, b);
+        if (!grid_sync(st)) break;
+        if (blockIdx.x == 0) body_pe_top(b, (int)f);
+        if (!grid_sync(st)) break;
+        body_pe_scan(b, (int)f);
+        if (!grid_sync(st)) break;
+        body_pe_expand(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
+        break;
+      default: body_pull(g, lv, stage, edges); break;
+    }
+    stage_flush(stage, lv, 1);
+    block_add_u64(edges, &st->edg3[(L + 1) % 3]);
+    if (v == V_PULL) vsel ^= 1u;
+    prev = v;
+    ok = grid_sync(st);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->levels = L;
+    st->discovered = discovered;
+    st->edges_reached = reached;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -28,15 +28,15 @@ def make(g, flags=bfs.BFS_SYMMETRIC):
     return bfs.Graph(g.off, g.idx, flags)
 
 
-def run(G, root, variant=bfs.VARIANT_TREE, log=64):
+def run(G, root, variant=bfs.VARIANT_TREE, log=64, mode=bfs.MODE_DEFAULT):
     d = torch.empty(G.n, dtype=torch.int32, device="cuda")
-    st = bfs.bfs_run_ex(G.handle, int(root), d, forced_variant=variant, stats=True, log_capacity=log)
+    st = bfs.bfs_run_ex(G.handle, int(root), d, forced_variant=variant, stats=True, log_capacity=log, mode=mode)
     return d.cpu().numpy(), st
 
 
-def assert_parity(g, G, root, variant=bfs.VARIANT_TREE):
+def assert_parity(g, G, root, variant=bfs.VARIANT_TREE, mode=bfs.MODE_DEFAULT):
     ref = oracle.bfs(g.off, g.idx, int(root))
-    dep, st = run(G, root, variant, log=max(ref.num_levels + 1, 1))
+    dep, st = run(G, root, variant, log=max(ref.num_levels + 1, 1), mode=mode)
     assert np.array_equal(dep, ref.depth), f"root {root} variant {variant}: depth mismatch " \
         f"({int((dep != ref.depth).sum())} entries)"
     assert st["edges_reached"] == ref.edges_reached
@@ -72,6 +72,20 @@ def test_each_variant(which, variant):
     with make(g) as G:
         for r in gg.sample_roots(g, 3, seed=5):
             assert_parity(g, G, r, variant)
+
+
+@pytest.mark.parametrize("mode", [bfs.MODE_PERSISTENT, bfs.MODE_GRAPH, bfs.MODE_HOST_LOOP])
+@pytest.mark.parametrize("variant", [bfs.VARIANT_TREE] + list(range(V)))
+def test_execution_modes_agree(mode, variant):
+    """The persistent kernel, the CUDA graph and the host loop run the same level
+    code: identical depths, counts, and (under the tree) identical schedules."""
+    for g in (gg.rmat(13, 16, seed=81), gg.grid(45, 61, 0.1, seed=82)):
+        with make(g) as G:
+            for r in gg.sample_roots(g, 2, seed=11):
+                ref, st = assert_parity(g, G, r, variant, mode)
+                if variant == bfs.VARIANT_TREE and mode != bfs.MODE_PERSISTENT:
+                    _, st2 = run(G, r, variant, log=ref.num_levels + 1, mode=bfs.MODE_PERSISTENT)
+                    assert st2["variant"].tolist() == st["variant"].tolist()
 
 
 @pytest.mark.parametrize("name", sorted(cf.ALL))
