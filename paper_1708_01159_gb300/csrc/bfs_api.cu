@@ -867,14 +867,11 @@ int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advanc
   TRY(sync_tree(g));
   Workspace* ws = nullptr;
   TRY(acquire(g, s, &ws));
-  const size_t n = (size_t)g->dg.n, words = (size_t)g->dg.words;
-  int32_t *depth = nullptr, *snap_depth = nullptr;
-  uint32_t* snap_vis = nullptr;
+  const size_t n = (size_t)g->dg.n;
+  int32_t* depth = nullptr;
   RunState* snap_st = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int r = dmalloc(reinterpret_cast<void**>(&depth), n * 4);
-  if (r == BFS_OK) r = dmalloc(reinterpret_cast<void**>(&snap_depth), n * 4);
-  if (r == BFS_OK) r = dmalloc(reinterpret_cast<void**>(&snap_vis), words * 4);
   if (r == BFS_OK) r = dmalloc(reinterpret_cast<void**>(&snap_st), sizeof(RunState));
   if (r == BFS_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
     r = fail(BFS_ERR_CUDA, "cudaEventCreate");
@@ -889,32 +886,26 @@ int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advanc
       CU(cudaMemcpyAsync(&hs, ws->st, sizeof hs, cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
       if (hs.frontier == 0 || hs.status != ST_OK) break;
-      uint32_t* vis = hs.vsel ? ws->b.vis[1] : ws->b.vis[0];
       if (L < capacity) {
         bfs_level_profile& P = out[L];
         for (int k = 0; k < F_NUM; ++k) P.features[k] = hs.feat[k];
         P.tree_variant = hs.variant;
         P.pad = 0;
-        CU(cudaMemcpyAsync(snap_depth, depth, n * 4, cudaMemcpyDeviceToDevice, s));
-        CU(cudaMemcpyAsync(snap_vis, vis, words * 4, cudaMemcpyDeviceToDevice, s));
         CU(cudaMemcpyAsync(snap_st, ws->st, sizeof(RunState), cudaMemcpyDeviceToDevice, s));
         for (int v = 0; v < V_NUM; ++v) {
           for (int k = 0; k < reps; ++k) {
-            CU(cudaMemcpyAsync(depth, snap_depth, n * 4, cudaMemcpyDeviceToDevice, s));
-            CU(cudaMemcpyAsync(vis, snap_vis, words * 4, cudaMemcpyDeviceToDevice, s));
-            CU(cudaMemcpyAsync(ws->st, snap_st, sizeof(RunState), cudaMemcpyDeviceToDevice, s));
             CU(cudaEventRecord(ev[0], s));
             TRY(launch_variant(g, ws, v, s));
             CU(cudaEventRecord(ev[1], s));
+            // undo the level (its discoveries are the output queue) and restore the counters
+            k_undo_level<<<g->shapes.init, kThreads, 0, s>>>(ws->b, ws->st);
+            CU(cudaMemcpyAsync(ws->st, snap_st, sizeof(RunState), cudaMemcpyDeviceToDevice, s));
             CU(cudaEventSynchronize(ev[1]));
             CU(cudaEventElapsedTime(&t[k], ev[0], ev[1]));
           }
           std::sort(t.begin(), t.end());
           P.ms[v] = t[reps / 2];
         }
-        CU(cudaMemcpyAsync(depth, snap_depth, n * 4, cudaMemcpyDeviceToDevice, s));
-        CU(cudaMemcpyAsync(vis, snap_vis, words * 4, cudaMemcpyDeviceToDevice, s));
-        CU(cudaMemcpyAsync(ws->st, snap_st, sizeof(RunState), cudaMemcpyDeviceToDevice, s));
       }
       // advance to the next level (the resulting state does not depend on the variant)
       int32_t adv = advance_variant >= 0 ? advance_variant : hs.variant;
@@ -930,7 +921,7 @@ int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advanc
   cudaStreamSynchronize(s);
   for (cudaEvent_t e : ev)
     if (e) cudaEventDestroy(e);
-  for (void* p : {(void*)depth, (void*)snap_depth, (void*)snap_vis, (void*)snap_st})
+  for (void* p : {(void*)depth, (void*)snap_st})
     if (p) cudaFree(p);
   int rr = release(g, ws, s);
   return r != BFS_OK ? r : rr;

@@ -123,8 +123,11 @@ __device__ bool grid_sync(RunState* st) {
 
 // ---- output staging and per-edge visit --------------------------------------
 
+// No __restrict__ on the queue or bitmaps: inside the persistent kernel they are
+// rewritten every level, so they must not be read through the non-coherent
+// read-only cache.
 struct Level {
-  const int32_t* __restrict__ qin;
+  const int32_t* qin;
   int32_t* qout;
   uint32_t* vis;       // current visited bitmap (push updates it in place; pull reads it)
   uint32_t* vis_next;  // the other bitmap (pull writes it)
@@ -647,10 +650,13 @@ __device__ void body_pe_expand(const DevGraph& g, const Level& lv, const Buffers
 // current bitmap is the frontier test. New bits go to the other bitmap (read
 // and write sets stay apart); the found vertices are staged and appended to
 // the queue, which is also the bitmap-to-queue conversion a following push
-// level needs.
+// level needs. kReadOnlyCache: the bitmap is read through the non-coherent
+// read-only cache, valid only when no earlier level ran in the same launch
+// (graph and host-loop drivers); the persistent kernel passes false.
 // ---------------------------------------------------------------------------
+template <bool kReadOnlyCache>
 __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
-  const uint32_t* __restrict__ cur_vis = lv.vis;
+  const uint32_t* cur_vis = lv.vis;
   uint32_t* nxt_vis = lv.vis_next;
   const uint32_t lane = lane_id();
   constexpr int kWarps = kThreads / 32;
@@ -673,7 +679,10 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
             for (int k = 0; k < 4; ++k) u[k] = g.in_idx[k < nv ? e + k : e];
             uint32_t hit = 0;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) hit |= (ld_nc_u32(cur_vis + (u[k] >> 5)) >> (u[k] & 31)) & 1u;
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t word = kReadOnlyCache ? ld_nc_u32(cur_vis + (u[k] >> 5)) : cur_vis[u[k] >> 5];
+              hit |= (word >> (u[k] & 31)) & 1u;
+            }
             if (hit) {
               found = true;
               break;
@@ -834,7 +843,7 @@ __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunSta
   BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(b, st);
   unsigned long long edges = 0;
-  body_pull(g, lv, stage, edges);
+  body_pull<true>(g, lv, stage, edges);
   stage_flush(stage, lv, 1);
   block_add_u64(edges, &st->next_edges);
 }
@@ -844,6 +853,24 @@ __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunSta
 // ===========================================================================
 // Clears the words the persistent kernel's blocks read before block 0 could
 // reset them (a previous run may have stopped with an error).
+// Timing harness: undo one level run from the graph path's state. The vertices
+// the level discovered are exactly the entries it appended to the output
+// queue, so resetting their depth and visited bit restores the state it
+// started from, in time proportional to the level's output (pull wrote only
+// the other bitmap, which is rewritten whole before it is read again).
+__global__ void k_undo_level(Buffers b, RunState* st) {
+  const unsigned int count = st->next_count;
+  const int32_t* qout = st->qsel ? b.q[0] : b.q[1];
+  uint32_t* vis = st->vsel ? b.vis[1] : b.vis[0];
+  int32_t* depth = st->depth;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)count; i += stride) {
+    const int32_t v = qout[i];
+    depth[v] = -1;
+    atomicAnd(&vis[v >> 5], ~(1u << (v & 31)));
+  }
+}
+
 __global__ void k_persist_reset(RunState* st) {
   st->status = ST_OK;
   st->bar_count = 0;
@@ -925,7 +952,7 @@ __global__ void __launch_bounds__(kThreads) k_bfs_persistent(DevGraph g, Buffers
         if (!grid_sync(st)) break;
         body_pe_expand(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
         break;
-      default: body_pull(g, lv, stage, edges); break;
+      default: body_pull<false>(g, lv, stage, edges); break;
     }
     stage_flush(stage, lv, 1);
     block_add_u64(edges, &st->edg3[(L + 1) % 3]);

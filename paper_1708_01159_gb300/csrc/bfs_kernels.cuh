@@ -23,6 +23,7 @@ __global__ void k_pe_scan(DevGraph g, Buffers b, RunState* st);
 __global__ void k_pe_expand(DevGraph g, Buffers b, RunState* st);
 __global__ void k_pull(DevGraph g, Buffers b, RunState* st);
 __global__ void k_persist_reset(RunState* st);
+__global__ void k_undo_level(Buffers b, RunState* st);
 __global__ void k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root, int32_t forced,
                                  const TreeNode* tree, int32_t tree_nodes);
 

@@ -74,6 +74,12 @@ TRAIN_GRAPHS = [
     ("er", dict(n=1 << 21, avg_degree=8.0, seed=3016)),
     ("er", dict(n=1 << 22, avg_degree=16.0, seed=3017)),
     ("er", dict(n=1 << 18, avg_degree=32.0, seed=3018)),
+    # the workloads' own sizes, other seeds: 16.8M-vertex grids, 2^23 ER, scale 23 R-MAT
+    ("grid", dict(rows=4096, cols=4096, drop=0.1, seed=3019)),
+    ("grid", dict(rows=3000, cols=3000, drop=0.15, seed=3020)),
+    ("er", dict(n=1 << 23, avg_degree=8.0, seed=3021)),
+    ("rmat", dict(scale=23, edge_factor=16, seed=3022)),
+    ("rmat", dict(scale=17, edge_factor=16, seed=3023, permute=True)),
 ]
 
 
@@ -89,7 +95,7 @@ def make_graph(kind, kw):
     raise ValueError(kind)
 
 
-def collect(out: str, roots_per_graph: int = 4, reps: int = 3, max_levels: int = 4096, graphs=None):
+def collect(out: str, roots_per_graph: int = 4, reps: int = 3, max_levels: int = 16384, graphs=None):
     import graphgen as gg
     import torch
     import paper_1708_01159_gb300 as bfs
