@@ -179,14 +179,38 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
 
 /*
  * Multi-source BFS: k independent traversals of one graph (the result equals k
- * single-source runs). roots: host, k int32. depth_out: device, k * n int32,
- * row-major (row i for roots[i]), caller-owned. Roots are processed in waves
- * of up to 64, one bit per root in a 64-bit visited / frontier mask per vertex.
+ * single-source runs, each the level-synchronous BFS of Section 3.1). roots:
+ * host, k int32 (repeats allowed). depth_out: device, k * n int32, row-major
+ * (row i for roots[i]), caller-owned. Roots are processed in waves of up to 64
+ * by one persistent kernel per wave, one bit per root in 64-bit visited /
+ * frontier masks per vertex (8 n bytes each, allocated on the first call and
+ * kept with the graph); each level pushes or pulls for all roots at once.
+ * Batches on one graph are ordered after each other on the device.
  * edges_out: optional host array of k int64 reached-edge counts; when given,
  * the call synchronises `stream`. Errors as bfs_run.
  */
 int bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_out, bfs_stream_t stream,
                   int64_t* edges_out);
+
+/* Launch shape of the multi-source kernel (chosen by bfs_batch_tune). */
+typedef struct bfs_batch_config {
+  int32_t push_mode;  /* 0: one thread per frontier vertex, 1: one warp per frontier vertex */
+  int32_t alpha;      /* a level pulls when its frontier's edge count x alpha exceeds m */
+  float ms;           /* bfs_batch_tune: measured time of one wave with this configuration */
+  int32_t reserved;
+} bfs_batch_config;
+
+/* Set the graph's multi-source configuration. Errors: BFS_ERR_INVALID_ARG. */
+int bfs_batch_set_config(bfs_graph_t g, const bfs_batch_config* cfg);
+
+/*
+ * Autotuner: time one wave of the given roots (host, 1..64) with every
+ * candidate configuration (push mode x alpha in {2, 4, ..., 64}; CUDA events on
+ * `stream`, one warm-up run each), keep the fastest for the graph and return
+ * it in *best. depth_scratch: device, k * n int32, overwritten. Synchronous.
+ */
+int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_scratch, bfs_stream_t stream,
+                   bfs_batch_config* best);
 
 /*
  * Single-source BFS that allocates nothing. The paper has no counterpart: this

@@ -77,6 +77,11 @@ class _Stats(ctypes.Structure):
                 ("log_frontier_edges", ctypes.POINTER(ctypes.c_int64))]
 
 
+class _BatchConfig(ctypes.Structure):
+    _fields_ = [("push_mode", ctypes.c_int32), ("alpha", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
 class _LevelProfile(ctypes.Structure):
     _fields_ = [("features", ctypes.c_int64 * NUM_FEATURES), ("ms", ctypes.c_float * NUM_VARIANTS),
                 ("tree_variant", ctypes.c_int32), ("pad", ctypes.c_int32)]
@@ -118,6 +123,8 @@ def lib():
                                                   ctypes.POINTER(c_i32)]),
             "bfs_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int]),
             "bfs_run_static": (ctypes.c_int, [vp, vp, c_i64, c_i64, c_i32, vp, vp]),
+            "bfs_batch_set_config": (ctypes.c_int, [vp, ctypes.POINTER(_BatchConfig)]),
+            "bfs_batch_tune": (ctypes.c_int, [vp, vp, c_i32, vp, vp, ctypes.POINTER(_BatchConfig)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -253,6 +260,22 @@ def bfs_run_batch(g: int, roots, depth_out, stream=None, edges: bool = False):
     _check(lib().bfs_run_batch(g, r.ctypes.data, r.size, p, _stream(stream),
                                e.ctypes.data if e is not None else None), "bfs_run_batch")
     return e[: r.size] if e is not None else None
+
+
+def bfs_batch_set_config(g: int, push_mode: int, alpha: int) -> None:
+    c = _BatchConfig(push_mode=push_mode, alpha=alpha)
+    _check(lib().bfs_batch_set_config(g, ctypes.byref(c)), "bfs_batch_set_config")
+
+
+def bfs_batch_tune(g: int, roots, depth_scratch, stream=None) -> dict:
+    """Autotune the multi-source kernel on up to 64 roots; returns the chosen configuration."""
+    r = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
+    p, dev, _ = _ptr(depth_scratch, what="depth_scratch")
+    if not dev:
+        raise ValueError("depth_scratch must be device memory")
+    c = _BatchConfig()
+    _check(lib().bfs_batch_tune(g, r.ctypes.data, r.size, p, _stream(stream), ctypes.byref(c)), "bfs_batch_tune")
+    return {"push_mode": c.push_mode, "alpha": c.alpha, "ms": c.ms}
 
 
 def bfs_profile_levels(g: int, root: int, reps: int = 5, advance_variant: int = VARIANT_TREE, stream=None,

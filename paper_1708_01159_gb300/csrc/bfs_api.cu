@@ -16,6 +16,7 @@
 
 #include "bfs.h"
 #include "bfs_kernels.cuh"
+#include "bfs_msbfs.cuh"
 
 using namespace bfs;
 
@@ -197,6 +198,15 @@ struct bfs_graph {
   TreeNode* tree = nullptr;
   int32_t tree_nodes = 0;
   uint64_t tree_version = 0;
+  // multi-source buffers (allocated on the first batch; batches on one graph
+  // are ordered through ms_done)
+  MsBuffers ms{};
+  MsState* ms_state = nullptr;
+  int32_t* ms_roots = nullptr;
+  cudaEvent_t ms_done = nullptr;
+  std::mutex ms_mu;
+  MsConfig ms_cfg{0, 16};
+  int ms_grid = 0;
 };
 
 namespace {
@@ -539,6 +549,66 @@ int check_graph(bfs_graph_t g) {
   return BFS_OK;
 }
 
+// Multi-source buffers: four masks of n x 8 bytes, the wave's roots and state.
+// Called with g->ms_mu held.
+int ms_prepare(bfs_graph* g) {
+  if (g->ms_state) return BFS_OK;
+  const size_t n = (size_t)g->dg.n;
+  void* p[7] = {};
+  int r = BFS_OK;
+  const size_t sizes[7] = {n * 8, n * 8, n * 8, n * 8, 64 * 4, sizeof(MsState), 0};
+  for (int i = 0; i < 6 && r == BFS_OK; ++i) r = dmalloc(&p[i], sizes[i]);
+  if (r == BFS_OK && cudaEventCreateWithFlags(&g->ms_done, cudaEventDisableTiming) != cudaSuccess)
+    r = fail(BFS_ERR_CUDA, "cudaEventCreate");
+  if (r == BFS_OK) {
+    MsState init{};
+    if (cudaMemcpy(p[5], &init, sizeof init, cudaMemcpyHostToDevice) != cudaSuccess)
+      r = fail(BFS_ERR_CUDA, "batch state init");
+  }
+  int per_sm = 0;
+  if (r == BFS_OK) {
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
+    if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(&k_msbfs),
+                                                               kMsThreads, 0) != cudaSuccess || per_sm < 1)
+      r = fail(BFS_ERR_CUDA, "multi-source BFS needs cooperative launch");
+  }
+  if (r != BFS_OK) {
+    for (void* q : p)
+      if (q) cudaFree(q);
+    if (g->ms_done) cudaEventDestroy(g->ms_done);
+    g->ms_done = nullptr;
+    return r;
+  }
+  for (int i = 0; i < 6; ++i) {
+    g->allocs.push_back(p[i]);
+    g->bytes += sizes[i];
+  }
+  g->ms.visit = static_cast<unsigned long long*>(p[0]);
+  g->ms.front[0] = static_cast<unsigned long long*>(p[1]);
+  g->ms.front[1] = static_cast<unsigned long long*>(p[2]);
+  g->ms.next = static_cast<unsigned long long*>(p[3]);
+  g->ms_roots = static_cast<int32_t*>(p[4]);
+  g->ms.roots = g->ms_roots;
+  g->ms_state = static_cast<MsState*>(p[5]);
+  g->ms_grid = g->sms * std::min(per_sm, 8);
+  return BFS_OK;
+}
+
+// One wave of up to 64 roots (host array) into k rows of depth_out.
+int ms_launch_wave(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t s, MsConfig cfg) {
+  CU(cudaMemcpyAsync(g->ms_roots, roots, (size_t)k * 4, cudaMemcpyHostToDevice, s));
+  k_ms_reset<<<1, 1, 0, s>>>(g->ms_state);
+  CU(cudaGetLastError());
+  DevGraph dg = g->dg;
+  MsBuffers mb = g->ms;
+  MsState* st = g->ms_state;
+  void* args[] = {&dg, &mb, &st, &k, &depth_out, &cfg};
+  CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_msbfs), dim3(g->ms_grid), dim3(kMsThreads), args, 0,
+                                 s));
+  return BFS_OK;
+}
+
 }  // namespace
 
 int bfs::set_error_detail(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -732,6 +802,7 @@ int bfs_graph_destroy(bfs_graph_t g) {
   cudaError_t e = cudaDeviceSynchronize();
   for (Workspace* ws : g->pool) free_workspace(ws);
   for (TreeNode* t : g->trees) cudaFree(t);
+  if (g->ms_done) cudaEventDestroy(g->ms_done);
   for (void* p : g->allocs) cudaFree(p);
   delete g;
   if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "destroy: %s", cudaGetErrorString(e));
@@ -847,11 +918,83 @@ int bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth
   for (int32_t i = 0; i < k; ++i)
     if (roots[i] < 0 || roots[i] >= g->dg.n)
       return fail(BFS_ERR_INVALID_ARG, "roots[%d] = %d not in [0, %d)", i, roots[i], g->dg.n);
-  for (int32_t i = 0; i < k; ++i) {
-    bfs_run_stats st{};
-    TRY(bfs_run_ex(g, roots[i], depth_out + (size_t)i * g->dg.n, stream, nullptr, edges_out ? &st : nullptr));
-    if (edges_out) edges_out[i] = st.edges_reached;
+  DeviceGuard dgd(g->device);
+  std::lock_guard<std::mutex> lk(g->ms_mu);
+  TRY(ms_prepare(g));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CU(cudaStreamWaitEvent(s, g->ms_done, 0));
+  const int64_t n = g->dg.n;
+  for (int32_t w0 = 0; w0 < k; w0 += 64) {
+    const int32_t kw = std::min<int32_t>(64, k - w0);
+    TRY(ms_launch_wave(g, roots + w0, kw, depth_out + (size_t)w0 * n, s, g->ms_cfg));
+    if (edges_out) {
+      unsigned long long e[64];
+      CU(cudaMemcpyAsync(e, g->ms_state->edges, sizeof e, cudaMemcpyDeviceToHost, s));
+      int32_t status = 0;
+      CU(cudaMemcpyAsync(&status, &g->ms_state->status, 4, cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (status != ST_OK) return fail(BFS_ERR_TIMEOUT, "a bounded device-side wait gave up");
+      for (int32_t i = 0; i < kw; ++i) edges_out[w0 + i] = (int64_t)e[i];
+    }
   }
+  CU(cudaEventRecord(g->ms_done, s));
+  return BFS_OK;
+}
+
+int bfs_batch_set_config(bfs_graph_t g, const bfs_batch_config* cfg) {
+  TRY(check_graph(g));
+  if (!cfg || cfg->push_mode < 0 || cfg->push_mode > 1 || cfg->alpha < 1)
+    return fail(BFS_ERR_INVALID_ARG, "batch config out of range");
+  std::lock_guard<std::mutex> lk(g->ms_mu);
+  g->ms_cfg = MsConfig{cfg->push_mode, cfg->alpha};
+  return BFS_OK;
+}
+
+int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_scratch, bfs_stream_t stream,
+                   bfs_batch_config* best) {
+  TRY(check_graph(g));
+  if (k < 1 || k > 64 || !roots || !depth_scratch || !best)
+    return fail(BFS_ERR_INVALID_ARG, "tune takes 1..64 roots, a k*n scratch buffer and an output");
+  for (int32_t i = 0; i < k; ++i)
+    if (roots[i] < 0 || roots[i] >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root out of range");
+  DeviceGuard dgd(g->device);
+  std::lock_guard<std::mutex> lk(g->ms_mu);
+  TRY(ms_prepare(g));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  CU(cudaStreamWaitEvent(s, g->ms_done, 0));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  const int alphas[] = {2, 4, 8, 16, 32, 64};
+  float best_ms = 1e30f;
+  MsConfig best_cfg = g->ms_cfg;
+  int r = BFS_OK;
+  for (int pm = 0; pm < 2 && r == BFS_OK; ++pm)
+    for (int a : alphas) {
+      const MsConfig c{pm, a};
+      r = ms_launch_wave(g, roots, k, depth_scratch, s, c);  // warm-up
+      if (r != BFS_OK) break;
+      float ms = 0;
+      if (cudaEventRecord(e0, s) != cudaSuccess || (r = ms_launch_wave(g, roots, k, depth_scratch, s, c)) != BFS_OK ||
+          cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        if (r == BFS_OK) r = fail(BFS_ERR_CUDA, "tuning run failed");
+        break;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_cfg = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r != BFS_OK) return r;
+  g->ms_cfg = best_cfg;
+  best->push_mode = best_cfg.push_mode;
+  best->alpha = best_cfg.alpha;
+  best->ms = best_ms;
+  best->reserved = 0;
+  CU(cudaEventRecord(g->ms_done, s));
   return BFS_OK;
 }
 

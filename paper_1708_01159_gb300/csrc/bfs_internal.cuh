@@ -170,6 +170,55 @@ __device__ __forceinline__ void queue_append(int32_t* qout, unsigned int* tail, 
   qout[base + __popc(mask & lanemask_lt())] = v;
 }
 
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s bound on any device-side wait
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for persistent kernels (cooperative launch, so every block
+// is resident): arrival counter plus generation word. Waiting is bounded by
+// kWaitLimitNs and abandoned early once *status is not ST_OK; on either the
+// status word is set and false returned, so a kernel never spins forever.
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen_word, int32_t* status) {
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    const unsigned int gen = ld_acquire_u32(gen_word);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(count, 1u);
+    if (arrived == gridDim.x - 1) {
+      *count = 0;
+      __threadfence();
+      st_release_u32(gen_word, gen + 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(gen_word) == gen) {
+        if (*reinterpret_cast<volatile int32_t*>(status) != ST_OK || global_ns() - t0 > kWaitLimitNs) {
+          *status = ST_TIMEOUT;
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
 // Try to claim vertex v: set its visited bit. True only for the one thread
 // whose atomicOr flipped the bit, so each vertex enters the queue once.
 __device__ __forceinline__ bool claim(uint32_t* vis, int32_t v) {

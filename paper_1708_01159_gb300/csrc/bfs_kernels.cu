@@ -25,13 +25,6 @@ namespace bfs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s bound on any device-side wait
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // ---- mbarrier + bulk async copy (TMA bulk, non-tensor) --------------------
 
@@ -77,49 +70,11 @@ __device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
   return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
-// Grid-wide barrier for the persistent driver (cooperative launch, so every
-// block is resident). Arrival counter plus generation word; waiting is bounded
-// by kWaitLimitNs, after which the status word is set and false returned.
-__device__ bool grid_sync(RunState* st) {
-  __syncthreads();
-  bool ok = true;
-  if (threadIdx.x == 0) {
-    const unsigned int gen = ld_acquire_u32(&st->bar_gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&st->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      st->bar_count = 0;
-      __threadfence();
-      st_release_u32(&st->bar_gen, gen + 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (ld_acquire_u32(&st->bar_gen) == gen) {
-        if (*reinterpret_cast<volatile int32_t*>(&st->status) != ST_OK || global_ns() - t0 > kWaitLimitNs) {
-          st->status = ST_TIMEOUT;
-          ok = false;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  return __syncthreads_and(ok) != 0;
-}
+__device__ __forceinline__ bool grid_sync(RunState* st) { return grid_barrier(&st->bar_count, &st->bar_gen, &st->status); }
 
 // ---- output staging and per-edge visit --------------------------------------
 

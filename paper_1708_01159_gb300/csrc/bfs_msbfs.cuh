@@ -1,0 +1,35 @@
+// Multi-source BFS (64 roots per wave, one bit per root in 64-bit masks).
+#pragma once
+
+#include "bfs_internal.cuh"
+
+namespace bfs {
+
+constexpr int kMsThreads = 256;
+
+struct MsBuffers {
+  unsigned long long* visit;     // n masks: bit i = reached by root i
+  unsigned long long* front[2];  // n masks each: bit i = at depth L (read) / L + 1 (write) for root i
+  unsigned long long* next;      // n masks: bits pushed to the vertex during a push level
+  const int32_t* roots;          // device copy of the wave's roots
+};
+
+struct MsState {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int32_t status;
+  int32_t levels;
+  unsigned long long fcount[3];  // frontier vertices (any lane) per level, indexed by level % 3
+  unsigned long long fedges[3];  // their out-degree sum
+  unsigned long long edges[64];  // reached-edge count per root
+};
+
+struct MsConfig {
+  int32_t push_mode;  // 0: thread per frontier vertex, 1: warp per frontier vertex
+  int32_t alpha;      // a level pulls when its frontier edges x alpha exceed m
+};
+
+__global__ void k_msbfs(DevGraph g, MsBuffers mb, MsState* st, int32_t k, int32_t* depth, MsConfig cfg);
+__global__ void k_ms_reset(MsState* st);
+
+}  // namespace bfs

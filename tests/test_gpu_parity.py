@@ -284,6 +284,40 @@ def test_batch_equals_single_runs():
         assert np.array_equal(edges, E)
 
 
+@pytest.mark.parametrize("push_mode", [0, 1])
+@pytest.mark.parametrize("alpha", [1, 8, 1 << 20])
+def test_batch_configs(push_mode, alpha):
+    """Multi-source BFS in every configuration (alpha 1: pull from level 1 on;
+    huge alpha: push only) equals independent oracle runs, repeated and isolated
+    roots included."""
+    g = gg.rmat(12, 8, seed=91)
+    iso = int(np.nonzero(g.degrees() == 0)[0][0])
+    roots = np.concatenate([gg.sample_roots(g, 40, seed=12), [iso, iso], gg.sample_roots(g, 3, seed=12)])
+    D, E = oracle.bfs_batch(g.off, g.idx, roots)
+    with make(g) as G:
+        bfs.bfs_batch_set_config(G.handle, push_mode, alpha)
+        out = torch.empty(len(roots) * g.n, dtype=torch.int32, device="cuda")
+        edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
+        assert np.array_equal(out.cpu().numpy().reshape(len(roots), g.n), D)
+        assert np.array_equal(edges, E)
+
+
+def test_batch_directed_and_tuner():
+    rng = np.random.default_rng(5)
+    n = 5000
+    g = gg.from_edges(n, rng.integers(0, n, 20000), rng.integers(0, n, 20000), symmetrize=False)
+    roots = gg.sample_roots(g, 64, seed=13)
+    D, E = oracle.bfs_batch(g.off, g.idx, roots)
+    with make(g, flags=0) as G:
+        scratch = torch.empty(64 * n, dtype=torch.int32, device="cuda")
+        cfg = bfs.bfs_batch_tune(G.handle, roots, scratch)
+        assert cfg["push_mode"] in (0, 1) and cfg["alpha"] >= 1 and cfg["ms"] > 0
+        out = torch.empty(64 * n, dtype=torch.int32, device="cuda")
+        edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
+        assert np.array_equal(out.cpu().numpy().reshape(64, n), D)
+        assert np.array_equal(edges, E)
+
+
 # --------------------------------------------------------- full-size workloads
 
 @pytest.mark.slow
