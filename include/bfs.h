@@ -238,6 +238,59 @@ int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* dept
 int bfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int64_t n, int64_t m, int32_t root,
                    int32_t* depth_out, bfs_stream_t stream);
 
+/*
+ * Serving: a request loop over graphs resident in HBM (the paper has no
+ * serving layer; this wraps the Section 3.1 traversal for many concurrent
+ * queries). A dispatcher thread admits submitted single-root queries whenever
+ * an in-flight slot and the memory the query needs (its traversal workspace,
+ * plus an n-entry depth buffer when the caller passes none) fit the budget,
+ * first fit over the head of the queue; admitted queries run on a pool of
+ * streams and overlap on the device; queued queries to the same graph are
+ * merged into one multi-source wave (continuous batching). Results are the
+ * same as alone: depths are exact.
+ */
+typedef struct bfs_server* bfs_server_t;
+
+typedef struct bfs_serve_config {
+  int64_t mem_budget_bytes; /* device bytes admitted queries may hold at once; 0 = unlimited */
+  int32_t max_inflight;     /* admitted units (queries or merged waves) on the device at once, 1..1024 */
+  int32_t num_streams;      /* streams the units are spread over, 1..64 */
+  int32_t queue_capacity;   /* pending submissions before bfs_serve_submit returns BFS_ERR_BUSY */
+  int32_t merge_batch;      /* up to this many queued queries to one graph run as one wave (0 or 1: off; <= 64) */
+  int32_t reserved[2];      /* must be zero */
+} bfs_serve_config;
+
+typedef struct bfs_serve_stats {
+  int64_t submitted, admitted, completed, rejected, failed;
+  int64_t peak_bytes_inflight; /* largest admitted memory at once */
+  int32_t merged_waves;        /* waves that merged several queries */
+  int32_t queued;              /* submissions waiting now */
+  double qps;                  /* completed / (last completion - first submission) */
+  double p50_ms, p99_ms, max_ms; /* submission-to-completion latency */
+  double gteps;                /* sum of edges_reached / 2 over completed queries / the same wall time / 1e9 */
+} bfs_serve_stats_t;
+
+/* Start a server (and its dispatcher thread) on the current device. */
+int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out);
+/* Register a graph (same device; up to 256; the caller keeps it alive until bfs_serve_destroy). */
+int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id);
+/* Queue a query; non-blocking. depth_out: device, n int32, or NULL (the server
+ * supplies a buffer and the depths are not returned). BFS_ERR_BUSY when the
+ * queue is full, BFS_ERR_NOT_FOUND for an unknown graph id. *ticket identifies it. */
+int bfs_serve_submit(bfs_server_t s, int32_t graph_id, int32_t root, int32_t* depth_out, uint64_t* ticket);
+/* *state: 0 done, 1 queued, 2 running. Returns the query's status once done
+ * (BFS_OK before), BFS_ERR_NOT_FOUND for an unknown or long-retired ticket. */
+int bfs_serve_poll(bfs_server_t s, uint64_t ticket, int* state);
+/* Block until the query is done (timeout_us < 0: no limit). BFS_ERR_TIMEOUT if
+ * it is still pending after timeout_us; otherwise the query's status. */
+int bfs_serve_wait(bfs_server_t s, uint64_t ticket, int64_t timeout_us);
+/* Counters and latency percentiles since creation (host struct). */
+int bfs_serve_stats(bfs_server_t s, bfs_serve_stats_t* out);
+/* Let running queries finish, cancel queued ones (BFS_ERR_CANCELLED), stop the
+ * dispatcher and free the server. A query larger than the whole budget is
+ * admitted when nothing else is in flight, so every query eventually runs. */
+int bfs_serve_destroy(bfs_server_t s);
+
 /* One level of a profiled traversal. */
 typedef struct bfs_level_profile {
   int64_t features[BFS_NUM_FEATURES]; /* the tree's input at this level (enum bfs_feature order) */

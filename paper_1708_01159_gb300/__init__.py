@@ -77,6 +77,20 @@ class _Stats(ctypes.Structure):
                 ("log_frontier_edges", ctypes.POINTER(ctypes.c_int64))]
 
 
+class _ServeConfig(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("num_streams", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("merge_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class _ServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("failed", ctypes.c_int64), ("peak_bytes_inflight", ctypes.c_int64),
+                ("merged_waves", ctypes.c_int32), ("queued", ctypes.c_int32), ("qps", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("gteps", ctypes.c_double)]
+
+
 class _BatchConfig(ctypes.Structure):
     _fields_ = [("push_mode", ctypes.c_int32), ("alpha", ctypes.c_int32), ("ms", ctypes.c_float),
                 ("reserved", ctypes.c_int32)]
@@ -125,6 +139,13 @@ def lib():
             "bfs_run_static": (ctypes.c_int, [vp, vp, c_i64, c_i64, c_i32, vp, vp]),
             "bfs_batch_set_config": (ctypes.c_int, [vp, ctypes.POINTER(_BatchConfig)]),
             "bfs_batch_tune": (ctypes.c_int, [vp, vp, c_i32, vp, vp, ctypes.POINTER(_BatchConfig)]),
+            "bfs_serve_create": (ctypes.c_int, [ctypes.POINTER(_ServeConfig), ctypes.POINTER(vp)]),
+            "bfs_serve_add_graph": (ctypes.c_int, [vp, vp, ctypes.POINTER(c_i32)]),
+            "bfs_serve_submit": (ctypes.c_int, [vp, c_i32, c_i32, vp, ctypes.POINTER(ctypes.c_uint64)]),
+            "bfs_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+            "bfs_serve_wait": (ctypes.c_int, [vp, ctypes.c_uint64, c_i64]),
+            "bfs_serve_stats": (ctypes.c_int, [vp, ctypes.POINTER(_ServeStats)]),
+            "bfs_serve_destroy": (ctypes.c_int, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -306,6 +327,57 @@ def bfs_run_static(row_offsets, col_indices, root: int, depth_out, stream=None) 
     if nd != no - 1:
         raise ValueError("depth_out must have n = len(row_offsets) - 1 entries")
     _check(lib().bfs_run_static(po, pi, no - 1, ni, int(root), pd, _stream(stream)), "bfs_run_static")
+
+
+def bfs_serve_create(mem_budget_bytes: int = 0, max_inflight: int = 16, num_streams: int = 8,
+                     queue_capacity: int = 1 << 16, merge_batch: int = 0) -> int:
+    c = _ServeConfig(mem_budget_bytes=mem_budget_bytes, max_inflight=max_inflight, num_streams=num_streams,
+                     queue_capacity=queue_capacity, merge_batch=merge_batch)
+    out = ctypes.c_void_p()
+    _check(lib().bfs_serve_create(ctypes.byref(c), ctypes.byref(out)), "bfs_serve_create")
+    return out.value
+
+
+def bfs_serve_add_graph(s: int, g: int) -> int:
+    gid = ctypes.c_int32()
+    _check(lib().bfs_serve_add_graph(s, g, ctypes.byref(gid)), "bfs_serve_add_graph")
+    return gid.value
+
+
+def bfs_serve_submit(s: int, graph_id: int, root: int, depth_out=None) -> int:
+    """Queue one query; returns its ticket. Raises BFSError(BFS_ERR_BUSY) when the queue is full."""
+    p = None
+    if depth_out is not None:
+        p, dev, _ = _ptr(depth_out, what="depth_out")
+        if not dev:
+            raise ValueError("depth_out must be device memory")
+    t = ctypes.c_uint64()
+    _check(lib().bfs_serve_submit(s, int(graph_id), int(root), p, ctypes.byref(t)), "bfs_serve_submit")
+    return t.value
+
+
+def bfs_serve_poll(s: int, ticket: int):
+    """(state, status): state 0 done, 1 queued, 2 running."""
+    st = ctypes.c_int()
+    rc = lib().bfs_serve_poll(s, ticket, ctypes.byref(st))
+    if rc == BFS_ERR_NOT_FOUND:
+        _check(rc, "bfs_serve_poll")
+    return st.value, rc
+
+
+def bfs_serve_wait(s: int, ticket: int, timeout_us: int = -1) -> int:
+    """The query's status once done; BFS_ERR_TIMEOUT if still pending after timeout_us."""
+    return int(lib().bfs_serve_wait(s, ticket, int(timeout_us)))
+
+
+def bfs_serve_stats(s: int) -> dict:
+    st = _ServeStats()
+    _check(lib().bfs_serve_stats(s, ctypes.byref(st)), "bfs_serve_stats")
+    return {f: getattr(st, f) for f, _ in _ServeStats._fields_}
+
+
+def bfs_serve_destroy(s: int) -> None:
+    _check(lib().bfs_serve_destroy(s), "bfs_serve_destroy")
 
 
 class Graph:

@@ -24,7 +24,7 @@ TREE_INC = os.path.join(BUILD, "default_tree.inc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-warn-spills"]
-SOURCES = ["bfs_kernels.cu", "bfs_api.cu", "bfs_static.cu", "bfs_msbfs.cu"]
+SOURCES = ["bfs_kernels.cu", "bfs_api.cu", "bfs_static.cu", "bfs_msbfs.cu", "bfs_serve.cu"]
 
 
 def nvcc() -> str:

@@ -613,6 +613,47 @@ int ms_launch_wave(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth
 
 int bfs::set_error_detail(int code, const char* msg) { return fail(code, "%s", msg); }
 
+long long bfs::workspace_bytes(const bfs_graph* g) {
+  const long long n = g->dg.n, words = g->dg.words;
+  // two queues, two bitmaps, edge-centric scan scratch, host-output stage, logs
+  return 4 * n * 2 + 4 * words * 2 + 4 * (n + 1) + 4 * n + 8 * ((n + kPeTile - 1) / kPeTile + 2) + 4 * n +
+         20 * std::min<long long>(n + 1, 1 << 16) + (long long)sizeof(RunState);
+}
+
+int32_t bfs::graph_vertices(const bfs_graph* g) { return g->dg.n; }
+
+int bfs::graph_device(const bfs_graph* g) { return g->device; }
+
+int bfs::run_async(bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t stream, int32_t mode,
+                   long long* edges_dst) {
+  if (root < 0 || root >= g->dg.n || !depth_out) return fail(BFS_ERR_INVALID_ARG, "run_async arguments");
+  DeviceGuard dgd(g->device);
+  TRY(sync_tree(g));
+  Workspace* ws = nullptr;
+  TRY(acquire(g, stream, &ws));
+  int r = launch_run(g, ws, root, depth_out, -1, mode, stream);
+  if (r == BFS_OK && edges_dst) {
+    cudaError_t e = cudaMemcpyAsync(edges_dst, &ws->st->edges_reached, sizeof(long long), cudaMemcpyDeviceToHost,
+                                    stream);
+    if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "edges copy: %s", cudaGetErrorString(e));
+  }
+  int rr = release(g, ws, stream);
+  return r != BFS_OK ? r : rr;
+}
+
+int bfs::batch_async(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t stream,
+                     unsigned long long* edges_dst) {
+  if (k < 1 || k > 64 || !roots || !depth_out) return fail(BFS_ERR_INVALID_ARG, "batch_async arguments");
+  DeviceGuard dgd(g->device);
+  std::lock_guard<std::mutex> lk(g->ms_mu);
+  TRY(ms_prepare(g));
+  CU(cudaStreamWaitEvent(stream, g->ms_done, 0));
+  TRY(ms_launch_wave(g, roots, k, depth_out, stream, g->ms_cfg));
+  if (edges_dst) CU(cudaMemcpyAsync(edges_dst, g->ms_state->edges, 64 * 8, cudaMemcpyDeviceToHost, stream));
+  CU(cudaEventRecord(g->ms_done, stream));
+  return BFS_OK;
+}
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

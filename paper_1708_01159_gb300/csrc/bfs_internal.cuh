@@ -16,6 +16,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct bfs_graph;  // the C ABI's graph object (defined in bfs_api.cu)
+
 namespace bfs {
 
 enum Variant : int32_t {
@@ -112,6 +114,21 @@ struct Buffers {
 
 // Records `msg` as the calling thread's bfs_last_error_detail() and returns code.
 int set_error_detail(int code, const char* msg);
+
+// Library-internal entry points used by the serving loop (not part of the C ABI).
+// run_async: enqueue one traversal on `stream` in the given bfs_mode and, when
+// edges_dst (pinned host memory) is not null, an asynchronous copy of its
+// reached-edge count there. batch_async: one multi-source wave (k <= 64) into k
+// rows of depth_out, per-root reached-edge counts copied to edges_dst (pinned,
+// 64 entries). Both return a bfs_status code.
+int run_async(struct ::bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t stream, int32_t mode,
+              long long* edges_dst);
+int batch_async(struct ::bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t stream,
+                unsigned long long* edges_dst);
+// Device bytes one traversal of the graph holds (workspace), for admission control.
+long long workspace_bytes(const struct ::bfs_graph* g);
+int32_t graph_vertices(const struct ::bfs_graph* g);
+int graph_device(const struct ::bfs_graph* g);
 
 // ---------------------------------------------------------------------------
 // Small device helpers
