@@ -49,6 +49,11 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fixed", action="store_true")
     p.add_argument("--no-roofline", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-grid", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-rates", default="1000,4000,16000", help="offered loads (queries/s)")
+    p.add_argument("--serve-seconds", type=float, default=2.0)
     return p.parse_args()
 
 
@@ -214,6 +219,120 @@ def traffic_for(kernel_key):
         return None
 
 
+def bench_batch(bfs, torch, stream):
+    """Multi-source BFS: ER 2^22, average degree 8, 64 roots in one launch (tuned), against
+    the same 64 roots as single-source switched traversals."""
+    import graphgen as gg
+    g = gg.er_2p22_d8()
+    roots = gg.sample_roots(g, 64, seed=gg.SEED_ROOTS + 3, giant=True)
+    out = {"workload": f"Erdos-Renyi 2^22 vertices, average degree 8 ({g.m:,} directed edges), 64 roots per launch"}
+    with bfs.Graph(g.off, g.idx) as G:
+        depth = torch.empty(64 * g.n, dtype=torch.int32, device="cuda")
+        cfg = bfs.bfs_batch_tune(G.handle, roots, depth, stream)
+        edges = bfs.bfs_run_batch(G.handle, roots, depth, stream, edges=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            bfs.bfs_run_batch(G.handle, roots, depth, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        single = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for r in roots[:4]:
+            bfs.bfs_run(G.handle, int(r), single, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for r in roots:
+            bfs.bfs_run(G.handle, int(r), single, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts = e0.elapsed_time(e1) / 1e3
+        out.update({"gteps": float(edges.sum()) / 2 / t / 1e9, "ms_per_launch": t * 1e3,
+                    "single_source_gteps": float(edges.sum()) / 2 / ts / 1e9, "speedup_vs_single": ts / t,
+                    "tuned": {"push_mode": ["thread", "warp"][cfg["push_mode"]], "alpha": cfg["alpha"]},
+                    "note": "depth output k x n int32 written inside the timed region (1.07 GB per launch)"})
+    return out
+
+
+def bench_grid(bfs, torch, stream):
+    """High diameter: 4096 x 4096 permuted grid, 10% edges dropped, 4 roots; both drivers."""
+    import graphgen as gg
+    g = gg.grid_4096_permuted()
+    roots = gg.sample_roots(g, 4, seed=gg.SEED_ROOTS + 2, giant=True)
+    out = {"workload": f"4096x4096 grid, 10% of edges dropped, ids permuted ({g.m:,} directed edges), 4 roots"}
+    with bfs.Graph(g.off, g.idx) as G:
+        depth = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        st = bfs.bfs_run_ex(G.handle, int(roots[0]), depth, stream, stats=True)
+        out["levels"] = st["levels"]
+        edges = st["edges_reached"]
+        for name, mode in (("persistent", bfs.MODE_PERSISTENT), ("graph", bfs.MODE_GRAPH)):
+            bfs.bfs_run_ex(G.handle, int(roots[0]), depth, stream, mode=mode)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for r in roots:
+                bfs.bfs_run_ex(G.handle, int(r), depth, stream, mode=mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3 / len(roots)
+            out[name] = {"gteps": edges / 2 / t / 1e9, "ms_per_traversal": t * 1e3,
+                         "us_per_level": t * 1e6 / st["levels"]}
+    return out
+
+
+def bench_serve(bfs, torch, args):
+    """Serving: 8 resident graphs, Poisson arrivals of single-root queries (graph
+    uniform, root uniform over vertices of nonzero degree), continuous batching."""
+    import graphgen as gg
+    specs = [("rmat16", lambda: gg.rmat(16, 16, seed=5016)), ("rmat18", lambda: gg.rmat(18, 16, seed=5018)),
+             ("rmat20", lambda: gg.rmat(20, 16, seed=5020)), ("rmat22", lambda: gg.rmat(22, 16, seed=5022)),
+             ("rmat24", lambda: gg.rmat(24, 16, seed=5024)), ("grid2048", lambda: gg.grid(2048, 2048, 0.1, seed=5025)),
+             ("grid4096", lambda: gg.grid(4096, 4096, 0.1, seed=5026)),
+             ("er21", lambda: gg.erdos_renyi(1 << 21, 16.0, seed=5027))]
+    Gs, cand = [], []
+    for name, mk in specs:
+        g = mk()
+        Gs.append(bfs.Graph(g.off, g.idx))
+        cand.append(np.nonzero(np.diff(g.off) > 0)[0].astype(np.int32))
+        del g
+    rng = np.random.default_rng(5000)
+    out = {"graphs": [n for n, _ in specs], "loads": []}
+    try:
+        for rate in [float(x) for x in args.serve_rates.split(",")]:
+            nq = int(rate * args.serve_seconds)
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, nq))
+            gsel = rng.integers(0, len(Gs), nq)
+            roots = [int(cand[k][rng.integers(0, len(cand[k]))]) for k in gsel]
+            s = bfs.bfs_serve_create(max_inflight=32, num_streams=16, queue_capacity=1 << 17, merge_batch=64)
+            try:
+                ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
+                tickets = []
+                rejected = 0
+                t0 = time.perf_counter()
+                for q in range(nq):
+                    while time.perf_counter() - t0 < arrivals[q]:
+                        pass
+                    try:
+                        tickets.append(bfs.bfs_serve_submit(s, ids[gsel[q]], roots[q]))
+                    except bfs.BFSError:
+                        rejected += 1
+                for t in tickets:
+                    bfs.bfs_serve_wait(s, t)
+                st = bfs.bfs_serve_stats(s)
+                out["loads"].append({"offered_qps": rate, "achieved_qps": st["qps"], "p50_ms": st["p50_ms"],
+                                     "p99_ms": st["p99_ms"], "gteps": st["gteps"], "completed": st["completed"],
+                                     "rejected": st["rejected"], "merged_waves": st["merged_waves"],
+                                     "peak_bytes_inflight": st["peak_bytes_inflight"]})
+            finally:
+                bfs.bfs_serve_destroy(s)
+    finally:
+        for G in Gs:
+            G.close()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -359,6 +478,15 @@ def run_ours(args):
                             "per_level_ms_chosen": [round(float(x), 4) for x in chosen],
                             "per_level_optimal_ms": float(ms.min(axis=1).sum()),
                             "per_level_tree_ms": float(chosen.sum())}
+
+    G.close()
+    del depth
+    if not args.no_batch:
+        line["batch"] = bench_batch(bfs, torch, stream)
+    if not args.no_grid:
+        line["high_diameter"] = bench_grid(bfs, torch, stream)
+    if not args.no_serve:
+        line["serve"] = bench_serve(bfs, torch, args)
 
     # the oracle on the host, bounded sample (rank 0, one GPU)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
