@@ -275,8 +275,10 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out);
 /* Register a graph (same device; up to 256; the caller keeps it alive until bfs_serve_destroy). */
 int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id);
 /* Queue a query; non-blocking. depth_out: device, n int32, or NULL (the server
- * supplies a buffer and the depths are not returned). BFS_ERR_BUSY when the
- * queue is full, BFS_ERR_NOT_FOUND for an unknown graph id. *ticket identifies it. */
+ * supplies a buffer and the depths are not returned). The server's streams do
+ * not wait on the caller's streams: depth_out must be ready to be written when
+ * submitted, and is valid once the query is done. BFS_ERR_BUSY when the queue
+ * is full, BFS_ERR_NOT_FOUND for an unknown graph id. *ticket identifies it. */
 int bfs_serve_submit(bfs_server_t s, int32_t graph_id, int32_t root, int32_t* depth_out, uint64_t* ticket);
 /* *state: 0 done, 1 queued, 2 running. Returns the query's status once done
  * (BFS_OK before), BFS_ERR_NOT_FOUND for an unknown or long-retired ticket. */

@@ -44,6 +44,8 @@ def test_mixed_results_equal_alone(graphs, merge):
             gi = int(rng.integers(0, len(gs)))
             root = int(gg.sample_roots(gs[gi], 1, seed=1000 + q)[0])
             out = torch.full((gs[gi].n,), -7, dtype=torch.int32, device="cuda")
+            # the server's streams do not wait on the caller's: the buffer must be ready when submitted
+            torch.cuda.synchronize()
             t = bfs.bfs_serve_submit(s, ids[gi], root, out)
             jobs.append((gi, root, out, t))
         for gi, root, out, t in jobs:
