@@ -219,6 +219,14 @@ def traffic_for(kernel_key):
         return None
 
 
+def progress(msg):
+    """Synchronise the device (so an asynchronous error is charged to the section
+    that caused it) and note the section on stderr."""
+    import torch
+    torch.cuda.synchronize()
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
 def bench_batch(bfs, torch, stream):
     """Multi-source BFS: ER 2^22, average degree 8, 64 roots in one launch (tuned), against
     the same 64 roots as single-source switched traversals."""
@@ -297,6 +305,7 @@ def bench_serve(bfs, torch, args):
         Gs.append(bfs.Graph(g.off, g.idx))
         cand.append(np.nonzero(np.diff(g.off) > 0)[0].astype(np.int32))
         del g
+        progress(f"serve graph {name} resident")
     rng = np.random.default_rng(5000)
     out = {"graphs": [n for n, _ in specs], "loads": []}
     try:
@@ -481,12 +490,16 @@ def run_ours(args):
 
     G.close()
     del depth
+    progress("switched, fixed, e2e and roofline done")
     if not args.no_batch:
         line["batch"] = bench_batch(bfs, torch, stream)
+        progress("batch done")
     if not args.no_grid:
         line["high_diameter"] = bench_grid(bfs, torch, stream)
+        progress("high-diameter done")
     if not args.no_serve:
         line["serve"] = bench_serve(bfs, torch, args)
+        progress("serve done")
 
     # the oracle on the host, bounded sample (rank 0, one GPU)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
