@@ -39,15 +39,14 @@ def test_mixed_results_equal_alone(graphs, merge):
     s = bfs.bfs_serve_create(max_inflight=12, num_streams=6, merge_batch=merge)
     try:
         ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
-        jobs = []
+        plan = []
         for q in range(240):
             gi = int(rng.integers(0, len(gs)))
             root = int(gg.sample_roots(gs[gi], 1, seed=1000 + q)[0])
-            out = torch.full((gs[gi].n,), -7, dtype=torch.int32, device="cuda")
-            # the server's streams do not wait on the caller's: the buffer must be ready when submitted
-            torch.cuda.synchronize()
-            t = bfs.bfs_serve_submit(s, ids[gi], root, out)
-            jobs.append((gi, root, out, t))
+            plan.append((gi, root, torch.full((gs[gi].n,), -7, dtype=torch.int32, device="cuda")))
+        # the server's streams do not wait on the caller's: buffers must be ready when submitted
+        torch.cuda.synchronize()
+        jobs = [(gi, root, out, bfs.bfs_serve_submit(s, ids[gi], root, out)) for gi, root, out in plan]
         for gi, root, out, t in jobs:
             assert bfs.bfs_serve_wait(s, t) == bfs.BFS_OK
         torch.cuda.synchronize()
