@@ -1,7 +1,8 @@
-// C ABI of libbfs: graph objects, workspaces, the device-resident level loop
-// (one CUDA graph per workspace: init -> WHILE(frontier) { decide -> SWITCH
-// (variant) { level kernels } }), the decision-tree store and the per-level
-// timing harness.
+// C ABI of libbfs: graph objects, workspaces, the three level-loop drivers
+// (persistent cooperative kernel; k_init followed by one CUDA graph per
+// workspace, loop_start -> WHILE(frontier) { decide -> SWITCH(variant) { level
+// kernels } }; host loop), the decision-tree store, multi-source batches and
+// the per-level timing harness.
 #include <algorithm>
 #include <atomic>
 #include <cstdarg>
@@ -164,7 +165,7 @@ struct Workspace {
   int32_t* host_depth_stage = nullptr;  // device buffer for runs whose output is host memory
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t init_node = nullptr;
+  cudaGraphNode_t start_node = nullptr;
   cudaEvent_t done = nullptr;
   cudaStream_t last_stream = nullptr;
   bool in_use = false;
@@ -259,70 +260,28 @@ int add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphNode_t* 
   return BFS_OK;
 }
 
-int fill_init_params(bfs_graph* g, Workspace* ws, int32_t* depth, int32_t root, int32_t forced,
-                     cudaKernelNodeParams* p, void** argp, void* storage) {
-  // storage layout: DevGraph, Buffers, RunState*, int32_t* depth, int32 root, int32 forced, TreeNode*, int32 nodes,
-  // int32 use_handles
-  struct InitArgs {
-    DevGraph g;
-    Buffers b;
-    RunState* st;
-    int32_t* depth;
-    int32_t root;
-    int32_t forced;
-    const TreeNode* tree;
-    int32_t nodes;
-    int32_t use_handles;
-  };
-  static_assert(sizeof(InitArgs) <= 1024, "init args");
-  InitArgs* a = static_cast<InitArgs*>(storage);
-  a->g = g->dg;
-  a->b = ws->b;
-  a->st = ws->st;
-  a->depth = depth;
-  a->root = root;
-  a->forced = forced;
-  a->tree = g->tree;
-  a->nodes = g->tree_nodes;
-  a->use_handles = 1;
-  argp[0] = &a->g;
-  argp[1] = &a->b;
-  argp[2] = &a->st;
-  argp[3] = &a->depth;
-  argp[4] = &a->root;
-  argp[5] = &a->forced;
-  argp[6] = &a->tree;
-  argp[7] = &a->nodes;
-  argp[8] = &a->use_handles;
-  *p = cudaKernelNodeParams{};
-  p->func = reinterpret_cast<void*>(&k_init);
-  p->gridDim = dim3(g->shapes.init);
-  p->blockDim = dim3(kThreads);
-  p->kernelParams = argp;
-  return BFS_OK;
-}
-
 // Build the level loop of one workspace as a CUDA graph with conditional nodes.
+// The graph holds the level loop only: k_loop_start opens the WHILE loop on the
+// device, and per-run values (root, output, forced variant, tree) reach it
+// through RunState, written by a k_init launched on the same stream just
+// before. Nothing in the instantiated graph changes between launches, so
+// back-to-back launches on one stream cannot see each other's parameters.
 int build_graph(bfs_graph* g, Workspace* ws) {
   CU(cudaGraphCreate(&ws->graph, 0));
-  alignas(16) unsigned char storage[1024];
-  void* argp[9];
-  cudaKernelNodeParams ip;
-  TRY(fill_init_params(g, ws, ws->host_depth_stage, 0, -1, &ip, argp, storage));
-  CU(cudaGraphAddKernelNode(&ws->init_node, ws->graph, nullptr, 0, &ip));
+  KArgs ka{g->dg, ws->b, ws->st, {}};
+  TRY(add_kernel(ws->graph, &ws->start_node, nullptr, reinterpret_cast<const void*>(&k_loop_start), 1, 32, ka));
 
   cudaGraphConditionalHandle hw;
-  CU(cudaGraphConditionalHandleCreate(&hw, ws->graph, 1, cudaGraphCondAssignDefault));
+  CU(cudaGraphConditionalHandleCreate(&hw, ws->graph, 0, 0));
   cudaGraphNodeParams wp{};
   wp.type = cudaGraphNodeTypeConditional;
   wp.conditional.handle = hw;
   wp.conditional.type = cudaGraphCondTypeWhile;
   wp.conditional.size = 1;
   cudaGraphNode_t wnode;
-  CU(cudaGraphAddNode(&wnode, ws->graph, &ws->init_node, nullptr, 1, &wp));
+  CU(cudaGraphAddNode(&wnode, ws->graph, &ws->start_node, nullptr, 1, &wp));
   cudaGraph_t body = wp.conditional.phGraph_out[0];
 
-  KArgs ka{g->dg, ws->b, ws->st, {}};
   cudaGraphNode_t decide;
   TRY(add_kernel(body, &decide, nullptr, reinterpret_cast<const void*>(&k_decide), 1, 32, ka));
 
@@ -468,11 +427,9 @@ int sync_tree(bfs_graph* g) {
 int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s);
 
 int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
-  alignas(16) unsigned char storage[1024];
-  void* argp[9];
-  cudaKernelNodeParams ip;
-  TRY(fill_init_params(g, ws, depth, root, forced, &ip, argp, storage));
-  CU(cudaGraphExecKernelNodeSetParams(ws->exec, ws->init_node, &ip));
+  k_init<<<g->shapes.init, kThreads, 0, stream>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes,
+                                                  1);
+  CU(cudaGetLastError());
   CU(cudaGraphLaunch(ws->exec, stream));
   return BFS_OK;
 }

@@ -693,6 +693,16 @@ __global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunSta
   }
 }
 
+// First node of the level-loop graph: opens the WHILE loop from the device.
+// (The handle has no launch-time default: a value applied by the host when a
+// launch is enqueued could reach a still-running earlier launch of the same
+// graph on that stream; a kernel inside the launch is ordered with it.)
+__global__ void k_loop_start(DevGraph g, Buffers b, RunState* st) {
+  (void)g;
+  (void)b;
+  if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)st->h_while, 1u);
+}
+
 // Level end + tree evaluation, between levels on the device (one thread).
 __global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;

@@ -14,6 +14,7 @@ constexpr int kPeTile = kThreads * kPeItems;  // frontier entries per scan block
 __global__ void k_init(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root, int32_t forced,
                        const TreeNode* tree, int32_t tree_nodes, int32_t use_handles);
 __global__ void k_decide(DevGraph g, Buffers b, RunState* st);
+__global__ void k_loop_start(DevGraph g, Buffers b, RunState* st);
 __global__ void k_push_thread(DevGraph g, Buffers b, RunState* st);
 __global__ void k_push_warp(DevGraph g, Buffers b, RunState* st);
 __global__ void k_push_cta(DevGraph g, Buffers b, RunState* st);
