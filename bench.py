@@ -327,11 +327,16 @@ def bench_serve(bfs, torch, args):
                         tickets.append(bfs.bfs_serve_submit(s, ids[gsel[q]], roots[q]))
                     except bfs.BFSError:
                         rejected += 1
+                # drain for at most 10 s; what is still queued then is cancelled at shutdown
+                deadline = time.perf_counter() + 10.0
                 for t in tickets:
-                    bfs.bfs_serve_wait(s, t)
+                    left_us = int((deadline - time.perf_counter()) * 1e6)
+                    if left_us <= 0 or bfs.bfs_serve_wait(s, t, left_us) == bfs.BFS_ERR_TIMEOUT:
+                        break
                 st = bfs.bfs_serve_stats(s)
                 out["loads"].append({"offered_qps": rate, "achieved_qps": st["qps"], "p50_ms": st["p50_ms"],
-                                     "p99_ms": st["p99_ms"], "gteps": st["gteps"], "completed": st["completed"],
+                                     "p99_ms": st["p99_ms"], "gteps": st["gteps"], "submitted": st["submitted"],
+                                     "completed": st["completed"], "not_finished": st["submitted"] - st["completed"],
                                      "rejected": st["rejected"], "merged_waves": st["merged_waves"],
                                      "peak_bytes_inflight": st["peak_bytes_inflight"]})
             finally:

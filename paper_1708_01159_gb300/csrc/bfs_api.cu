@@ -426,17 +426,33 @@ int sync_tree(bfs_graph* g) {
 
 int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s);
 
+// Graph-driver traversals run one after another on each device, whatever their
+// streams: with several level-loop graphs (different workspaces) executing at
+// once, about 1 % of runs found their WHILE loop not entered (init written, no
+// level run) on CUDA 13.0 / driver 580, while the same runs alone, one stream,
+// or the persistent driver under the same load were always exact. A per-device
+// gate event orders every graph-driver launch after the previous one.
+std::mutex g_gate_mu;
+cudaEvent_t g_gate[64] = {};
+
 int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_gate_mu);
+  cudaEvent_t& gate = g_gate[g->device & 63];
+  if (!gate) CU(cudaEventCreateWithFlags(&gate, cudaEventDisableTiming));
+  CU(cudaStreamWaitEvent(stream, gate, 0));
   k_init<<<g->shapes.init, kThreads, 0, stream>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes,
                                                   1);
   CU(cudaGetLastError());
   CU(cudaGraphLaunch(ws->exec, stream));
+  CU(cudaEventRecord(gate, stream));
   return BFS_OK;
 }
 
 // One cooperative launch runs the whole traversal (k_bfs_persistent).
+// grid_blocks > 0 runs the traversal on fewer blocks (every loop strides, the
+// barrier counts gridDim), so several traversals can be resident at once.
 int launch_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, int32_t grid_blocks) {
   k_persist_reset<<<1, 1, 0, stream>>>(ws->st);
   CU(cudaGetLastError());
   DevGraph dg = g->dg;
@@ -445,8 +461,9 @@ int launch_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth,
   const TreeNode* tree = g->tree;
   int32_t nodes = g->tree_nodes;
   void* args[] = {&dg, &b, &st, &depth, &root, &forced, &tree, &nodes};
-  CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_bfs_persistent), dim3(g->shapes.persist),
-                                 dim3(kThreads), args, 0, stream));
+  const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->shapes.persist) : g->shapes.persist;
+  CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_bfs_persistent), dim3(grid), dim3(kThreads), args, 0,
+                                 stream));
   return BFS_OK;
 }
 
@@ -467,12 +484,12 @@ int launch_host_loop(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, 
 }
 
 int launch_run(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, int32_t mode,
-               cudaStream_t stream) {
+               cudaStream_t stream, int32_t grid_blocks = 0) {
   if (mode == BFS_MODE_DEFAULT) mode = g->shapes.persist > 0 ? BFS_MODE_PERSISTENT : BFS_MODE_GRAPH;
   switch (mode) {
     case BFS_MODE_PERSISTENT:
       if (g->shapes.persist <= 0) return fail(BFS_ERR_INVALID_ARG, "device lacks cooperative launch");
-      return launch_persistent(g, ws, root, depth, forced, stream);
+      return launch_persistent(g, ws, root, depth, forced, stream, grid_blocks);
     case BFS_MODE_GRAPH: return launch_graph(g, ws, root, depth, forced, stream);
     case BFS_MODE_HOST_LOOP: return launch_host_loop(g, ws, root, depth, forced, stream);
     default: return fail(BFS_ERR_INVALID_ARG, "mode %d", mode);
@@ -511,10 +528,12 @@ int check_graph(bfs_graph_t g) {
 int ms_prepare(bfs_graph* g) {
   if (g->ms_state) return BFS_OK;
   const size_t n = (size_t)g->dg.n;
-  void* p[7] = {};
+  constexpr int kBufs = 9;
+  void* p[kBufs] = {};
   int r = BFS_OK;
-  const size_t sizes[7] = {n * 8, n * 8, n * 8, n * 8, 64 * 4, sizeof(MsState), 0};
-  for (int i = 0; i < 6 && r == BFS_OK; ++i) r = dmalloc(&p[i], sizes[i]);
+  // visit, front x 2, next, roots, state, frontier lists x 2, touched list
+  const size_t sizes[kBufs] = {n * 8, n * 8, n * 8, n * 8, 64 * 4, sizeof(MsState), n * 4, n * 4, n * 4};
+  for (int i = 0; i < kBufs && r == BFS_OK; ++i) r = dmalloc(&p[i], sizes[i]);
   if (r == BFS_OK && cudaEventCreateWithFlags(&g->ms_done, cudaEventDisableTiming) != cudaSuccess)
     r = fail(BFS_ERR_CUDA, "cudaEventCreate");
   if (r == BFS_OK) {
@@ -537,7 +556,7 @@ int ms_prepare(bfs_graph* g) {
     g->ms_done = nullptr;
     return r;
   }
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < kBufs; ++i) {
     g->allocs.push_back(p[i]);
     g->bytes += sizes[i];
   }
@@ -545,6 +564,9 @@ int ms_prepare(bfs_graph* g) {
   g->ms.front[0] = static_cast<unsigned long long*>(p[1]);
   g->ms.front[1] = static_cast<unsigned long long*>(p[2]);
   g->ms.next = static_cast<unsigned long long*>(p[3]);
+  g->ms.flist[0] = static_cast<int32_t*>(p[6]);
+  g->ms.flist[1] = static_cast<int32_t*>(p[7]);
+  g->ms.tlist = static_cast<int32_t*>(p[8]);
   g->ms_roots = static_cast<int32_t*>(p[4]);
   g->ms.roots = g->ms_roots;
   g->ms_state = static_cast<MsState*>(p[5]);
@@ -582,13 +604,13 @@ int32_t bfs::graph_vertices(const bfs_graph* g) { return g->dg.n; }
 int bfs::graph_device(const bfs_graph* g) { return g->device; }
 
 int bfs::run_async(bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t stream, int32_t mode,
-                   long long* edges_dst) {
+                   long long* edges_dst, int32_t grid_blocks) {
   if (root < 0 || root >= g->dg.n || !depth_out) return fail(BFS_ERR_INVALID_ARG, "run_async arguments");
   DeviceGuard dgd(g->device);
   TRY(sync_tree(g));
   Workspace* ws = nullptr;
   TRY(acquire(g, stream, &ws));
-  int r = launch_run(g, ws, root, depth_out, -1, mode, stream);
+  int r = launch_run(g, ws, root, depth_out, -1, mode, stream, grid_blocks);
   if (r == BFS_OK && edges_dst) {
     cudaError_t e = cudaMemcpyAsync(edges_dst, &ws->st->edges_reached, sizeof(long long), cudaMemcpyDeviceToHost,
                                     stream);

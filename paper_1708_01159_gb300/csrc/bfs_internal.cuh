@@ -120,9 +120,10 @@ int set_error_detail(int code, const char* msg);
 // edges_dst (pinned host memory) is not null, an asynchronous copy of its
 // reached-edge count there. batch_async: one multi-source wave (k <= 64) into k
 // rows of depth_out, per-root reached-edge counts copied to edges_dst (pinned,
-// 64 entries). Both return a bfs_status code.
+// 64 entries). grid_blocks > 0 limits a persistent run to that many blocks so
+// several runs can be resident at once. Both return a bfs_status code.
 int run_async(struct ::bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t stream, int32_t mode,
-              long long* edges_dst);
+              long long* edges_dst, int32_t grid_blocks);
 int batch_async(struct ::bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t stream,
                 unsigned long long* edges_dst);
 // Device bytes one traversal of the graph holds (workspace), for admission control.
@@ -185,6 +186,54 @@ __device__ __forceinline__ void queue_append(int32_t* qout, unsigned int* tail, 
   if ((int)lane_id() == leader) base = atomicAdd(tail, (unsigned)__popc(mask));
   base = __shfl_sync(mask, base, leader);
   qout[base + __popc(mask & lanemask_lt())] = v;
+}
+
+// Block-local staging of queue appends. Lanes reserve slots with one
+// shared-memory atomic per warp; a block-uniform drain reserves space in the
+// output queue with one global atomic per block and copies the slots out with
+// coalesced stores. (One global queue tail shared by every warp serialises
+// under dense levels; the block stage removes that.) Slots beyond the capacity
+// fall back to a warp-aggregated global append.
+constexpr int kStageCap = 2048;
+
+struct Stage {
+  int32_t* buf;
+  unsigned int* cnt;
+  unsigned int* base;
+};
+
+#define BFS_DECLARE_STAGE(name)                   \
+  __shared__ int32_t name##_buf[kStageCap];       \
+  __shared__ unsigned int name##_cnt, name##_base; \
+  if (threadIdx.x == 0) name##_cnt = 0;           \
+  __syncthreads();                                \
+  const Stage name { name##_buf, &name##_cnt, &name##_base }
+
+__device__ __forceinline__ void stage_put(const Stage& s, int32_t* out, unsigned int* tail, int32_t v) {
+  const uint32_t mask = __activemask();
+  const int leader = __ffs(mask) - 1;
+  unsigned int pos = 0;
+  if ((int)lane_id() == leader) pos = atomicAdd(s.cnt, (unsigned)__popc(mask));
+  pos = __shfl_sync(mask, pos, leader) + (unsigned)__popc(mask & lanemask_lt());
+  if (pos < (unsigned)kStageCap)
+    s.buf[pos] = v;
+  else
+    queue_append(out, tail, v);
+}
+
+// Copies the staged entries out once at least `threshold` are waiting. Every
+// thread of the block must call it (it synchronises).
+__device__ __forceinline__ void stage_drain(const Stage& s, int32_t* out, unsigned int* tail, unsigned int threshold) {
+  __syncthreads();
+  const unsigned int c = min(*s.cnt, (unsigned)kStageCap);
+  if (c == 0 || c < threshold) return;  // uniform: every thread read the same count
+  if (threadIdx.x == 0) *s.base = atomicAdd(tail, c);
+  __syncthreads();
+  const unsigned int b = *s.base;
+  for (unsigned int i = threadIdx.x; i < c; i += blockDim.x) out[b + i] = s.buf[i];
+  __syncthreads();
+  if (threadIdx.x == 0) *s.cnt = 0;
+  __syncthreads();
 }
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s bound on any device-side wait

@@ -108,52 +108,14 @@ __device__ __forceinline__ Level load_level(const Buffers& b, RunState* st) {
   return lv;
 }
 
-// Block-local staging of newly reached vertices. Lanes reserve slots with one
-// shared-memory atomic per warp; a block-uniform flush reserves space in the
-// output queue with one global atomic per block and copies the slots out with
-// coalesced stores. (One global queue tail shared by every warp serialises
-// under dense levels; the block stage removes that.) Slots beyond the
-// capacity fall back to a warp-aggregated global append.
-constexpr int kStageCap = 2048;
-
-struct Stage {
-  int32_t* buf;
-  unsigned int* cnt;
-  unsigned int* base;
-};
-
-#define BFS_DECLARE_STAGE(name)                   \
-  __shared__ int32_t name##_buf[kStageCap];       \
-  __shared__ unsigned int name##_cnt, name##_base; \
-  if (threadIdx.x == 0) name##_cnt = 0;           \
-  __syncthreads();                                \
-  const Stage name { name##_buf, &name##_cnt, &name##_base }
-
+// Newly reached vertices go through a block-local stage (see stage_put) into
+// the level's output queue.
 __device__ __forceinline__ void stage_push(const Stage& s, const Level& lv, int32_t v) {
-  const uint32_t mask = __activemask();
-  const int leader = __ffs(mask) - 1;
-  unsigned int pos = 0;
-  if ((int)lane_id() == leader) pos = atomicAdd(s.cnt, (unsigned)__popc(mask));
-  pos = __shfl_sync(mask, pos, leader) + (unsigned)__popc(mask & lanemask_lt());
-  if (pos < (unsigned)kStageCap)
-    s.buf[pos] = v;
-  else
-    queue_append(lv.qout, lv.tail, v);
+  stage_put(s, lv.qout, lv.tail, v);
 }
 
-// Copies the staged entries out once at least `threshold` are waiting. Every
-// thread of the block must call it (it synchronises).
 __device__ __forceinline__ void stage_flush(const Stage& s, const Level& lv, unsigned int threshold) {
-  __syncthreads();
-  const unsigned int c = min(*s.cnt, (unsigned)kStageCap);
-  if (c == 0 || c < threshold) return;  // uniform: every thread read the same count
-  if (threadIdx.x == 0) *s.base = atomicAdd(lv.tail, c);
-  __syncthreads();
-  const unsigned int b = *s.base;
-  for (unsigned int i = threadIdx.x; i < c; i += blockDim.x) lv.qout[b + i] = s.buf[i];
-  __syncthreads();
-  if (threadIdx.x == 0) *s.cnt = 0;
-  __syncthreads();
+  stage_drain(s, lv.qout, lv.tail, threshold);
 }
 
 // Top-down visit of up to K edges u -> v[k] (Section 3.1.2 push). The bitmap
@@ -841,7 +803,7 @@ __global__ void k_persist_reset(RunState* st) {
   st->bar_count = 0;
 }
 
-__global__ void __launch_bounds__(kThreads) k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth,
+__global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth,
                                                              int32_t root, int32_t forced, const TreeNode* tree,
                                                              int32_t tree_nodes) {
   // one shared buffer serves the CTA variant's copy stage or the edge-centric tile
@@ -850,6 +812,13 @@ __global__ void __launch_bounds__(kThreads) k_bfs_persistent(DevGraph g, Buffers
   __shared__ alignas(128) int32_t ubuf[2 * kPeSlot];
   __shared__ alignas(8) uint64_t bar[2];
   __shared__ int s_split[2];
+  // the tree is walked by every block every level: keep it in shared memory
+  constexpr int kSmemTree = 255;
+  __shared__ TreeNode s_tree[kSmemTree];
+  const bool tree_in_smem = tree != nullptr && tree_nodes > 0 && tree_nodes <= kSmemTree;
+  if (tree_in_smem)
+    for (int i = threadIdx.x; i < tree_nodes; i += blockDim.x) s_tree[i] = tree[i];
+  const TreeNode* walk_tree = tree_in_smem ? s_tree : tree;
   BFS_DECLARE_STAGE(stage);
   init_fill(g, b.vis[0], depth, root);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -884,7 +853,7 @@ __global__ void __launch_bounds__(kThreads) k_bfs_persistent(DevGraph g, Buffers
     }
     long long x[F_NUM];
     int32_t vw = 32;
-    const int32_t v = decide_variant(g, tree, tree_nodes, forced, L, f, (long long)e, discovered, prev, x, &vw);
+    const int32_t v = decide_variant(g, walk_tree, tree_nodes, forced, L, f, (long long)e, discovered, prev, x, &vw);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->cnt3[(L + 2) % 3] = 0;  // last read by level L - 1, which every block has finished
       st->edg3[(L + 2) % 3] = 0;

@@ -3,15 +3,22 @@
 // Each vertex carries three 64-bit masks: visit (bit i: reached by root i),
 // frontier (bit i: at depth L for root i) and next (bits pushed to it during
 // the level). Every level runs one direction for all roots at once:
-//   push: every vertex with a nonzero frontier mask ORs its mask, minus the
-//         target's visited bits, into each neighbour's next mask (atomicOr),
-//         then a commit pass turns next into the new frontier;
+//   push: the vertices of the frontier list OR their frontier mask, minus the
+//         target's visited bits, into each neighbour's next mask (atomicOr);
+//         a target whose next mask leaves zero joins a touched list, and a
+//         commit pass over that list turns next into the new frontier;
 //   pull: every vertex still unvisited in some lane ORs its in-neighbours'
 //         frontier masks, stopping once every unvisited lane is found.
-// The result equals k independent single-source traversals (each lane is one
-// level-synchronous BFS from its root, Section 3.1). A warp owns 32
-// consecutive vertices in the commit and pull passes, so for each root the
-// new depths of those vertices are written as one coalesced row segment.
+// Push and commit touch only the frontier and its neighbours (so thousands of
+// small levels stay cheap); pull sweeps every vertex, a warp per 32
+// consecutive vertices, so each root's new depths are written as coalesced row
+// segments. The result equals k independent single-source traversals (each
+// lane is one level-synchronous BFS from its root, Section 3.1).
+//
+// Level L uses frontier slot L % 4 (ftail, fedges), appends to (L + 1) % 4 and
+// clears (L + 2) % 4, which every block finished reading two levels ago; the
+// previous level's list (slot (L + 3) % 4) names the masks of front[(L+1) & 1]
+// to clear before that array receives the new frontier.
 #include "bfs_msbfs.cuh"
 
 namespace bfs {
@@ -26,24 +33,15 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
   return x;
 }
 
-// Record lane masks `nb` of the warp's 32 vertices (u = w * 32 + lane) as
-// newly reached at depth d: depth rows, per-root reached-edge sums (in shared
-// memory), and the next level's frontier statistics.
-__device__ __forceinline__ void ms_record(int32_t* depth, int64_t n, int32_t u, bool valid, unsigned long long nb,
-                                          int32_t deg, int32_t d, unsigned long long* s_edges,
-                                          unsigned long long& fcount, unsigned long long& fedges) {
+// Depth rows of a warp's 32 consecutive vertices (u = w * 32 + lane) newly
+// reached in lanes nb: one coalesced masked store per root present.
+__device__ __forceinline__ void ms_depth_rows(int32_t* depth, int64_t n, int64_t u, bool valid, unsigned long long nb,
+                                              int32_t d) {
   unsigned long long any = warp_or64(valid ? nb : 0ull);
-  if (valid && nb) {
-    fcount += 1;
-    fedges += (unsigned long long)deg;
-  }
   while (any) {
     const int i = __ffsll((long long)any) - 1;
     any &= any - 1;
-    const bool has = valid && ((nb >> i) & 1ull);
-    const unsigned sum = __reduce_add_sync(kFullMask, has ? (unsigned)deg : 0u);
-    if (has) depth[(int64_t)i * n + u] = d;
-    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&s_edges[i], (unsigned long long)sum);
+    if (valid && ((nb >> i) & 1ull)) depth[(int64_t)i * n + u] = d;
   }
 }
 
@@ -52,10 +50,14 @@ __device__ __forceinline__ void ms_record(int32_t* depth, int64_t n, int32_t u, 
 __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, MsState* st, int32_t k,
                                                        int32_t* depth, MsConfig cfg) {
   __shared__ unsigned long long s_edges[64];
+  BFS_DECLARE_STAGE(stage);
   const int64_t n = g.n;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const unsigned long long act = k >= 64 ? ~0ull : ((1ull << k) - 1ull);
+  const uint32_t lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  constexpr int kWarps = kMsThreads / 32;
   for (int i = threadIdx.x; i < 64; i += blockDim.x) s_edges[i] = 0;
   // init: masks cleared, depth rows -1 (16-byte stores when aligned)
   for (int64_t v = tid; v < n; v += stride) {
@@ -75,109 +77,114 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
   }
   if (!grid_barrier(&st->bar_count, &st->bar_gen, &st->status)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // roots: level 0 frontier; a vertex repeated as several roots carries several bits
-    unsigned long long fc = 0, fe = 0;
+    // roots: the level 0 frontier; a vertex repeated as several roots carries several bits
+    unsigned int fc = 0;
+    unsigned long long fe = 0;
     for (int i = 0; i < k; ++i) {
       const int32_t r = mb.roots[i];
-      const int32_t deg = g.off[r + 1] - g.off[r];
       if (mb.visit[r] == 0) {
-        fc += 1;
-        fe += (unsigned long long)deg;
+        mb.flist[0][fc++] = r;
+        fe += (unsigned long long)(g.off[r + 1] - g.off[r]);
       }
       mb.visit[r] |= 1ull << i;
       mb.front[0][r] |= 1ull << i;
       depth[(int64_t)i * n + r] = 0;
-      st->edges[i] = (unsigned long long)deg;
     }
-    for (int i = k; i < 64; ++i) st->edges[i] = 0;
-    st->fcount[0] = fc;
+    for (int i = 0; i < 64; ++i) st->edges[i] = 0;
+    for (int s = 0; s < 4; ++s) {
+      st->ftail[s] = 0;
+      st->fedges[s] = 0;
+    }
+    st->ftail[0] = fc;
     st->fedges[0] = fe;
-    st->fcount[1] = st->fcount[2] = 0;
-    st->fedges[1] = st->fedges[2] = 0;
+    st->ttail[0] = st->ttail[1] = 0;
   }
   bool ok = grid_barrier(&st->bar_count, &st->bar_gen, &st->status);
-  const uint32_t lane = threadIdx.x & 31;
   const int64_t words = (n + 31) / 32;
-  const int64_t warp = tid >> 5;
-  const int64_t nwarps = stride >> 5;
   int32_t L = 0;
   for (; ok; ++L) {
-    const unsigned long long fc = *reinterpret_cast<volatile unsigned long long*>(&st->fcount[L % 3]);
-    const unsigned long long fe = *reinterpret_cast<volatile unsigned long long*>(&st->fedges[L % 3]);
-    if (fc == 0) break;
+    const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&st->ftail[L % 4]);
+    const unsigned int pf = *reinterpret_cast<volatile unsigned int*>(&st->ftail[(L + 3) % 4]);
+    const unsigned long long fe = *reinterpret_cast<volatile unsigned long long*>(&st->fedges[L % 4]);
+    if (f == 0) break;
     if (L > g.n) {
       if (blockIdx.x == 0 && threadIdx.x == 0) st->status = ST_TIMEOUT;
       break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st->fcount[(L + 2) % 3] = 0;
-      st->fedges[(L + 2) % 3] = 0;
+      st->ftail[(L + 2) % 4] = 0;
+      st->fedges[(L + 2) % 4] = 0;
+      st->ttail[(L + 1) % 2] = 0;
     }
     const unsigned long long* cur = (L & 1) ? mb.front[1] : mb.front[0];
     unsigned long long* nxt = (L & 1) ? mb.front[0] : mb.front[1];
+    const int32_t* list = (L & 1) ? mb.flist[1] : mb.flist[0];
+    int32_t* out_list = (L & 1) ? mb.flist[0] : mb.flist[1];  // holds level L-1's list until the commit
+    unsigned int* out_tail = &st->ftail[(L + 1) % 4];
+    unsigned long long my_fe = 0;
     // direction: pull once the frontier's edges exceed m / alpha (Beamer's rule, alpha tuned)
     const bool pull = fe * (unsigned long long)cfg.alpha > (unsigned long long)g.m;
-    unsigned long long my_fc = 0, my_fe = 0;
     if (!pull) {
+      // nxt still holds level L-1's frontier: clear exactly those masks
+      for (int64_t i = tid; i < (int64_t)pf; i += stride) nxt[out_list[i]] = 0;
+      unsigned int* ttail = &st->ttail[L % 2];
       if (cfg.push_mode == 0) {
-        // thread per frontier vertex
-        for (int64_t v = tid; v < n; v += stride) {
-          const unsigned long long f = cur[v];
-          if (!f) continue;
-          for (int32_t e = g.off[v]; e < g.off[v + 1]; ++e) {
-            const int32_t u = g.idx[e];
-            const unsigned long long nb = f & ~mb.visit[u];
-            if (nb) atomicOr(&mb.next[u], nb);
-          }
-        }
-      } else {
-        // warp per frontier vertex: the warp's lanes with work take turns, all 32 stride the list
-        for (int64_t w = warp; w < words; w += nwarps) {
-          const int64_t v0 = w * 32 + lane;
-          const unsigned long long f0 = v0 < n ? cur[v0] : 0ull;
-          unsigned int todo = __ballot_sync(kFullMask, f0 != 0ull);
-          while (todo) {
-            const int j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int32_t v = (int32_t)(w * 32 + j);
-            const unsigned long long f = __shfl_sync(kFullMask, f0, j);
-            const int32_t beg = g.off[v], end = g.off[v + 1];
-            for (int32_t e = beg + (int32_t)lane; e < end; e += 32) {
+        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < f; base += stride) {
+          const int64_t i = base + threadIdx.x;
+          if (i < f) {
+            const int32_t v = list[i];
+            const unsigned long long fv = cur[v];
+            for (int32_t e = g.off[v]; e < g.off[v + 1]; ++e) {
               const int32_t u = g.idx[e];
-              const unsigned long long nb = f & ~mb.visit[u];
-              if (nb) atomicOr(&mb.next[u], nb);
+              const unsigned long long nb = fv & ~mb.visit[u];
+              if (nb && atomicOr(&mb.next[u], nb) == 0ull) stage_put(stage, mb.tlist, ttail, u);
             }
           }
+          stage_drain(stage, mb.tlist, ttail, kStageCap / 2);
+        }
+      } else {
+        for (int64_t base = (int64_t)blockIdx.x * kWarps; base < f; base += (int64_t)gridDim.x * kWarps) {
+          const int64_t i = base + wib;
+          if (i < f) {
+            const int32_t v = list[i];
+            const unsigned long long fv = cur[v];
+            for (int32_t e = g.off[v] + (int32_t)lane; e < g.off[v + 1]; e += 32) {
+              const int32_t u = g.idx[e];
+              const unsigned long long nb = fv & ~mb.visit[u];
+              if (nb && atomicOr(&mb.next[u], nb) == 0ull) stage_put(stage, mb.tlist, ttail, u);
+            }
+          }
+          stage_drain(stage, mb.tlist, ttail, kStageCap / 2);
         }
       }
+      stage_drain(stage, mb.tlist, ttail, 1);
       ok = grid_barrier(&st->bar_count, &st->bar_gen, &st->status);
       if (!ok) break;
-      // commit: next -> new frontier, depths, statistics
-      for (int64_t w = warp; w < words; w += nwarps) {
-        const int64_t u = w * 32 + lane;
-        const bool valid = u < n;
-        unsigned long long nb = 0;
-        int32_t deg = 0;
-        if (valid) {
-          const unsigned long long nx = mb.next[u];
-          if (nx) {
-            nb = nx & ~mb.visit[u];
-            mb.visit[u] |= nb;
-            mb.next[u] = 0;
-            deg = g.off[u + 1] - g.off[u];
-          }
+      // commit the touched vertices: next -> new frontier, depths, next frontier list
+      const unsigned int t = *reinterpret_cast<volatile unsigned int*>(ttail);
+      for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < t; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        if (i < t) {
+          const int32_t u = mb.tlist[i];
+          const unsigned long long nb = mb.next[u] & ~mb.visit[u];
+          mb.next[u] = 0;
+          mb.visit[u] |= nb;
           nxt[u] = nb;
+          if (nb) {
+            my_fe += (unsigned long long)(g.off[u + 1] - g.off[u]);
+            stage_put(stage, out_list, out_tail, u);
+            for (unsigned long long m = nb; m; m &= m - 1) depth[(int64_t)(__ffsll((long long)m) - 1) * n + u] = L + 1;
+          }
         }
-        if (__any_sync(kFullMask, nb != 0ull))
-          ms_record(depth, n, (int32_t)u, valid, nb, deg, L + 1, s_edges, my_fc, my_fe);
+        stage_drain(stage, out_list, out_tail, kStageCap / 2);
       }
     } else {
       // pull: OR the in-neighbours' frontier masks until every unvisited lane is found
-      for (int64_t w = warp; w < words; w += nwarps) {
+      for (int64_t wbase = (int64_t)blockIdx.x * kWarps; wbase < words; wbase += (int64_t)gridDim.x * kWarps) {
+        const int64_t w = wbase + wib;
         const int64_t u = w * 32 + lane;
-        const bool valid = u < n;
+        const bool valid = w < words && u < n;
         unsigned long long nb = 0;
-        int32_t deg = 0;
         if (valid) {
           const unsigned long long vis = mb.visit[u];
           const unsigned long long unv = ~vis & act;
@@ -194,18 +201,36 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
             nb = acc & unv;
             if (nb) {
               mb.visit[u] = vis | nb;
-              deg = g.symmetric ? end - beg : g.off[u + 1] - g.off[u];
+              my_fe += (unsigned long long)(g.off[u + 1] - g.off[u]);
+              stage_put(stage, out_list, out_tail, (int32_t)u);
             }
           }
           nxt[u] = nb;
         }
-        if (__any_sync(kFullMask, nb != 0ull))
-          ms_record(depth, n, (int32_t)u, valid, nb, deg, L + 1, s_edges, my_fc, my_fe);
+        if (w < words) ms_depth_rows(depth, n, u, valid, nb, L + 1);
+        stage_drain(stage, out_list, out_tail, kStageCap - kMsThreads);
       }
     }
-    block_add_u64(my_fc, &st->fcount[(L + 1) % 3]);
-    block_add_u64(my_fe, &st->fedges[(L + 1) % 3]);
+    stage_drain(stage, out_list, out_tail, 1);
+    block_add_u64(my_fe, &st->fedges[(L + 1) % 4]);
     ok = grid_barrier(&st->bar_count, &st->bar_gen, &st->status);
+  }
+  // per-root reached-edge counts: for each root, the sum of out-degrees of the
+  // vertices whose visit mask carries its bit
+  for (int64_t wbase = (int64_t)blockIdx.x * kWarps; wbase < words; wbase += (int64_t)gridDim.x * kWarps) {
+    const int64_t w = wbase + wib;
+    if (w >= words) continue;  // whole warp
+    const int64_t u = w * 32 + lane;
+    const bool valid = u < n;
+    const unsigned long long vis = valid ? mb.visit[u] : 0ull;
+    const unsigned deg = valid ? (unsigned)(g.off[u + 1] - g.off[u]) : 0u;
+    unsigned long long any = warp_or64(vis);
+    while (any) {
+      const int i = __ffsll((long long)any) - 1;
+      any &= any - 1;
+      const unsigned s = __reduce_add_sync(kFullMask, ((vis >> i) & 1ull) ? deg : 0u);
+      if (lane == 0 && s) atomicAdd(&s_edges[i], (unsigned long long)s);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < k; i += blockDim.x)

@@ -9,8 +9,10 @@ constexpr int kMsThreads = 256;
 
 struct MsBuffers {
   unsigned long long* visit;     // n masks: bit i = reached by root i
-  unsigned long long* front[2];  // n masks each: bit i = at depth L (read) / L + 1 (write) for root i
-  unsigned long long* next;      // n masks: bits pushed to the vertex during a push level
+  unsigned long long* front[2];  // n masks each: bit i = in root i's frontier (nonzero only on frontier vertices)
+  unsigned long long* next;      // n masks: bits pushed to the vertex during a push level (zero between levels)
+  int32_t* flist[2];             // frontier vertex lists (any lane), for level L in flist[L & 1]
+  int32_t* tlist;                // vertices whose next mask became nonzero during a push level
   const int32_t* roots;          // device copy of the wave's roots
 };
 
@@ -19,9 +21,10 @@ struct MsState {
   unsigned int bar_gen;
   int32_t status;
   int32_t levels;
-  unsigned long long fcount[3];  // frontier vertices (any lane) per level, indexed by level % 3
-  unsigned long long fedges[3];  // their out-degree sum
-  unsigned long long edges[64];  // reached-edge count per root
+  unsigned int ftail[4];           // frontier list length (= frontier vertices) of level L in slot L % 4
+  unsigned int ttail[2];           // touched list length of a push level L in slot L % 2
+  unsigned long long fedges[4];    // out-degree sum of level L's frontier, slot L % 4
+  unsigned long long edges[64];    // reached-edge count per root
 };
 
 struct MsConfig {

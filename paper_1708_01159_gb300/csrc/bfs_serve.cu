@@ -9,9 +9,9 @@
 // the same graph are merged into one multi-source wave (up to merge_batch
 // roots, one bit each in 64-bit masks). Completion is observed by polling a
 // CUDA event per admitted unit; latency runs from submission to that
-// observation. Single queries use the CUDA-graph driver, whose ordinary
-// kernels from several streams can share the GPU (cooperative launches would
-// serialise).
+// observation. Single queries use the persistent driver on one block per SM
+// (a quarter of a full cooperative grid), so up to four traversals are
+// resident together; a full grid each would serialise them.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -60,6 +60,7 @@ struct Unit {  // one admitted launch: a single query or a merged wave
 struct bfs_server {
   bfs_serve_config cfg{};
   int device = 0;
+  int32_t query_blocks = 0;  // blocks of one single-query persistent traversal (one per SM)
   std::vector<bfs_graph*> graphs;
   std::vector<cudaStream_t> streams;
   size_t next_stream = 0;
@@ -133,7 +134,7 @@ int launch_unit(bfs_server* s, Unit& u) {
       }
       u.scratch = out;
     }
-    int rc = bfs::run_async(g, r.root, out, u.stream, BFS_MODE_GRAPH, u.edges);
+    int rc = bfs::run_async(g, r.root, out, u.stream, BFS_MODE_PERSISTENT, u.edges, s->query_blocks);
     if (rc != BFS_OK) return rc;
   } else {
     int32_t roots[64];
@@ -307,7 +308,8 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out) {
   s->free_depth.reserve(kMaxGraphs);
   s->wave_staging.reserve(kMaxGraphs);
   s->wave_busy.reserve(kMaxGraphs);
-  if (cudaGetDevice(&s->device) != cudaSuccess) {
+  if (cudaGetDevice(&s->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&s->query_blocks, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
     delete s;
     return bfs::set_error_detail(BFS_ERR_CUDA, "cudaGetDevice failed");
   }

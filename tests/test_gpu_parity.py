@@ -272,6 +272,36 @@ def test_concurrent_streams():
         assert G.info()["num_workspaces"] >= 1
 
 
+@pytest.mark.parametrize("mode", [bfs.MODE_PERSISTENT, bfs.MODE_GRAPH, bfs.MODE_HOST_LOOP])
+def test_many_streams_mixed_graphs(mode):
+    """400 traversals over four graphs spread round-robin over 16 streams, all
+    enqueued before any finishes: every output equals the run alone."""
+    gs = [gg.rmat(14, 16, seed=501), gg.grid(120, 90, 0.1, seed=502), gg.erdos_renyi(30000, 6.0, seed=503),
+          gg.rmat(12, 8, seed=504, permute=True)]
+    Gs = [make(g) for g in gs]
+    try:
+        rng = np.random.default_rng(1)
+        streams = [torch.cuda.Stream() for _ in range(16)]
+        plan = []
+        for q in range(400 if mode != bfs.MODE_HOST_LOOP else 64):
+            gi = int(rng.integers(0, 4))
+            r = int(gg.sample_roots(gs[gi], 1, seed=q)[0])
+            plan.append((gi, r, torch.full((gs[gi].n,), -7, dtype=torch.int32, device="cuda")))
+        want = {}
+        for gi, r, _ in plan:
+            if (gi, r) not in want:
+                want[(gi, r)] = oracle.bfs(gs[gi].off, gs[gi].idx, r).depth
+        torch.cuda.synchronize()
+        for q, (gi, r, out) in enumerate(plan):
+            bfs.bfs_run_ex(Gs[gi].handle, r, out, streams[q % 16], mode=mode)
+        torch.cuda.synchronize()
+        bad = [q for q, (gi, r, out) in enumerate(plan) if not np.array_equal(out.cpu().numpy(), want[(gi, r)])]
+        assert not bad, f"{len(bad)} of {len(plan)} traversals wrong (first: {bad[:5]})"
+    finally:
+        for G in Gs:
+            G.close()
+
+
 def test_batch_equals_single_runs():
     g = gg.rmat(12, 16, seed=71)
     roots = gg.sample_roots(g, 70, seed=10)  # more than one wave of 64
@@ -284,13 +314,16 @@ def test_batch_equals_single_runs():
         assert np.array_equal(edges, E)
 
 
+@pytest.mark.parametrize("which", ["rmat", "grid"])
 @pytest.mark.parametrize("push_mode", [0, 1])
 @pytest.mark.parametrize("alpha", [1, 8, 1 << 20])
-def test_batch_configs(push_mode, alpha):
+def test_batch_configs(which, push_mode, alpha):
     """Multi-source BFS in every configuration (alpha 1: pull from level 1 on;
     huge alpha: push only) equals independent oracle runs, repeated and isolated
-    roots included."""
-    g = gg.rmat(12, 8, seed=91)
+    roots included, on a skewed graph and on a high-diameter grid."""
+    g = gg.rmat(12, 8, seed=91) if which == "rmat" else gg.grid(70, 60, 0.15, seed=92)
+    if which == "grid":  # an isolated vertex for the isolated-root case
+        g = gg.Graph(np.concatenate([g.off, [g.m]]).astype(np.int32), g.idx, "grid+isolated")
     iso = int(np.nonzero(g.degrees() == 0)[0][0])
     roots = np.concatenate([gg.sample_roots(g, 40, seed=12), [iso, iso], gg.sample_roots(g, 3, seed=12)])
     D, E = oracle.bfs_batch(g.off, g.idx, roots)
