@@ -54,6 +54,8 @@ def parse_args():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--serve-rates", default="1000,4000,16000", help="offered loads (queries/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--mode", default="default", choices=["default", "persistent", "graph", "host_loop"],
+                   help="level-loop driver of the timed switched runs (host_loop: every kernel visible to profilers)")
     return p.parse_args()
 
 
@@ -372,7 +374,11 @@ def run_ours(args):
     for r in roots:
         st = bfs.bfs_run_ex(G.handle, int(r), depth[0], stats=True, log_capacity=4096)
         edges.append(st["edges_reached"])
-        launches += 2  # default mode on GB300: state reset + one cooperative persistent kernel per traversal
+        if args.mode in ("default", "persistent"):
+            launches += 2  # state reset + one cooperative persistent kernel per traversal
+        else:  # init, (graph: loop start), per level decide + the variant's kernels, final decide
+            kern = {0: 1, 1: 1, 2: 1, 3: 4, 4: 1}
+            launches += 2 + (args.mode == "graph") + sum(1 + kern[int(v)] for v in st["variant"])
     edges = np.array(edges, dtype=np.int64)
 
     def step(forced=-1, mode=bfs.MODE_DEFAULT):
@@ -394,14 +400,15 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
+    main_mode = bfs.MODES[args.mode]
     for _ in range(args.warmup):
-        step()
+        step(-1, main_mode)
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     barrier()
     torch.cuda.synchronize()
-    all_evs = [step() for _ in range(args.steps)]
+    all_evs = [step(-1, main_mode) for _ in range(args.steps)]
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
@@ -428,7 +435,10 @@ def run_ours(args):
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": workload_name(args, g), "roots": R,
                    "switching": "decision tree evaluated on the device every level",
-                   "mode": "persistent cooperative kernel per traversal (grid barrier between levels)",
+                   "mode": {"default": "persistent cooperative kernel per traversal (grid barrier between levels)",
+                            "persistent": "persistent cooperative kernel per traversal (grid barrier between levels)",
+                            "graph": "CUDA graph with WHILE and SWITCH conditional nodes",
+                            "host_loop": "host-driven level loop (one launch per kernel)"}[args.mode],
                    "l2": "inputs larger than L2 (CSR %.0f MB vs 129 MB L2)" % ((g.off.nbytes + g.idx.nbytes) / 1e6),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "gpu_launches": launches * args.steps,

@@ -21,6 +21,8 @@ def main():
     p.add_argument("--seed", type=int, default=1001)
     p.add_argument("--roots", type=int, default=2)
     p.add_argument("--variant", type=int, default=-1)
+    p.add_argument("--mode", default="host_loop", choices=["default", "persistent", "graph", "host_loop"],
+                   help="host_loop launches every level kernel on its own, which profilers can capture")
     a = p.parse_args()
     import torch
 
@@ -32,7 +34,8 @@ def main():
     with bfs.Graph(g.off, g.idx) as G:
         depth = torch.empty(g.n, dtype=torch.int32, device="cuda")
         for r in roots:
-            st = bfs.bfs_run_ex(G.handle, int(r), depth, forced_variant=a.variant, stats=True, log_capacity=64)
+            st = bfs.bfs_run_ex(G.handle, int(r), depth, forced_variant=a.variant, stats=True, log_capacity=64,
+                                mode=bfs.MODES[a.mode])
             names = [bfs.VARIANTS[v] for v in st["variant"]]
             print(f"root {int(r)}: levels {st['levels']} edges {st['edges_reached']} schedule {names}")
 
