@@ -502,6 +502,11 @@ def run_ours(args):
                             "per_level_ms_chosen": [round(float(x), 4) for x in chosen],
                             "per_level_optimal_ms": float(ms.min(axis=1).sum()),
                             "per_level_tree_ms": float(chosen.sum())}
+        # the same traversal inside the real drivers: device timestamps per level
+        for name, mode in (("persistent", bfs.MODE_PERSISTENT), ("graph", bfs.MODE_GRAPH)):
+            st = bfs.bfs_run_ex(G.handle, r0, depth[0], stream, stats=True, log_capacity=64, mode=mode)
+            if "level_ns" in st:
+                line["roofline"][f"per_level_ms_in_{name}"] = [round(float(x) / 1e6, 4) for x in st["level_ns"]]
 
     G.close()
     del depth

@@ -116,6 +116,8 @@ typedef struct bfs_run_stats {
   int32_t* log_variant;      /* host, log_capacity entries */
   int64_t* log_frontier;     /* host, vertices in the frontier of level L */
   int64_t* log_frontier_edges; /* host, sum of out-degrees over that frontier */
+  int64_t* log_time_ns;      /* host, log_capacity + 1 entries: device %globaltimer (ns) at the start
+                                of level L, and entry [levels] at the end (graph and persistent drivers) */
 } bfs_run_stats;
 
 /* Text of a status code (static storage). */

@@ -74,7 +74,7 @@ class _Stats(ctypes.Structure):
     _fields_ = [("edges_reached", ctypes.c_int64), ("vertices_reached", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("log_capacity", ctypes.c_int32),
                 ("log_variant", ctypes.POINTER(ctypes.c_int32)), ("log_frontier", ctypes.POINTER(ctypes.c_int64)),
-                ("log_frontier_edges", ctypes.POINTER(ctypes.c_int64))]
+                ("log_frontier_edges", ctypes.POINTER(ctypes.c_int64)), ("log_time_ns", ctypes.POINTER(ctypes.c_int64))]
 
 
 class _ServeConfig(ctypes.Structure):
@@ -252,11 +252,12 @@ def bfs_run_ex(g: int, root: int, depth_out, stream=None, forced_variant: int = 
         st = _Stats()
         if log_capacity > 0:
             logs = (np.zeros(log_capacity, np.int32), np.zeros(log_capacity, np.int64),
-                    np.zeros(log_capacity, np.int64))
+                    np.zeros(log_capacity, np.int64), np.zeros(log_capacity + 1, np.int64))
             st.log_capacity = log_capacity
             st.log_variant = logs[0].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
             st.log_frontier = logs[1].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
             st.log_frontier_edges = logs[2].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+            st.log_time_ns = logs[3].ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     _check(lib().bfs_run_ex(g, int(root), p, _stream(stream), ctypes.byref(opts),
                             ctypes.byref(st) if st is not None else None), "bfs_run_ex")
     if st is None:
@@ -268,6 +269,9 @@ def bfs_run_ex(g: int, root: int, depth_out, stream=None, forced_variant: int = 
         out["variant"] = logs[0][:k].copy()
         out["frontier"] = logs[1][:k].copy()
         out["frontier_edges"] = logs[2][:k].copy()
+        # per-level device time (ns) from the start stamps (graph and persistent drivers)
+        if st.levels < log_capacity + 1 and mode != MODE_HOST_LOOP:
+            out["level_ns"] = np.diff(logs[3][: st.levels + 1])
     return out
 
 

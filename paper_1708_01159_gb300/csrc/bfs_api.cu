@@ -161,6 +161,7 @@ struct Workspace {
   int32_t* log_variant = nullptr;
   long long* log_frontier = nullptr;
   long long* log_edges = nullptr;
+  long long* log_time = nullptr;
   int32_t log_cap = 0;
   int32_t* host_depth_stage = nullptr;  // device buffer for runs whose output is host memory
   cudaGraph_t graph = nullptr;
@@ -319,6 +320,7 @@ int build_graph(bfs_graph* g, Workspace* ws) {
   init.log_variant = ws->log_variant;
   init.log_frontier = ws->log_frontier;
   init.log_edges = ws->log_edges;
+  init.log_time = ws->log_time;
   CU(cudaMemcpy(ws->st, &init, sizeof init, cudaMemcpyHostToDevice));
   return BFS_OK;
 }
@@ -348,6 +350,7 @@ int create_workspace(bfs_graph* g, Workspace** out) {
   ws->log_variant = static_cast<int32_t*>(A(ws->log_cap * 4));
   ws->log_frontier = static_cast<long long*>(A(ws->log_cap * 8));
   ws->log_edges = static_cast<long long*>(A(ws->log_cap * 8));
+  ws->log_time = static_cast<long long*>(A(ws->log_cap * 8));
   ws->host_depth_stage = static_cast<int32_t*>(A(n * 4));
   if (r == BFS_OK) {
     cudaError_t e = cudaEventCreateWithFlags(&ws->done, cudaEventDisableTiming);
@@ -904,6 +907,10 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
           e = cudaMemcpy(stats->log_frontier, ws->log_frontier, cnt * 8, cudaMemcpyDeviceToHost);
         if (e == cudaSuccess && stats->log_frontier_edges)
           e = cudaMemcpy(stats->log_frontier_edges, ws->log_edges, cnt * 8, cudaMemcpyDeviceToHost);
+        // level start stamps plus the end stamp (entry `levels`) when it fits
+        const int32_t tcnt = std::min(std::min(hs.levels + 1, ws->log_cap), stats->log_capacity + 1);
+        if (e == cudaSuccess && stats->log_time_ns)
+          e = cudaMemcpy(stats->log_time_ns, ws->log_time, tcnt * 8, cudaMemcpyDeviceToHost);
       }
     }
     if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "stats: %s", cudaGetErrorString(e));

@@ -100,6 +100,7 @@ struct RunState {
   int32_t* log_variant;
   long long* log_frontier;
   long long* log_edges;
+  long long* log_time;  // %globaltimer (ns) at the start of level L; entry `levels` marks the end
 };
 
 struct Buffers {

@@ -686,6 +686,7 @@ __global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
   // a traversal has at most n nonempty levels; more means corrupted state, so
   // end the loop with an error instead of iterating on
   if (L > g.n || s.discovered > g.n) s.status = ST_TIMEOUT;
+  if (L < s.log_cap) s.log_time[L] = (long long)global_ns();
   if (f == 0 || s.status != ST_OK) {
     s.levels = L;
     if (s.use_handles) {
@@ -861,6 +862,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
         st->log_variant[L] = v;
         st->log_frontier[L] = f;
         st->log_edges[L] = (long long)e;
+        st->log_time[L] = (long long)global_ns();
       }
     }
     Level lv;
@@ -896,6 +898,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->levels = L;
+    if (L < st->log_cap) st->log_time[L] = (long long)global_ns();
     st->discovered = discovered;
     st->edges_reached = reached;
   }
