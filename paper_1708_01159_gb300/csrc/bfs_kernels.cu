@@ -572,51 +572,79 @@ __device__ void body_pe_expand(const DevGraph& g, const Level& lv, const Buffers
 // (graph and host-loop drivers); the persistent kernel passes false.
 // ---------------------------------------------------------------------------
 template <bool kReadOnlyCache>
+__device__ __forceinline__ uint32_t vis_bit(const uint32_t* vis, int32_t u) {
+  const uint32_t word = kReadOnlyCache ? ld_nc_u32(vis + (u >> 5)) : vis[u >> 5];
+  return (word >> (u & 31)) & 1u;
+}
+
+// A warp takes two bitmap words (kPullWords x 32 vertices) per step and each
+// lane interleaves the scans of its two vertices, four in-neighbours of each
+// per round, so twice as many independent loads are in flight per thread as
+// with one vertex per lane (the scan is a chain of dependent loads: row
+// extent, adjacency entries, bitmap words).
+constexpr int kPullWords = 2;
+
+template <bool kReadOnlyCache>
 __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
   const uint32_t* cur_vis = lv.vis;
   uint32_t* nxt_vis = lv.vis_next;
   const uint32_t lane = lane_id();
   constexpr int kWarps = kThreads / 32;
   const int wib = threadIdx.x >> 5;
-  for (int wbase = blockIdx.x * kWarps; wbase < g.words; wbase += gridDim.x * kWarps) {
-    const int w = wbase + wib;
-    if (w < g.words) {
-      const uint32_t cw = cur_vis[w];
-      uint32_t fm = 0;
-      if (cw != kFull) {
-        const int32_t v = w * 32 + (int32_t)lane;
-        bool found = false;
-        int32_t deg = 0;
-        if (v < g.n && !((cw >> lane) & 1u)) {
-          const int32_t beg = g.in_off[v], end = g.in_off[v + 1];
-          for (int32_t e = beg; e < end; e += 4) {
-            const int nv = min(4, end - e);
-            int32_t u[4];
+  for (int wbase = blockIdx.x * kWarps * kPullWords; wbase < g.words; wbase += gridDim.x * kWarps * kPullWords) {
+    int32_t w[kPullWords], v[kPullWords], pos[kPullWords], beg[kPullWords], end[kPullWords];
+    uint32_t cw[kPullWords];
+    bool active[kPullWords], found[kPullWords];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) u[k] = g.in_idx[k < nv ? e + k : e];
-            uint32_t hit = 0;
+    for (int j = 0; j < kPullWords; ++j) {
+      w[j] = wbase + j * kWarps + wib;  // consecutive warps take consecutive words
+      cw[j] = w[j] < g.words ? cur_vis[w[j]] : kFull;
+      v[j] = w[j] * 32 + (int32_t)lane;
+      active[j] = cw[j] != kFull && v[j] < g.n && !((cw[j] >> lane) & 1u);
+      found[j] = false;
+      beg[j] = end[j] = 0;
+      if (active[j]) {
+        beg[j] = g.in_off[v[j]];
+        end[j] = g.in_off[v[j] + 1];
+      }
+      pos[j] = beg[j];
+      active[j] = active[j] && beg[j] < end[j];
+    }
+    while (active[0] || active[1]) {
+      int32_t u[kPullWords][4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const uint32_t word = kReadOnlyCache ? ld_nc_u32(cur_vis + (u[k] >> 5)) : cur_vis[u[k] >> 5];
-              hit |= (word >> (u[k] & 31)) & 1u;
-            }
-            if (hit) {
-              found = true;
-              break;
-            }
-          }
-          if (found) deg = g.symmetric ? end - beg : g.off[v + 1] - g.off[v];
-        }
-        fm = __ballot_sync(kFull, found);
-        if (found) {
-          lv.depth[v] = lv.next_depth;
-          edges += (unsigned long long)deg;
-          stage_push(stage, lv, v);
+      for (int j = 0; j < kPullWords; ++j) {
+        const int nv = active[j] ? min(4, end[j] - pos[j]) : 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u[j][k] = nv ? g.in_idx[k < nv ? pos[j] + k : pos[j]] : 0;
+      }
+#pragma unroll
+      for (int j = 0; j < kPullWords; ++j) {
+        if (!active[j]) continue;
+        uint32_t hit = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) hit |= vis_bit<kReadOnlyCache>(cur_vis, u[j][k]);
+        pos[j] += 4;
+        if (hit) {
+          found[j] = true;
+          active[j] = false;
+        } else if (pos[j] >= end[j]) {
+          active[j] = false;
         }
       }
-      if (lane == 0) nxt_vis[w] = cw | fm;
     }
-    stage_flush(stage, lv, kStageCap - kThreads);
+#pragma unroll
+    for (int j = 0; j < kPullWords; ++j) {
+      const uint32_t fm = __ballot_sync(kFull, found[j]);
+      if (found[j]) {
+        const int32_t deg = g.symmetric ? end[j] - beg[j] : g.off[v[j] + 1] - g.off[v[j]];
+        lv.depth[v[j]] = lv.next_depth;
+        edges += (unsigned long long)deg;
+        stage_push(stage, lv, v[j]);
+      }
+      if (lane == 0 && w[j] < g.words) nxt_vis[w[j]] = cw[j] | fm;
+    }
+    stage_flush(stage, lv, kStageCap - kPullWords * kThreads);
   }
 }
 
