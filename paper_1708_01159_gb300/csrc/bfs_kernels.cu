@@ -577,28 +577,56 @@ __device__ __forceinline__ uint32_t vis_bit(const uint32_t* vis, int32_t u) {
   return (word >> (u & 31)) & 1u;
 }
 
-// A warp takes two bitmap words (kPullWords x 32 vertices) per step and each
-// lane interleaves the scans of its two vertices, four in-neighbours of each
-// per round, so twice as many independent loads are in flight per thread as
-// with one vertex per lane (the scan is a chain of dependent loads: row
-// extent, adjacency entries, bitmap words).
-constexpr int kPullWords = 2;
+// A warp takes kWords bitmap words (kWords x 32 vertices) per step and each
+// lane interleaves the scans of its kWords vertices, four in-neighbours of each
+// per round, so kWords times as many independent loads are in flight per
+// thread as with one vertex per lane (a scan is a chain of dependent loads:
+// row extent, adjacency entries, bitmap words). The bitmap words of the next
+// step are loaded at the start of the current one. Found vertices go to a
+// warp-private slice of the block stage, flushed by the warp alone (one queue
+// atomic per slice), so warps never wait for one another inside the level.
+constexpr int kPullWordsLaunch = 2;      // k_pull
+constexpr int kPullWordsPersistent = 2;  // pull level of the persistent kernel
+constexpr int kWarpStage = kStageCap / (kThreads / 32);
+static_assert(kStageCap % (kThreads / 32) == 0, "stage slices");
 
-template <bool kReadOnlyCache>
+__device__ __forceinline__ void warp_stage_flush(int32_t* wbuf, unsigned int cnt, const Level& lv) {
+  __syncwarp();
+  unsigned int base = 0;
+  if (lane_id() == 0) base = atomicAdd(lv.tail, cnt);
+  base = __shfl_sync(kFull, base, 0);
+  for (unsigned int i = lane_id(); i < cnt; i += 32) lv.qout[base + i] = wbuf[i];
+  __syncwarp();
+}
+
+template <bool kReadOnlyCache, int kWords>
 __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
+  static_assert(kWords * 32 <= kWarpStage, "a step must fit a stage slice");
   const uint32_t* cur_vis = lv.vis;
   uint32_t* nxt_vis = lv.vis_next;
   const uint32_t lane = lane_id();
   constexpr int kWarps = kThreads / 32;
   const int wib = threadIdx.x >> 5;
-  for (int wbase = blockIdx.x * kWarps * kPullWords; wbase < g.words; wbase += gridDim.x * kWarps * kPullWords) {
-    int32_t w[kPullWords], v[kPullWords], pos[kPullWords], beg[kPullWords], end[kPullWords];
-    uint32_t cw[kPullWords];
-    bool active[kPullWords], found[kPullWords];
+  int32_t* wbuf = stage.buf + wib * kWarpStage;  // the block stage is empty on entry
+  unsigned int wcnt = 0;
+  const int stride = gridDim.x * kWarps * kWords;
+  uint32_t cw_next[kWords];
 #pragma unroll
-    for (int j = 0; j < kPullWords; ++j) {
+  for (int j = 0; j < kWords; ++j) {
+    const int wn = blockIdx.x * kWarps * kWords + j * kWarps + wib;
+    cw_next[j] = wn < g.words ? cur_vis[wn] : kFull;
+  }
+  for (int wbase = blockIdx.x * kWarps * kWords; wbase < g.words; wbase += stride) {
+    int32_t w[kWords], v[kWords], pos[kWords], beg[kWords], end[kWords];
+    uint32_t cw[kWords];
+    bool active[kWords], found[kWords];
+    bool any = false;
+#pragma unroll
+    for (int j = 0; j < kWords; ++j) {
       w[j] = wbase + j * kWarps + wib;  // consecutive warps take consecutive words
-      cw[j] = w[j] < g.words ? cur_vis[w[j]] : kFull;
+      cw[j] = cw_next[j];
+      const int wn = w[j] + stride;
+      cw_next[j] = wn < g.words ? cur_vis[wn] : kFull;
       v[j] = w[j] * 32 + (int32_t)lane;
       active[j] = cw[j] != kFull && v[j] < g.n && !((cw[j] >> lane) & 1u);
       found[j] = false;
@@ -609,17 +637,19 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
       }
       pos[j] = beg[j];
       active[j] = active[j] && beg[j] < end[j];
+      any = any || active[j];
     }
-    while (active[0] || active[1]) {
-      int32_t u[kPullWords][4];
+    while (any) {
+      int32_t u[kWords][4];
 #pragma unroll
-      for (int j = 0; j < kPullWords; ++j) {
+      for (int j = 0; j < kWords; ++j) {
         const int nv = active[j] ? min(4, end[j] - pos[j]) : 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) u[j][k] = nv ? g.in_idx[k < nv ? pos[j] + k : pos[j]] : 0;
       }
+      any = false;
 #pragma unroll
-      for (int j = 0; j < kPullWords; ++j) {
+      for (int j = 0; j < kWords; ++j) {
         if (!active[j]) continue;
         uint32_t hit = 0;
 #pragma unroll
@@ -631,21 +661,27 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
         } else if (pos[j] >= end[j]) {
           active[j] = false;
         }
+        any = any || active[j];
       }
     }
 #pragma unroll
-    for (int j = 0; j < kPullWords; ++j) {
+    for (int j = 0; j < kWords; ++j) {
       const uint32_t fm = __ballot_sync(kFull, found[j]);
       if (found[j]) {
         const int32_t deg = g.symmetric ? end[j] - beg[j] : g.off[v[j] + 1] - g.off[v[j]];
         lv.depth[v[j]] = lv.next_depth;
         edges += (unsigned long long)deg;
-        stage_push(stage, lv, v[j]);
+        wbuf[wcnt + __popc(fm & lanemask_lt())] = v[j];
       }
+      wcnt += (unsigned)__popc(fm);
       if (lane == 0 && w[j] < g.words) nxt_vis[w[j]] = cw[j] | fm;
     }
-    stage_flush(stage, lv, kStageCap - kPullWords * kThreads);
+    if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
+      warp_stage_flush(wbuf, wcnt, lv);
+      wcnt = 0;
+    }
   }
+  if (wcnt) warp_stage_flush(wbuf, wcnt, lv);
 }
 
 }  // namespace
@@ -799,7 +835,7 @@ __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunSta
   BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(b, st);
   unsigned long long edges = 0;
-  body_pull<true>(g, lv, stage, edges);
+  body_pull<true, kPullWordsLaunch>(g, lv, stage, edges);
   stage_flush(stage, lv, 1);
   block_add_u64(edges, &st->next_edges);
 }
@@ -916,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
         if (!grid_sync(st)) break;
         body_pe_expand(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
         break;
-      default: body_pull<false>(g, lv, stage, edges); break;
+      default: body_pull<false, kPullWordsPersistent>(g, lv, stage, edges); break;
     }
     stage_flush(stage, lv, 1);
     block_add_u64(edges, &st->edg3[(L + 1) % 3]);
