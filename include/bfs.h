@@ -91,9 +91,8 @@ typedef struct bfs_graph_info {
 enum bfs_mode {
   BFS_MODE_DEFAULT = 0,    /* persistent when the device supports cooperative launch, else graph */
   BFS_MODE_PERSISTENT = 1, /* one cooperative kernel for the whole traversal; levels separated by a grid barrier */
-  BFS_MODE_GRAPH = 2,      /* one CUDA graph: WHILE node over levels, SWITCH node over variant kernels;
-                              graph-mode traversals are ordered one after another on the device, even
-                              across streams (concurrent level-loop graphs proved unreliable) */
+  BFS_MODE_GRAPH = 2,      /* one CUDA graph per workspace: WHILE node over levels, SWITCH node over
+                              the variant kernels; runs on different streams overlap */
   BFS_MODE_HOST_LOOP = 3,  /* the graph's kernels launched level by level from the host (for profilers) */
 };
 

@@ -223,6 +223,21 @@ int grid_for(const void* func, int sms, int cap_per_sm) {
   return sms * per_sm;
 }
 
+// Host-to-device copy that has reached the device when it returns. A plain
+// cudaMemcpy from pageable memory may return once the source is staged, before
+// its DMA lands, and a kernel launched next on a non-blocking stream is not
+// ordered after that DMA: it could read the old contents, or have its own
+// writes overwritten when the DMA lands.
+int upload_now(void* dst, const void* src, size_t bytes) {
+  cudaStream_t s;
+  CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "upload of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  return BFS_OK;
+}
+
 void free_workspace(Workspace* ws) {
   if (!ws) return;
   if (ws->exec) cudaGraphExecDestroy(ws->exec);
@@ -321,8 +336,7 @@ int build_graph(bfs_graph* g, Workspace* ws) {
   init.log_frontier = ws->log_frontier;
   init.log_edges = ws->log_edges;
   init.log_time = ws->log_time;
-  CU(cudaMemcpy(ws->st, &init, sizeof init, cudaMemcpyHostToDevice));
-  return BFS_OK;
+  return upload_now(ws->st, &init, sizeof init);
 }
 
 int create_workspace(bfs_graph* g, Workspace** out) {
@@ -415,10 +429,10 @@ int sync_tree(bfs_graph* g) {
   if (g->tree_version == ts.version && g->tree) return BFS_OK;
   void* p = nullptr;
   TRY(dmalloc(&p, ts.nodes.size() * sizeof(TreeNode)));
-  cudaError_t e = cudaMemcpy(p, ts.nodes.data(), ts.nodes.size() * sizeof(TreeNode), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
+  const int r = upload_now(p, ts.nodes.data(), ts.nodes.size() * sizeof(TreeNode));
+  if (r != BFS_OK) {
     cudaFree(p);
-    return fail(BFS_ERR_CUDA, "tree upload: %s", cudaGetErrorString(e));
+    return r;
   }
   g->trees.push_back(static_cast<TreeNode*>(p));
   g->tree = static_cast<TreeNode*>(p);
@@ -429,25 +443,11 @@ int sync_tree(bfs_graph* g) {
 
 int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s);
 
-// Graph-driver traversals run one after another on each device, whatever their
-// streams: with several level-loop graphs (different workspaces) executing at
-// once, about 1 % of runs found their WHILE loop not entered (init written, no
-// level run) on CUDA 13.0 / driver 580, while the same runs alone, one stream,
-// or the persistent driver under the same load were always exact. A per-device
-// gate event orders every graph-driver launch after the previous one.
-std::mutex g_gate_mu;
-cudaEvent_t g_gate[64] = {};
-
 int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
-  std::lock_guard<std::mutex> lk(g_gate_mu);
-  cudaEvent_t& gate = g_gate[g->device & 63];
-  if (!gate) CU(cudaEventCreateWithFlags(&gate, cudaEventDisableTiming));
-  CU(cudaStreamWaitEvent(stream, gate, 0));
   k_init<<<g->shapes.init, kThreads, 0, stream>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes,
                                                   1);
   CU(cudaGetLastError());
   CU(cudaGraphLaunch(ws->exec, stream));
-  CU(cudaEventRecord(gate, stream));
   return BFS_OK;
 }
 
@@ -541,8 +541,7 @@ int ms_prepare(bfs_graph* g) {
     r = fail(BFS_ERR_CUDA, "cudaEventCreate");
   if (r == BFS_OK) {
     MsState init{};
-    if (cudaMemcpy(p[5], &init, sizeof init, cudaMemcpyHostToDevice) != cudaSuccess)
-      r = fail(BFS_ERR_CUDA, "batch state init");
+    r = upload_now(p[5], &init, sizeof init);
   }
   int per_sm = 0;
   if (r == BFS_OK) {

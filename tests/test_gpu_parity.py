@@ -296,7 +296,17 @@ def test_many_streams_mixed_graphs(mode):
             bfs.bfs_run_ex(Gs[gi].handle, r, out, streams[q % 16], mode=mode)
         torch.cuda.synchronize()
         bad = [q for q, (gi, r, out) in enumerate(plan) if not np.array_equal(out.cpu().numpy(), want[(gi, r)])]
-        assert not bad, f"{len(bad)} of {len(plan)} traversals wrong (first: {bad[:5]})"
+        detail = []
+        for q in bad[:3]:
+            gi, r, out = plan[q]
+            o, e = out.cpu().numpy(), want[(gi, r)]
+            dif = np.nonzero(o != e)[0]
+            pairs = sorted(set(zip(e[dif].tolist(), o[dif].tolist())))[:8]
+            _, st = run(Gs[gi], r, log=64, mode=mode)
+            detail.append(f"q={q} graph={gi} root={r} stream={q % 16}: {len(dif)} depths differ, unreached "
+                          f"{int((o == -1).sum())} vs {int((e == -1).sum())}, untouched {int((o == -7).sum())}, "
+                          f"(want, got) {pairs}; schedule alone {st['variant'].tolist()}")
+        assert not bad, f"{len(bad)} of {len(plan)} traversals wrong: " + " | ".join(detail)
     finally:
         for G in Gs:
             G.close()
