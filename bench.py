@@ -187,11 +187,12 @@ def algorithmic_bytes(g, depth, feats, L, variant):
     if variant != 4:  # push: queue read, row extents, adjacency, depth + queue writes, degree of new vertices
         e = int(feats[L][F_FE])
         return 4 * f + 8 * f + 4 * e + 4 * nxt + 4 * nxt + 8 * nxt
-    # pull: bitmap words read/written, row extents of unvisited vertices, the
-    # adjacency entries scanned up to the first frontier neighbour, writes
+    # pull: bitmap words read/written, row extents of unvisited vertices that
+    # have in-edges (the others start visited), the adjacency entries scanned
+    # up to the first frontier neighbour, writes
     words = (n + 31) // 32
-    unvis = (depth < 0) | (depth > L)
     deg = np.diff(g.off.astype(np.int64))
+    unvis = ((depth < 0) | (depth > L)) & (deg > 0)
     hit = depth[g.idx] == L
     pos = np.arange(g.m, dtype=np.int64)
     cand = np.where(hit, pos, np.int64(g.m + 1))

@@ -781,6 +781,15 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
       return r;
     }
   }
+  // starting bitmap: isolated vertices are marked visited up front
+  uint32_t* vis_init = nullptr;
+  const int64_t words = (n + 31) / 32;
+  r = galloc(reinterpret_cast<void**>(&vis_init), words * 4);
+  if (r != BFS_OK) {
+    cleanup();
+    return r;
+  }
+  k_vis_init<<<blocks, kThreads>>>(off, in_off, (int32_t)n, (int32_t)words, vis_init);
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     cleanup();
@@ -791,6 +800,7 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
   dg.idx = idx;
   dg.in_off = in_off;
   dg.in_idx = in_idx;
+  dg.vis_init = vis_init;
   dg.n = (int32_t)n;
   dg.m = (int32_t)m;
   dg.words = (int32_t)((n + 31) / 32);

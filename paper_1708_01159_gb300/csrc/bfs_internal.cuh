@@ -57,6 +57,9 @@ struct DevGraph {
   const int32_t* idx;
   const int32_t* in_off;
   const int32_t* in_idx;
+  // visited bitmap a traversal starts from (before the root's bit): bit v set
+  // iff v has no edges at all, so no level reaches it and pull never scans it
+  const uint32_t* vis_init;
   int32_t n;
   int32_t m;
   int32_t words;  // ceil(n / 32)

@@ -203,7 +203,8 @@ __device__ __forceinline__ void init_fill(const DevGraph& g, uint32_t* vis0, int
   } else {
     for (int64_t i = tid; i < n; i += stride) depth[i] = (i == root) ? 0 : -1;
   }
-  for (int64_t w = tid; w < g.words; w += stride) vis0[w] = (w == (root >> 5)) ? (1u << (root & 31)) : 0u;
+  for (int64_t w = tid; w < g.words; w += stride)
+    vis0[w] = g.vis_init[w] | ((w == (root >> 5)) ? (1u << (root & 31)) : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -1131,6 +1132,21 @@ __global__ void k_tr_scatter(const int32_t* off, const int32_t* idx, int32_t n, 
       const int32_t v = idx[e];
       in_idx[atomicAdd(&cursor[v], 1)] = (int32_t)u;
     }
+}
+
+// Bit v of the starting bitmap: set iff v has neither in- nor out-edges. No
+// level can reach such a vertex, and it is nobody's in-neighbour, so marking it
+// visited changes no depth; pull then skips it, and skips whole words of them.
+// (A vertex with out-edges only must stay clear: pull would take its set bit
+// for a frontier in-neighbour.) Bits past n stay clear.
+__global__ void k_vis_init(const int32_t* off, const int32_t* in_off, int32_t n, int32_t words, uint32_t* vis_init) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < (int64_t)words * 32; v += stride) {
+    // 32 consecutive threads share one word; every lane of a warp runs the same trips
+    const bool isolated = v < n && off[v + 1] == off[v] && in_off[v + 1] == in_off[v];
+    const uint32_t word = __ballot_sync(kFull, isolated);
+    if ((v & 31) == 0) vis_init[v >> 5] = word;
+  }
 }
 
 }  // namespace bfs

@@ -111,6 +111,30 @@ def test_directed_graph_uses_transpose():
                 assert_parity(g, G, r, v)
 
 
+@pytest.mark.parametrize("mode", [bfs.MODE_PERSISTENT, bfs.MODE_GRAPH])
+def test_sources_and_isolated_vertices(mode):
+    """Isolated vertices start out marked visited (pull skips them, and whole
+    bitmap words of them); sources (out-edges, no in-edges) must not be: they
+    stay unreached unless they are the root, and are never taken for frontier
+    in-neighbours by pull."""
+    rng = np.random.default_rng(11)
+    n = 4096
+    sources = np.arange(0, n, 3)
+    isolated = np.concatenate([np.arange(2048, 2112), np.arange(3001, n, 7)])  # two whole words + scattered
+    sources = np.setdiff1d(sources, isolated)
+    rest = np.setdiff1d(np.arange(n), np.concatenate([sources, isolated]))
+    s = np.concatenate([rng.choice(sources, 6000), rng.choice(rest, 20000)])
+    t = rng.choice(rest, 26000)
+    g = gg.from_edges(n, s, t, symmetrize=False, name="sources")
+    deg_in = np.bincount(g.idx, minlength=n)
+    assert (deg_in[sources] == 0).all() and (np.diff(g.off)[isolated] == 0).all() and (deg_in[isolated] == 0).all()
+    with make(g, flags=0) as G:
+        for r in (0, 1023, int(rest[5]), 2050):
+            for v in [bfs.VARIANT_TREE] + list(range(V)):
+                ref, _ = assert_parity(g, G, r, v, mode=mode)
+                assert (ref.depth[sources[sources != r]] == -1).all()
+
+
 def test_hub_star_exercises_staged_cta_path():
     # one hub of degree 200k (staged through shared memory in many chunks) plus a tail
     n = 200_003
