@@ -259,19 +259,28 @@ __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) 
 }
 
 // Grid-wide barrier for persistent kernels (cooperative launch, so every block
-// is resident): arrival counter plus generation word. Waiting is bounded by
-// kWaitLimitNs and abandoned early once *status is not ST_OK; on either the
-// status word is set and false returned, so a kernel never spins forever.
+// is resident): arrival counter plus generation word. Thread 0 of each block
+// arrives with an acq_rel atomic (releasing its block's writes, which the
+// preceding __syncthreads ordered before it); the last arrival clears the
+// counter and publishes the next generation with a release store; the others
+// poll the generation with acquire loads, and the closing __syncthreads passes
+// what thread 0 acquired on to its block. Waiting is bounded by kWaitLimitNs
+// and abandoned early once *status is not ST_OK; on either the status word is
+// set and false returned, so a kernel never spins forever.
+__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen_word, int32_t* status) {
   __syncthreads();
   bool ok = true;
   if (threadIdx.x == 0) {
     const unsigned int gen = ld_acquire_u32(gen_word);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(count, 1u);
+    const unsigned int arrived = atom_add_acq_rel_u32(count, 1u);
     if (arrived == gridDim.x - 1) {
       *count = 0;
-      __threadfence();
       st_release_u32(gen_word, gen + 1u);
     } else {
       const unsigned long long t0 = global_ns();
@@ -284,7 +293,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* 
         __nanosleep(64);
       }
     }
-    __threadfence();
   }
   return __syncthreads_and(ok) != 0;
 }
