@@ -52,7 +52,7 @@ def parse_args():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-grid", action="store_true")
     p.add_argument("--no-serve", action="store_true")
-    p.add_argument("--serve-rates", default="1000,4000,16000", help="offered loads (queries/s)")
+    p.add_argument("--serve-rates", default="1000,4000,16000,50000", help="offered loads (queries/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--mode", default="default", choices=["default", "persistent", "graph", "host_loop"],
                    help="level-loop driver of the timed switched runs (host_loop: every kernel visible to profilers)")
@@ -310,16 +310,33 @@ def bench_serve(bfs, torch, args):
         del g
         progress(f"serve graph {name} resident")
     rng = np.random.default_rng(5000)
-    out = {"graphs": [n for n, _ in specs], "loads": []}
+    out = {"graphs": [n for n, _ in specs], "loads": [],
+           "warmup": "1000 queries submitted at once on a throwaway server before the measured loads (grows each "
+                     "graph's workspace pool; not reported)"}
     try:
+        # warm-up: workspaces are created on first need and then pooled with the graph
+        s = bfs.bfs_serve_create(max_inflight=256, num_streams=256, queue_capacity=1 << 17, merge_batch=64)
+        try:
+            ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
+            gsel = rng.integers(0, len(Gs), 1000)
+            tickets = [bfs.bfs_serve_submit(s, ids[k], int(cand[k][rng.integers(0, len(cand[k]))])) for k in gsel]
+            deadline = time.perf_counter() + 20.0
+            for t in tickets:
+                left_us = int((deadline - time.perf_counter()) * 1e6)
+                if left_us <= 0 or bfs.bfs_serve_wait(s, t, left_us) == bfs.BFS_ERR_TIMEOUT:
+                    break
+        finally:
+            bfs.bfs_serve_destroy(s)
+        progress("serve warm-up done")
         for rate in [float(x) for x in args.serve_rates.split(",")]:
             nq = int(rate * args.serve_seconds)
             arrivals = np.cumsum(rng.exponential(1.0 / rate, nq))
             gsel = rng.integers(0, len(Gs), nq)
             roots = [int(cand[k][rng.integers(0, len(cand[k]))]) for k in gsel]
-            s = bfs.bfs_serve_create(max_inflight=32, num_streams=16, queue_capacity=1 << 17, merge_batch=64)
+            s = bfs.bfs_serve_create(max_inflight=256, num_streams=256, queue_capacity=1 << 17, merge_batch=64)
             try:
                 ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
+                out["shapes"] = {name: bfs.bfs_serve_graph_shape(s, i) for (name, _), i in zip(specs, ids)}
                 tickets = []
                 rejected = 0
                 t0 = time.perf_counter()
@@ -340,7 +357,8 @@ def bench_serve(bfs, torch, args):
                 out["loads"].append({"offered_qps": rate, "achieved_qps": st["qps"], "p50_ms": st["p50_ms"],
                                      "p99_ms": st["p99_ms"], "gteps": st["gteps"], "submitted": st["submitted"],
                                      "completed": st["completed"], "not_finished": st["submitted"] - st["completed"],
-                                     "rejected": st["rejected"], "merged_waves": st["merged_waves"],
+                                     "rejected": st["rejected"], "failed": st["failed"],
+                                     "merged_waves": st["merged_waves"],
                                      "peak_bytes_inflight": st["peak_bytes_inflight"]})
             finally:
                 bfs.bfs_serve_destroy(s)

@@ -100,7 +100,12 @@ typedef struct bfs_options {
   int32_t forced_variant;    /* BFS_VARIANT_TREE or a fixed bfs_variant for every level */
   int32_t depth_on_host;     /* 1: depth_out is host memory; the library copies the result there */
   int32_t mode;              /* enum bfs_mode */
-  int32_t reserved[5];       /* must be zero */
+  int32_t grid_blocks;       /* persistent driver: blocks of the cooperative grid, 0 for one full
+                                occupancy wave (larger values are clamped to it). Fewer blocks let
+                                several traversals be resident at once and shorten the grid barrier
+                                (latency-bound, high-diameter graphs). Must be 0 for BFS_MODE_GRAPH
+                                and BFS_MODE_HOST_LOOP, and >= 0. */
+  int32_t reserved[4];       /* must be zero */
 } bfs_options;
 
 typedef struct bfs_run_stats {
@@ -200,7 +205,8 @@ typedef struct bfs_batch_config {
   int32_t push_mode;  /* 0: one thread per frontier vertex, 1: one warp per frontier vertex */
   int32_t alpha;      /* a level pulls when its frontier's edge count x alpha exceeds m */
   float ms;           /* bfs_batch_tune: measured time of one wave with this configuration */
-  int32_t reserved;
+  int32_t grid_blocks; /* blocks of the multi-source kernel, 0 for one full occupancy wave (larger
+                          values are clamped to it) */
 } bfs_batch_config;
 
 /* Set the graph's multi-source configuration. Errors: BFS_ERR_INVALID_ARG. */
@@ -208,9 +214,10 @@ int bfs_batch_set_config(bfs_graph_t g, const bfs_batch_config* cfg);
 
 /*
  * Autotuner: time one wave of the given roots (host, 1..64) with every
- * candidate configuration (push mode x alpha in {2, 4, ..., 64}; CUDA events on
- * `stream`, one warm-up run each), keep the fastest for the graph and return
- * it in *best. depth_scratch: device, k * n int32, overwritten. Synchronous.
+ * candidate configuration (push mode x alpha in {2, 4, ..., 64} x grid of a
+ * full occupancy wave, a half or a quarter of it; CUDA events on `stream`, one
+ * warm-up run each), keep the fastest for the graph and return it in *best.
+ * depth_scratch: device, k * n int32, overwritten. Synchronous.
  */
 int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_scratch, bfs_stream_t stream,
                    bfs_batch_config* best);
@@ -257,10 +264,12 @@ typedef struct bfs_server* bfs_server_t;
 typedef struct bfs_serve_config {
   int64_t mem_budget_bytes; /* device bytes admitted queries may hold at once; 0 = unlimited */
   int32_t max_inflight;     /* admitted units (queries or merged waves) on the device at once, 1..1024 */
-  int32_t num_streams;      /* streams the units are spread over, 1..64 */
+  int32_t num_streams;      /* streams the units are spread over, 1..1024 */
   int32_t queue_capacity;   /* pending submissions before bfs_serve_submit returns BFS_ERR_BUSY */
   int32_t merge_batch;      /* up to this many queued queries to one graph run as one wave (0 or 1: off; <= 64) */
-  int32_t reserved[2];      /* must be zero */
+  int32_t merge_policy;     /* 0: merge a graph's queries where the registration probe found a wave
+                               cheaper per query than single runs; 1: merge wherever merge_batch allows */
+  int32_t reserved;         /* must be zero */
 } bfs_serve_config;
 
 typedef struct bfs_serve_stats {
@@ -275,8 +284,21 @@ typedef struct bfs_serve_stats {
 
 /* Start a server (and its dispatcher thread) on the current device. */
 int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out);
-/* Register a graph (same device; up to 256; the caller keeps it alive until bfs_serve_destroy). */
+/* Register a graph (same device; up to 256; the caller keeps it alive until
+ * bfs_serve_destroy). Synchronous: probe runs on a private stream size the
+ * graph's queries. Traversals from vertices 0, n/3, 2n/3 and n-1 pick the one
+ * reaching the most edges; it is timed on 8, 16, 32, 64 blocks, one per SM and
+ * a full occupancy wave, and queries get the count with the least blocks x time
+ * among those at most 4x slower than the fastest. One 64-root multi-source wave
+ * (roots the probe reached; needs 256 n bytes of scratch, skipped if that does
+ * not fit) decides whether queued queries are merged (merge_policy 0): when its
+ * blocks x time per root is below a single query's. Takes a few traversals'
+ * time, up to about a second on a high-diameter graph of 16M vertices. */
 int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id);
+/* The launch shape registration chose for a graph: *query_blocks, the blocks of
+ * one query's persistent grid, and *merges, 1 when its queued queries may be
+ * merged into waves under merge_policy 0. BFS_ERR_NOT_FOUND for an unknown id. */
+int bfs_serve_graph_shape(bfs_server_t s, int32_t graph_id, int32_t* query_blocks, int32_t* merges);
 /* Queue a query; non-blocking. depth_out: device, n int32, or NULL (the server
  * supplies a buffer and the depths are not returned). The server's streams do
  * not wait on the caller's streams: depth_out must be ready to be written when

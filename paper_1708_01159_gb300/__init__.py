@@ -67,7 +67,7 @@ class _GraphInfo(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("forced_variant", ctypes.c_int32), ("depth_on_host", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("grid_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class _Stats(ctypes.Structure):
@@ -80,7 +80,7 @@ class _Stats(ctypes.Structure):
 class _ServeConfig(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("num_streams", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("merge_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("merge_policy", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _ServeStats(ctypes.Structure):
@@ -93,7 +93,7 @@ class _ServeStats(ctypes.Structure):
 
 class _BatchConfig(ctypes.Structure):
     _fields_ = [("push_mode", ctypes.c_int32), ("alpha", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("reserved", ctypes.c_int32)]
+                ("grid_blocks", ctypes.c_int32)]
 
 
 class _LevelProfile(ctypes.Structure):
@@ -141,6 +141,7 @@ def lib():
             "bfs_batch_tune": (ctypes.c_int, [vp, vp, c_i32, vp, vp, ctypes.POINTER(_BatchConfig)]),
             "bfs_serve_create": (ctypes.c_int, [ctypes.POINTER(_ServeConfig), ctypes.POINTER(vp)]),
             "bfs_serve_add_graph": (ctypes.c_int, [vp, vp, ctypes.POINTER(c_i32)]),
+            "bfs_serve_graph_shape": (ctypes.c_int, [vp, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
             "bfs_serve_submit": (ctypes.c_int, [vp, c_i32, c_i32, vp, ctypes.POINTER(ctypes.c_uint64)]),
             "bfs_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
             "bfs_serve_wait": (ctypes.c_int, [vp, ctypes.c_uint64, c_i64]),
@@ -241,11 +242,13 @@ def bfs_run(g: int, root: int, depth_out, stream=None) -> None:
 
 def bfs_run_ex(g: int, root: int, depth_out, stream=None, forced_variant: int = VARIANT_TREE,
                depth_on_host: Optional[bool] = None, stats: bool = False, log_capacity: int = 0,
-               mode: int = MODE_DEFAULT):
-    """BFS with options. Returns a stats dict when stats=True (then the stream is synchronised)."""
+               mode: int = MODE_DEFAULT, grid_blocks: int = 0):
+    """BFS with options. Returns a stats dict when stats=True (then the stream is synchronised).
+    grid_blocks: persistent driver only, blocks of the cooperative grid (0: a full occupancy wave)."""
     p, dev, _ = _ptr(depth_out, what="depth_out")
     host = (not dev) if depth_on_host is None else bool(depth_on_host)
-    opts = _Options(forced_variant=int(forced_variant), depth_on_host=int(host), mode=int(mode))
+    opts = _Options(forced_variant=int(forced_variant), depth_on_host=int(host), mode=int(mode),
+                    grid_blocks=int(grid_blocks))
     st = None
     logs = None
     if stats:
@@ -287,8 +290,8 @@ def bfs_run_batch(g: int, roots, depth_out, stream=None, edges: bool = False):
     return e[: r.size] if e is not None else None
 
 
-def bfs_batch_set_config(g: int, push_mode: int, alpha: int) -> None:
-    c = _BatchConfig(push_mode=push_mode, alpha=alpha)
+def bfs_batch_set_config(g: int, push_mode: int, alpha: int, grid_blocks: int = 0) -> None:
+    c = _BatchConfig(push_mode=push_mode, alpha=alpha, grid_blocks=grid_blocks)
     _check(lib().bfs_batch_set_config(g, ctypes.byref(c)), "bfs_batch_set_config")
 
 
@@ -300,7 +303,7 @@ def bfs_batch_tune(g: int, roots, depth_scratch, stream=None) -> dict:
         raise ValueError("depth_scratch must be device memory")
     c = _BatchConfig()
     _check(lib().bfs_batch_tune(g, r.ctypes.data, r.size, p, _stream(stream), ctypes.byref(c)), "bfs_batch_tune")
-    return {"push_mode": c.push_mode, "alpha": c.alpha, "ms": c.ms}
+    return {"push_mode": c.push_mode, "alpha": c.alpha, "ms": c.ms, "grid_blocks": c.grid_blocks}
 
 
 def bfs_profile_levels(g: int, root: int, reps: int = 5, advance_variant: int = VARIANT_TREE, stream=None,
@@ -334,9 +337,9 @@ def bfs_run_static(row_offsets, col_indices, root: int, depth_out, stream=None) 
 
 
 def bfs_serve_create(mem_budget_bytes: int = 0, max_inflight: int = 16, num_streams: int = 8,
-                     queue_capacity: int = 1 << 16, merge_batch: int = 0) -> int:
+                     queue_capacity: int = 1 << 16, merge_batch: int = 0, merge_policy: int = 0) -> int:
     c = _ServeConfig(mem_budget_bytes=mem_budget_bytes, max_inflight=max_inflight, num_streams=num_streams,
-                     queue_capacity=queue_capacity, merge_batch=merge_batch)
+                     queue_capacity=queue_capacity, merge_batch=merge_batch, merge_policy=merge_policy)
     out = ctypes.c_void_p()
     _check(lib().bfs_serve_create(ctypes.byref(c), ctypes.byref(out)), "bfs_serve_create")
     return out.value
@@ -346,6 +349,13 @@ def bfs_serve_add_graph(s: int, g: int) -> int:
     gid = ctypes.c_int32()
     _check(lib().bfs_serve_add_graph(s, g, ctypes.byref(gid)), "bfs_serve_add_graph")
     return gid.value
+
+
+def bfs_serve_graph_shape(s: int, graph_id: int) -> dict:
+    """Launch shape registration chose for a graph: query blocks and whether its queries merge."""
+    b, m = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(lib().bfs_serve_graph_shape(s, int(graph_id), ctypes.byref(b), ctypes.byref(m)), "bfs_serve_graph_shape")
+    return {"query_blocks": b.value, "merges": bool(m.value)}
 
 
 def bfs_serve_submit(s: int, graph_id: int, root: int, depth_out=None) -> int:

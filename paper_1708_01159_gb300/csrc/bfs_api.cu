@@ -208,7 +208,8 @@ struct bfs_graph {
   cudaEvent_t ms_done = nullptr;
   std::mutex ms_mu;
   MsConfig ms_cfg{0, 16};
-  int ms_grid = 0;
+  int ms_grid = 0;       // one full occupancy wave of the multi-source kernel
+  int ms_grid_user = 0;  // configured grid (0: ms_grid)
 };
 
 namespace {
@@ -577,7 +578,8 @@ int ms_prepare(bfs_graph* g) {
 }
 
 // One wave of up to 64 roots (host array) into k rows of depth_out.
-int ms_launch_wave(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t s, MsConfig cfg) {
+int ms_launch_wave(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t s, MsConfig cfg,
+                   int32_t grid_blocks = 0) {
   CU(cudaMemcpyAsync(g->ms_roots, roots, (size_t)k * 4, cudaMemcpyHostToDevice, s));
   k_ms_reset<<<1, 1, 0, s>>>(g->ms_state);
   CU(cudaGetLastError());
@@ -585,8 +587,8 @@ int ms_launch_wave(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth
   MsBuffers mb = g->ms;
   MsState* st = g->ms_state;
   void* args[] = {&dg, &mb, &st, &k, &depth_out, &cfg};
-  CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_msbfs), dim3(g->ms_grid), dim3(kMsThreads), args, 0,
-                                 s));
+  const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->ms_grid) : g->ms_grid;
+  CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_msbfs), dim3(grid), dim3(kMsThreads), args, 0, s));
   return BFS_OK;
 }
 
@@ -604,6 +606,14 @@ long long bfs::workspace_bytes(const bfs_graph* g) {
 int32_t bfs::graph_vertices(const bfs_graph* g) { return g->dg.n; }
 
 int bfs::graph_device(const bfs_graph* g) { return g->device; }
+
+int32_t bfs::persistent_grid(const bfs_graph* g) { return g->shapes.persist; }
+
+int32_t bfs::wave_grid(bfs_graph* g) {
+  std::lock_guard<std::mutex> lk(g->ms_mu);
+  if (ms_prepare(g) != BFS_OK) return 0;
+  return g->ms_grid;
+}
 
 int bfs::run_async(bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t stream, int32_t mode,
                    long long* edges_dst, int32_t grid_blocks) {
@@ -623,13 +633,13 @@ int bfs::run_async(bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t 
 }
 
 int bfs::batch_async(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t stream,
-                     unsigned long long* edges_dst) {
+                     unsigned long long* edges_dst, int32_t grid_blocks) {
   if (k < 1 || k > 64 || !roots || !depth_out) return fail(BFS_ERR_INVALID_ARG, "batch_async arguments");
   DeviceGuard dgd(g->device);
   std::lock_guard<std::mutex> lk(g->ms_mu);
   TRY(ms_prepare(g));
   CU(cudaStreamWaitEvent(stream, g->ms_done, 0));
-  TRY(ms_launch_wave(g, roots, k, depth_out, stream, g->ms_cfg));
+  TRY(ms_launch_wave(g, roots, k, depth_out, stream, g->ms_cfg, grid_blocks));
   if (edges_dst) CU(cudaMemcpyAsync(edges_dst, g->ms_state->edges, 64 * 8, cudaMemcpyDeviceToHost, stream));
   CU(cudaEventRecord(g->ms_done, stream));
   return BFS_OK;
@@ -881,25 +891,29 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (!depth_out) return fail(BFS_ERR_INVALID_ARG, "depth_out is null");
   if (root < 0 || root >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root %d not in [0, %d)", root, g->dg.n);
-  int32_t forced = -1, mode = BFS_MODE_DEFAULT;
+  int32_t forced = -1, mode = BFS_MODE_DEFAULT, grid_blocks = 0;
   bool host_out = false;
   if (opts) {
     if (opts->forced_variant < -1 || opts->forced_variant >= V_NUM)
       return fail(BFS_ERR_INVALID_ARG, "forced_variant %d out of range", opts->forced_variant);
     if (opts->mode < BFS_MODE_DEFAULT || opts->mode > BFS_MODE_HOST_LOOP)
       return fail(BFS_ERR_INVALID_ARG, "mode %d out of range", opts->mode);
-    for (int k = 0; k < 5; ++k)
+    for (int k = 0; k < 4; ++k)
       if (opts->reserved[k]) return fail(BFS_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (opts->grid_blocks < 0) return fail(BFS_ERR_INVALID_ARG, "grid_blocks < 0");
+    if (opts->grid_blocks > 0 && (opts->mode == BFS_MODE_GRAPH || opts->mode == BFS_MODE_HOST_LOOP))
+      return fail(BFS_ERR_INVALID_ARG, "grid_blocks applies to the persistent driver only");
     forced = opts->forced_variant;
     mode = opts->mode;
     host_out = opts->depth_on_host != 0;
+    grid_blocks = opts->grid_blocks;
   }
   DeviceGuard dgd(g->device);
   TRY(sync_tree(g));
   Workspace* ws = nullptr;
   TRY(acquire(g, stream, &ws));
   int32_t* dst = host_out ? ws->host_depth_stage : depth_out;
-  int r = launch_run(g, ws, root, dst, forced, mode, stream);
+  int r = launch_run(g, ws, root, dst, forced, mode, stream, grid_blocks);
   RunState hs{};
   if (r == BFS_OK && host_out) {
     cudaError_t e = cudaMemcpyAsync(depth_out, dst, (size_t)g->dg.n * 4, cudaMemcpyDeviceToHost, stream);
@@ -962,7 +976,7 @@ int bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth
   const int64_t n = g->dg.n;
   for (int32_t w0 = 0; w0 < k; w0 += 64) {
     const int32_t kw = std::min<int32_t>(64, k - w0);
-    TRY(ms_launch_wave(g, roots + w0, kw, depth_out + (size_t)w0 * n, s, g->ms_cfg));
+    TRY(ms_launch_wave(g, roots + w0, kw, depth_out + (size_t)w0 * n, s, g->ms_cfg, g->ms_grid_user));
     if (edges_out) {
       unsigned long long e[64];
       CU(cudaMemcpyAsync(e, g->ms_state->edges, sizeof e, cudaMemcpyDeviceToHost, s));
@@ -979,10 +993,11 @@ int bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth
 
 int bfs_batch_set_config(bfs_graph_t g, const bfs_batch_config* cfg) {
   TRY(check_graph(g));
-  if (!cfg || cfg->push_mode < 0 || cfg->push_mode > 1 || cfg->alpha < 1)
+  if (!cfg || cfg->push_mode < 0 || cfg->push_mode > 1 || cfg->alpha < 1 || cfg->grid_blocks < 0)
     return fail(BFS_ERR_INVALID_ARG, "batch config out of range");
   std::lock_guard<std::mutex> lk(g->ms_mu);
   g->ms_cfg = MsConfig{cfg->push_mode, cfg->alpha};
+  g->ms_grid_user = cfg->grid_blocks;
   return BFS_OK;
 }
 
@@ -1002,34 +1017,42 @@ int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* dept
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   const int alphas[] = {2, 4, 8, 16, 32, 64};
+  const int grids[] = {g->ms_grid, g->ms_grid / 2, g->ms_grid / 4};
   float best_ms = 1e30f;
   MsConfig best_cfg = g->ms_cfg;
+  int best_grid = g->ms_grid_user;
   int r = BFS_OK;
-  for (int pm = 0; pm < 2 && r == BFS_OK; ++pm)
-    for (int a : alphas) {
-      const MsConfig c{pm, a};
-      r = ms_launch_wave(g, roots, k, depth_scratch, s, c);  // warm-up
-      if (r != BFS_OK) break;
-      float ms = 0;
-      if (cudaEventRecord(e0, s) != cudaSuccess || (r = ms_launch_wave(g, roots, k, depth_scratch, s, c)) != BFS_OK ||
-          cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        if (r == BFS_OK) r = fail(BFS_ERR_CUDA, "tuning run failed");
-        break;
+  for (int gi = 0; gi < 3 && r == BFS_OK; ++gi) {
+    const int grid = std::max(1, grids[gi]);
+    for (int pm = 0; pm < 2 && r == BFS_OK; ++pm)
+      for (int a : alphas) {
+        const MsConfig c{pm, a};
+        r = ms_launch_wave(g, roots, k, depth_scratch, s, c, grid);  // warm-up
+        if (r != BFS_OK) break;
+        float ms = 0;
+        if (cudaEventRecord(e0, s) != cudaSuccess ||
+            (r = ms_launch_wave(g, roots, k, depth_scratch, s, c, grid)) != BFS_OK ||
+            cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          if (r == BFS_OK) r = fail(BFS_ERR_CUDA, "tuning run failed");
+          break;
+        }
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_cfg = c;
+          best_grid = grid;
+        }
       }
-      if (ms < best_ms) {
-        best_ms = ms;
-        best_cfg = c;
-      }
-    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (r != BFS_OK) return r;
   g->ms_cfg = best_cfg;
+  g->ms_grid_user = best_grid;
   best->push_mode = best_cfg.push_mode;
   best->alpha = best_cfg.alpha;
   best->ms = best_ms;
-  best->reserved = 0;
+  best->grid_blocks = best_grid;
   CU(cudaEventRecord(g->ms_done, s));
   return BFS_OK;
 }

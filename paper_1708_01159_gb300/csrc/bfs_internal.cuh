@@ -124,16 +124,20 @@ int set_error_detail(int code, const char* msg);
 // edges_dst (pinned host memory) is not null, an asynchronous copy of its
 // reached-edge count there. batch_async: one multi-source wave (k <= 64) into k
 // rows of depth_out, per-root reached-edge counts copied to edges_dst (pinned,
-// 64 entries). grid_blocks > 0 limits a persistent run to that many blocks so
-// several runs can be resident at once. Both return a bfs_status code.
+// 64 entries). grid_blocks > 0 limits a persistent run (or a wave) to that many
+// blocks so several can be resident at once. Both return a bfs_status code.
 int run_async(struct ::bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t stream, int32_t mode,
               long long* edges_dst, int32_t grid_blocks);
 int batch_async(struct ::bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t stream,
-                unsigned long long* edges_dst);
+                unsigned long long* edges_dst, int32_t grid_blocks);
 // Device bytes one traversal of the graph holds (workspace), for admission control.
 long long workspace_bytes(const struct ::bfs_graph* g);
 int32_t graph_vertices(const struct ::bfs_graph* g);
 int graph_device(const struct ::bfs_graph* g);
+// Blocks of one full occupancy wave of the persistent traversal kernel and of
+// the multi-source kernel (0 when cooperative launch is unsupported).
+int32_t persistent_grid(const struct ::bfs_graph* g);
+int32_t wave_grid(struct ::bfs_graph* g);
 
 // ---------------------------------------------------------------------------
 // Small device helpers

@@ -26,6 +26,7 @@ namespace bfs {
 namespace {
 
 constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int32_t kMsBlockDegree = 128;  // push_mode 0: degree from which the block expands a vertex together
 
 __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
 #pragma unroll
@@ -50,6 +51,8 @@ __device__ __forceinline__ void ms_depth_rows(int32_t* depth, int64_t n, int64_t
 __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, MsState* st, int32_t k,
                                                        int32_t* depth, MsConfig cfg) {
   __shared__ unsigned long long s_edges[64];
+  __shared__ int32_t s_big[kMsThreads];
+  __shared__ int s_nbig;
   BFS_DECLARE_STAGE(stage);
   const int64_t n = g.n;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,16 +132,39 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
       for (int64_t i = tid; i < (int64_t)pf; i += stride) nxt[out_list[i]] = 0;
       unsigned int* ttail = &st->ttail[L % 2];
       if (cfg.push_mode == 0) {
+        // a thread per frontier vertex; vertices of degree >= kMsBlockDegree are
+        // set aside in shared memory and expanded by the whole block, one after
+        // another, so a hub never serialises on one thread
         for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < f; base += stride) {
+          if (threadIdx.x == 0) s_nbig = 0;
+          __syncthreads();
           const int64_t i = base + threadIdx.x;
           if (i < f) {
             const int32_t v = list[i];
+            const int32_t beg = g.off[v], end = g.off[v + 1];
+            if (end - beg >= kMsBlockDegree) {
+              s_big[atomicAdd(&s_nbig, 1)] = v;
+            } else {
+              const unsigned long long fv = cur[v];
+              for (int32_t e = beg; e < end; ++e) {
+                const int32_t u = g.idx[e];
+                const unsigned long long nb = fv & ~mb.visit[u];
+                if (nb && atomicOr(&mb.next[u], nb) == 0ull) stage_put(stage, mb.tlist, ttail, u);
+              }
+            }
+          }
+          __syncthreads();
+          const int nbig = s_nbig;
+          for (int b = 0; b < nbig; ++b) {
+            const int32_t v = s_big[b];
             const unsigned long long fv = cur[v];
-            for (int32_t e = g.off[v]; e < g.off[v + 1]; ++e) {
+            const int32_t end = g.off[v + 1];
+            for (int32_t e = g.off[v] + (int32_t)threadIdx.x; e < end; e += (int32_t)blockDim.x) {
               const int32_t u = g.idx[e];
               const unsigned long long nb = fv & ~mb.visit[u];
               if (nb && atomicOr(&mb.next[u], nb) == 0ull) stage_put(stage, mb.tlist, ttail, u);
             }
+            if ((b & 7) == 7) stage_drain(stage, mb.tlist, ttail, kStageCap / 2);
           }
           stage_drain(stage, mb.tlist, ttail, kStageCap / 2);
         }

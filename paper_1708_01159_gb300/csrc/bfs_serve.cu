@@ -9,9 +9,13 @@
 // the same graph are merged into one multi-source wave (up to merge_batch
 // roots, one bit each in 64-bit masks). Completion is observed by polling a
 // CUDA event per admitted unit; latency runs from submission to that
-// observation. Single queries use the persistent driver on one block per SM
-// (a quarter of a full cooperative grid), so up to four traversals are
-// resident together; a full grid each would serialise them.
+// observation. Queries run as persistent cooperative kernels whose block count
+// is chosen per graph from probe runs at registration (probe_shape), as is
+// whether its queued queries are merged into waves: a high-diameter graph (a
+// grid: thousands of latency-bound levels) runs narrow queries, many resident
+// at once; a wide, shallow one runs a block per SM or more. Each unit goes to
+// the stream with the fewest units in flight, so a short query never queues
+// behind a long one on a shared stream.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -47,6 +51,7 @@ struct TicketInfo {
 struct Unit {  // one admitted launch: a single query or a merged wave
   std::vector<Request> reqs;
   int32_t graph_id = 0;
+  int stream_index = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   long long bytes = 0;
@@ -60,10 +65,12 @@ struct Unit {  // one admitted launch: a single query or a merged wave
 struct bfs_server {
   bfs_serve_config cfg{};
   int device = 0;
-  int32_t query_blocks = 0;  // blocks of one single-query persistent traversal (one per SM)
+  int32_t sms = 0;
   std::vector<bfs_graph*> graphs;
+  std::vector<int32_t> single_blocks;  // per graph: blocks of a single-query traversal
+  std::vector<char> merge_ok;          // per graph: queued queries may be merged into waves
   std::vector<cudaStream_t> streams;
-  size_t next_stream = 0;
+  std::vector<int> stream_units;  // units in flight per stream (dispatcher thread only)
   std::vector<cudaEvent_t> free_events;
   std::vector<long long*> free_pinned;
   // per graph: free single-query depth buffers, and one wave staging buffer
@@ -95,6 +102,8 @@ namespace {
 constexpr size_t kTicketCap = 1 << 20;
 constexpr size_t kMaxGraphs = 256;
 constexpr int kScanDepth = 32;  // queue entries considered per admission pass
+// a query's block count may cost up to this factor in latency over the fastest
+constexpr float kLatencySlack = 4.0f;
 
 void finish_ticket(bfs_server* s, uint64_t t, int status) {
   auto it = s->tickets.find(t);
@@ -134,7 +143,7 @@ int launch_unit(bfs_server* s, Unit& u) {
       }
       u.scratch = out;
     }
-    int rc = bfs::run_async(g, r.root, out, u.stream, BFS_MODE_PERSISTENT, u.edges, s->query_blocks);
+    int rc = bfs::run_async(g, r.root, out, u.stream, BFS_MODE_PERSISTENT, u.edges, s->single_blocks[u.graph_id]);
     if (rc != BFS_OK) return rc;
   } else {
     int32_t roots[64];
@@ -149,7 +158,7 @@ int launch_unit(bfs_server* s, Unit& u) {
       s->wave_staging[u.graph_id] = stage;
     }
     u.scratch = stage;
-    int rc = bfs::batch_async(g, roots, k, stage, u.stream, reinterpret_cast<unsigned long long*>(u.edges));
+    int rc = bfs::batch_async(g, roots, k, stage, u.stream, reinterpret_cast<unsigned long long*>(u.edges), 0);
     if (rc != BFS_OK) return rc;
     for (int i = 0; i < k; ++i)
       if (u.reqs[i].depth_out &&
@@ -162,6 +171,7 @@ int launch_unit(bfs_server* s, Unit& u) {
 }
 
 void release_unit(bfs_server* s, Unit& u) {
+  s->stream_units[u.stream_index] -= 1;
   if (!u.wave && u.scratch) s->free_depth[u.graph_id].push_back(u.scratch);
   if (u.wave) s->wave_busy[u.graph_id] = 0;
   s->free_events.push_back(u.done);
@@ -220,7 +230,7 @@ void dispatcher(bfs_server* s) {
         ++scanned;
         const int gid = it->graph_id;
         int k = 1;
-        if (s->cfg.merge_batch > 1 && !s->wave_busy[gid]) {
+        if (s->cfg.merge_batch > 1 && (s->merge_ok[gid] || s->cfg.merge_policy == 1) && !s->wave_busy[gid]) {
           for (auto jt = std::next(it); jt != s->queue.end() && k < s->cfg.merge_batch; ++jt)
             if (jt->graph_id == gid) ++k;
         }
@@ -238,7 +248,10 @@ void dispatcher(bfs_server* s) {
         s->free_events.pop_back();
         u.edges = s->free_pinned.back();
         s->free_pinned.pop_back();
-        u.stream = s->streams[s->next_stream++ % s->streams.size()];
+        u.stream_index = (int)(std::min_element(s->stream_units.begin(), s->stream_units.end()) -
+                               s->stream_units.begin());
+        u.stream = s->streams[u.stream_index];
+        s->stream_units[u.stream_index] += 1;
         u.reqs.push_back(*it);
         it = s->queue.erase(it);  // list: erasing leaves the other iterators valid
         if (u.wave) {
@@ -291,25 +304,136 @@ void dispatcher(bfs_server* s) {
   }
 }
 
+// Launch shape of a graph's queries, from probe runs at registration
+// (synchronous, on a private stream):
+//  1. traversals from up to four spread vertices (0, n/3, 2n/3, n-1); the one
+//     reaching the most edges is the probe root;
+//  2. that traversal timed on 8, 16, 32, 64 blocks, one per SM and a full
+//     occupancy wave: a query gets the block count that minimises blocks x time
+//     (the device share it holds) among those within kLatencySlack of the
+//     fastest, so latency-bound graphs run narrow and many of their queries
+//     share the GPU;
+//  3. one multi-source wave from 64 vertices the probe reached, on its full
+//     grid: same-graph queries are merged into waves only when a wave's
+//     blocks x time per root is below a single query's.
+struct Shape {
+  int32_t single_blocks = 0;
+  bool merge = false;
+};
+
+int probe_shape(bfs_server* s, bfs_graph* g, Shape* out) {
+  const int32_t n = bfs::graph_vertices(g);
+  const int32_t full = std::max(1, bfs::persistent_grid(g));
+  out->single_blocks = std::min(full, s->sms);
+  out->merge = false;
+  cudaStream_t stream;
+  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return bfs::set_error_detail(BFS_ERR_CUDA, "probe stream");
+  }
+  int32_t* depth = nullptr;
+  int32_t* wave_out = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = BFS_OK;
+  if (cudaMalloc(&depth, (size_t)n * 4) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    rc = bfs::set_error_detail(BFS_ERR_OOM, "probe buffers");
+  // 1. probe root
+  int32_t root = 0;
+  long long best_e = -1;
+  const int32_t cand[4] = {0, n / 3, (int32_t)(2LL * n / 3), n - 1};
+  for (int c = 0; c < 4 && rc == BFS_OK; ++c) {
+    bfs_run_stats st{};
+    bfs_options opt{};
+    opt.forced_variant = BFS_VARIANT_TREE;
+    opt.mode = BFS_MODE_PERSISTENT;
+    rc = bfs_run_ex(g, cand[c], depth, stream, &opt, &st);  // with stats: synchronous
+    if (rc == BFS_OK && st.edges_reached > best_e) {
+      best_e = st.edges_reached;
+      root = cand[c];
+    }
+  }
+  // 2. blocks of a single query
+  auto timed = [&](auto&& launch, float* ms) -> int {
+    if (cudaEventRecord(e0, stream) != cudaSuccess) return BFS_ERR_CUDA;
+    const int r = launch();
+    if (r != BFS_OK) return r;
+    if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return BFS_ERR_CUDA;
+    return BFS_OK;
+  };
+  const int32_t sizes[6] = {8, 16, 32, 64, s->sms, full};
+  float t[6] = {0, 0, 0, 0, 0, 0};
+  float fastest = 1e30f;
+  for (int i = 0; i < 6 && rc == BFS_OK; ++i) {
+    bfs_options opt{};
+    opt.forced_variant = BFS_VARIANT_TREE;
+    opt.mode = BFS_MODE_PERSISTENT;
+    opt.grid_blocks = std::min(sizes[i], full);
+    rc = timed([&] { return bfs_run_ex(g, root, depth, stream, &opt, nullptr); }, &t[i]);
+    fastest = std::min(fastest, t[i]);
+  }
+  double single_cost = 0;
+  if (rc == BFS_OK) {
+    double best_cost = 1e300;
+    for (int i = 0; i < 6; ++i) {
+      const int32_t b = std::min(sizes[i], full);
+      const double cost = (double)b * t[i];
+      if (t[i] <= kLatencySlack * fastest && cost < best_cost) {
+        best_cost = cost;
+        out->single_blocks = b;
+      }
+    }
+    single_cost = best_cost;
+  }
+  // 3. merge or not: a 64-root wave from vertices the probe reached
+  if (rc == BFS_OK) {
+    std::vector<int32_t> d((size_t)n);
+    if (cudaMemcpy(d.data(), depth, (size_t)n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = BFS_ERR_CUDA;
+    std::vector<int32_t> reached;
+    for (int32_t v = 0; v < n && rc == BFS_OK; ++v)
+      if (d[(size_t)v] >= 0) reached.push_back(v);
+    const int32_t wg = bfs::wave_grid(g);
+    if (rc == BFS_OK && wg > 0 && cudaMalloc(&wave_out, (size_t)64 * n * 4) == cudaSuccess) {
+      int32_t roots[64];
+      for (int i = 0; i < 64; ++i) roots[i] = reached[(size_t)i * reached.size() / 64];
+      float wave_ms = 0;
+      rc = timed([&] { return bfs_run_batch(g, roots, 64, wave_out, stream, nullptr); }, &wave_ms);
+      if (rc == BFS_OK) out->merge = (double)wg * wave_ms / 64.0 < single_cost;
+    }
+    cudaGetLastError();  // a wave buffer that did not fit only disables merging
+  }
+  if (wave_out) cudaFree(wave_out);
+  if (depth) cudaFree(depth);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(stream);
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
 
 int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out) {
   if (!cfg || !out) return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "null argument");
-  if (cfg->max_inflight < 1 || cfg->max_inflight > 1024 || cfg->num_streams < 1 || cfg->num_streams > 64 ||
-      cfg->queue_capacity < 1 || cfg->merge_batch < 0 || cfg->merge_batch > 64 || cfg->mem_budget_bytes < 0)
+  if (cfg->max_inflight < 1 || cfg->max_inflight > 1024 || cfg->num_streams < 1 || cfg->num_streams > 1024 ||
+      cfg->queue_capacity < 1 || cfg->merge_batch < 0 || cfg->merge_batch > 64 || cfg->mem_budget_bytes < 0 ||
+      cfg->merge_policy < 0 || cfg->merge_policy > 1 || cfg->reserved != 0)
     return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "serve config out of range");
   auto* s = new bfs_server;
   s->cfg = *cfg;
   // graphs are registered while the dispatcher runs: fixed capacity, so these
   // vectors never reallocate under it
   s->graphs.reserve(kMaxGraphs);
+  s->single_blocks.reserve(kMaxGraphs);
+  s->merge_ok.reserve(kMaxGraphs);
   s->free_depth.reserve(kMaxGraphs);
   s->wave_staging.reserve(kMaxGraphs);
   s->wave_busy.reserve(kMaxGraphs);
   if (cudaGetDevice(&s->device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&s->query_blocks, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+      cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
     delete s;
     return bfs::set_error_detail(BFS_ERR_CUDA, "cudaGetDevice failed");
   }
@@ -318,6 +442,7 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out) {
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
     s->streams.push_back(st);
   }
+  s->stream_units.assign(s->streams.size(), 0);
   for (int i = 0; i < cfg->max_inflight; ++i) {
     cudaEvent_t e;
     long long* p = nullptr;
@@ -346,13 +471,28 @@ int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id) {
   if (!s || !g || !graph_id) return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "null argument");
   if (bfs::graph_device(g) != s->device)
     return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "graph lives on another device");
+  Shape shape;
+  const int rc = probe_shape(s, g, &shape);
+  if (rc != BFS_OK) return rc;
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->graphs.size() >= kMaxGraphs) return bfs::set_error_detail(BFS_ERR_BUSY, "too many graphs (256)");
   s->graphs.push_back(g);
+  s->single_blocks.push_back(shape.single_blocks);
+  s->merge_ok.push_back(shape.merge ? 1 : 0);
   s->free_depth.emplace_back();
   s->wave_staging.push_back(nullptr);
   s->wave_busy.push_back(0);
   *graph_id = (int32_t)s->graphs.size() - 1;
+  return BFS_OK;
+}
+
+int bfs_serve_graph_shape(bfs_server_t s, int32_t graph_id, int32_t* query_blocks, int32_t* merges) {
+  if (!s || !query_blocks || !merges) return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size())
+    return bfs::set_error_detail(BFS_ERR_NOT_FOUND, "unknown graph id");
+  *query_blocks = s->single_blocks[graph_id];
+  *merges = s->merge_ok[graph_id];
   return BFS_OK;
 }
 

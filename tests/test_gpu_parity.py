@@ -348,10 +348,28 @@ def test_batch_equals_single_runs():
         assert np.array_equal(edges, E)
 
 
+@pytest.mark.parametrize("grid_blocks", [1, 5, 37, 1 << 20])
+def test_persistent_grid_blocks(grid_blocks):
+    """The persistent driver on any number of blocks (1, odd, fewer than the SMs,
+    more than one occupancy wave: clamped) gives the oracle's depths; the other
+    drivers reject a block count."""
+    for g in (gg.rmat(13, 16, seed=83), gg.grid(45, 61, 0.1, seed=84)):
+        with make(g) as G:
+            for r in gg.sample_roots(g, 2, seed=13):
+                ref = oracle.bfs(g.off, g.idx, int(r))
+                d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+                st = bfs.bfs_run_ex(G.handle, int(r), d, mode=bfs.MODE_PERSISTENT, grid_blocks=grid_blocks, stats=True)
+                assert np.array_equal(d.cpu().numpy(), ref.depth) and st["levels"] == ref.num_levels
+            for m in (bfs.MODE_GRAPH, bfs.MODE_HOST_LOOP):
+                with pytest.raises(bfs.BFSError) as e:
+                    bfs.bfs_run_ex(G.handle, 0, d, mode=m, grid_blocks=grid_blocks)
+                assert e.value.code == bfs.BFS_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("which", ["rmat", "grid"])
 @pytest.mark.parametrize("push_mode", [0, 1])
-@pytest.mark.parametrize("alpha", [1, 8, 1 << 20])
-def test_batch_configs(which, push_mode, alpha):
+@pytest.mark.parametrize("alpha,grid_blocks", [(1, 0), (8, 3), (1 << 20, 0), (8, 1 << 20)])
+def test_batch_configs(which, push_mode, alpha, grid_blocks):
     """Multi-source BFS in every configuration (alpha 1: pull from level 1 on;
     huge alpha: push only) equals independent oracle runs, repeated and isolated
     roots included, on a skewed graph and on a high-diameter grid."""
@@ -362,7 +380,7 @@ def test_batch_configs(which, push_mode, alpha):
     roots = np.concatenate([gg.sample_roots(g, 40, seed=12), [iso, iso], gg.sample_roots(g, 3, seed=12)])
     D, E = oracle.bfs_batch(g.off, g.idx, roots)
     with make(g) as G:
-        bfs.bfs_batch_set_config(G.handle, push_mode, alpha)
+        bfs.bfs_batch_set_config(G.handle, push_mode, alpha, grid_blocks)
         out = torch.empty(len(roots) * g.n, dtype=torch.int32, device="cuda")
         edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
         assert np.array_equal(out.cpu().numpy().reshape(len(roots), g.n), D)
@@ -378,7 +396,7 @@ def test_batch_directed_and_tuner():
     with make(g, flags=0) as G:
         scratch = torch.empty(64 * n, dtype=torch.int32, device="cuda")
         cfg = bfs.bfs_batch_tune(G.handle, roots, scratch)
-        assert cfg["push_mode"] in (0, 1) and cfg["alpha"] >= 1 and cfg["ms"] > 0
+        assert cfg["push_mode"] in (0, 1) and cfg["alpha"] >= 1 and cfg["ms"] > 0 and cfg["grid_blocks"] > 0
         out = torch.empty(64 * n, dtype=torch.int32, device="cuda")
         edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
         assert np.array_equal(out.cpu().numpy().reshape(64, n), D)

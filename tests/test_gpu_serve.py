@@ -32,11 +32,14 @@ def alone(G, n, root):
     return d.cpu().numpy()
 
 
-@pytest.mark.parametrize("merge", [0, 16])
-def test_mixed_results_equal_alone(graphs, merge):
+@pytest.mark.parametrize("merge,policy", [(0, 0), (16, 1), (16, 0)])
+def test_mixed_results_equal_alone(graphs, merge, policy):
+    """policy 1 merges wherever it can; policy 0 merges only graphs whose
+    registration probe found waves cheaper (each graph's query block count is
+    probed too): either way every result equals the query run alone."""
     gs, Gs = graphs
-    rng = np.random.default_rng(7 + merge)
-    s = bfs.bfs_serve_create(max_inflight=12, num_streams=6, merge_batch=merge)
+    rng = np.random.default_rng(7 + merge + policy)
+    s = bfs.bfs_serve_create(max_inflight=12, num_streams=6, merge_batch=merge, merge_policy=policy)
     try:
         ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
         plan = []
@@ -58,8 +61,13 @@ def test_mixed_results_equal_alone(graphs, merge):
         st = bfs.bfs_serve_stats(s)
         assert st["completed"] == 240 and st["failed"] == 0 and st["admitted"] == 240
         assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"] and st["qps"] > 0 and st["gteps"] > 0
-        if merge:
+        if merge and policy == 1:
             assert st["merged_waves"] >= 1
+        for gi in ids:
+            shape = bfs.bfs_serve_graph_shape(s, gi)
+            assert 1 <= shape["query_blocks"] <= 8 * torch.cuda.get_device_properties(0).multi_processor_count
+        with pytest.raises(bfs.BFSError):
+            bfs.bfs_serve_graph_shape(s, len(ids))
         for _, _, _, t in jobs[:3]:
             assert bfs.bfs_serve_poll(s, t) == (0, bfs.BFS_OK)
     finally:
