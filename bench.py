@@ -262,9 +262,72 @@ def bench_batch(bfs, torch, stream):
         ts = e0.elapsed_time(e1) / 1e3
         out.update({"gteps": float(edges.sum()) / 2 / t / 1e9, "ms_per_launch": t * 1e3,
                     "single_source_gteps": float(edges.sum()) / 2 / ts / 1e9, "speedup_vs_single": ts / t,
-                    "tuned": {"push_mode": ["thread", "warp"][cfg["push_mode"]], "alpha": cfg["alpha"]},
+                    "tuned": {"push_mode": ["thread+block", "warp"][cfg["push_mode"]], "alpha": cfg["alpha"],
+                              "grid_blocks": cfg["grid_blocks"]},
                     "note": "depth output k x n int32 written inside the timed region (1.07 GB per launch)"})
     return out
+
+
+def bench_batch_graphs(bfs, torch):
+    """Multi-source BFS over a batch of 32 uneven R-MAT graphs (scale 12-20, edge
+    factor 8-32, seeded): each graph's 64 roots in one launch, the 32 launches
+    spread over 8 streams; against the same 2048 roots as single-source runs."""
+    import graphgen as gg
+    rng = np.random.default_rng(6000)
+    specs = [(int(rng.integers(12, 21)), int(rng.choice([8, 16, 32]))) for _ in range(32)]
+    streams = [torch.cuda.Stream() for _ in range(8)]
+    main = torch.cuda.current_stream()
+    Gs, roots, outs, tuned = [], [], [], 0
+    edges_total = 0
+    try:
+        for i, (sc, ef) in enumerate(specs):
+            g = gg.rmat(sc, ef, seed=6000 + i)
+            G = bfs.Graph(g.off, g.idx)
+            Gs.append(G)
+            r = gg.sample_roots(g, 64, seed=6100 + i, giant=True)
+            roots.append(r)
+            out = torch.empty(64 * g.n, dtype=torch.int32, device="cuda")
+            outs.append(out)
+            if sc >= 16:  # smaller graphs keep the default configuration
+                bfs.bfs_batch_tune(G.handle, r, out)
+                tuned += 1
+            edges_total += int(bfs.bfs_run_batch(G.handle, r, out, edges=True).sum())
+        single = [torch.empty(G.n, dtype=torch.int32, device="cuda") for G in Gs]
+
+        def run(batch):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(main)
+            for st in streams:
+                st.wait_event(e0)
+            for i, G in enumerate(Gs):
+                st = streams[i % len(streams)]
+                if batch:
+                    bfs.bfs_run_batch(G.handle, roots[i], outs[i], st)
+                else:
+                    for r in roots[i]:
+                        bfs.bfs_run(G.handle, int(r), single[i], st)
+            for st in streams:
+                ev = torch.cuda.Event()
+                ev.record(st)
+                main.wait_event(ev)
+            e1.record(main)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / 1e3
+
+        run(True)
+        t = min(run(True) for _ in range(3))
+        run(False)
+        ts = min(run(False) for _ in range(2))
+    finally:
+        for G in Gs:
+            G.close()
+    return {"workload": "32 R-MAT graphs (a/b/c/d .57/.19/.19/.05), scale 12-20 and edge factor 8-32 drawn with "
+                        "seed 6000, 64 giant-component roots each; one multi-source launch per graph, 8 streams",
+            "scales": [sc for sc, _ in specs], "edge_factors": [ef for _, ef in specs],
+            "gteps": edges_total / 2 / t / 1e9, "ms_per_batch": t * 1e3,
+            "single_source_gteps": edges_total / 2 / ts / 1e9, "speedup_vs_single": ts / t,
+            "tuned_graphs": tuned}
 
 
 def bench_grid(bfs, torch, stream):
@@ -532,6 +595,8 @@ def run_ours(args):
     progress("switched, fixed, e2e and roofline done")
     if not args.no_batch:
         line["batch"] = bench_batch(bfs, torch, stream)
+        progress("batch (ER) done")
+        line["batch_graphs"] = bench_batch_graphs(bfs, torch)
         progress("batch done")
     if not args.no_grid:
         line["high_diameter"] = bench_grid(bfs, torch, stream)

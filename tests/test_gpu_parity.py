@@ -387,6 +387,30 @@ def test_batch_configs(which, push_mode, alpha, grid_blocks):
         assert np.array_equal(edges, E)
 
 
+def test_batch_uneven_graphs_concurrently():
+    """A batch of uneven R-MAT graphs (scale 8-13, edge factor 8-32), 64 roots
+    each in one launch per graph, launches spread over streams and overlapping:
+    every depth row equals the oracle's."""
+    rng = np.random.default_rng(21)
+    specs = [(int(rng.integers(8, 14)), int(rng.choice([8, 16, 32]))) for _ in range(6)]
+    gs = [gg.rmat(sc, ef, seed=700 + i) for i, (sc, ef) in enumerate(specs)]
+    Gs = [make(g) for g in gs]
+    try:
+        streams = [torch.cuda.Stream() for _ in range(3)]
+        roots = [gg.sample_roots(g, 64, seed=800 + i) for i, g in enumerate(gs)]
+        outs = [torch.full((64 * g.n,), -7, dtype=torch.int32, device="cuda") for g in gs]
+        torch.cuda.synchronize()
+        for i, G in enumerate(Gs):
+            bfs.bfs_run_batch(G.handle, roots[i], outs[i], streams[i % 3])
+        torch.cuda.synchronize()
+        for i, g in enumerate(gs):
+            D, _ = oracle.bfs_batch(g.off, g.idx, roots[i])
+            assert np.array_equal(outs[i].cpu().numpy().reshape(64, g.n), D), specs[i]
+    finally:
+        for G in Gs:
+            G.close()
+
+
 def test_batch_directed_and_tuner():
     rng = np.random.default_rng(5)
     n = 5000
