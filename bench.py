@@ -331,28 +331,45 @@ def bench_batch_graphs(bfs, torch):
 
 
 def bench_grid(bfs, torch, stream):
-    """High diameter: 4096 x 4096 permuted grid, 10% edges dropped, 4 roots; both drivers."""
+    """High diameter: 4096 x 4096 permuted grid, 10% edges dropped, 16 roots in the
+    giant component; the switched traversal under both drivers, and every fixed
+    variant (persistent driver) on the first 4 roots."""
     import graphgen as gg
     g = gg.grid_4096_permuted()
-    roots = gg.sample_roots(g, 4, seed=gg.SEED_ROOTS + 2, giant=True)
-    out = {"workload": f"4096x4096 grid, 10% of edges dropped, ids permuted ({g.m:,} directed edges), 4 roots"}
+    roots = [int(r) for r in gg.sample_roots(g, 16, seed=gg.SEED_ROOTS + 2, giant=True)]
+    out = {"workload": f"4096x4096 grid, 10% of edges dropped, ids permuted ({g.m:,} directed edges), "
+                       f"{len(roots)} roots in the giant component"}
     with bfs.Graph(g.off, g.idx) as G:
         depth = torch.empty(g.n, dtype=torch.int32, device="cuda")
-        st = bfs.bfs_run_ex(G.handle, int(roots[0]), depth, stream, stats=True)
-        out["levels"] = st["levels"]
-        edges = st["edges_reached"]
+        stats = [bfs.bfs_run_ex(G.handle, r, depth, stream, stats=True) for r in roots]
+        edges = [st["edges_reached"] for st in stats]
+        levels = [st["levels"] for st in stats]
+        out["levels"] = {"min": min(levels), "max": max(levels), "mean": float(np.mean(levels))}
+
+        def timed(rs, **kw):
+            bfs.bfs_run_ex(G.handle, rs[0], depth, stream, **kw)
+            torch.cuda.synchronize()
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(rs) + 1)]
+            evs[0].record(stream)
+            for i, r in enumerate(rs):
+                bfs.bfs_run_ex(G.handle, r, depth, stream, **kw)
+                evs[i + 1].record(stream)
+            torch.cuda.synchronize()
+            return [evs[i].elapsed_time(evs[i + 1]) / 1e3 for i in range(len(rs))]
+
         for name, mode in (("persistent", bfs.MODE_PERSISTENT), ("graph", bfs.MODE_GRAPH)):
-            bfs.bfs_run_ex(G.handle, int(roots[0]), depth, stream, mode=mode)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for r in roots:
-                bfs.bfs_run_ex(G.handle, int(r), depth, stream, mode=mode)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / 1e3 / len(roots)
-            out[name] = {"gteps": edges / 2 / t / 1e9, "ms_per_traversal": t * 1e3,
-                         "us_per_level": t * 1e6 / st["levels"]}
+            ts = timed(roots, mode=mode)
+            out[name] = {"gteps": harmonic_gteps(ts, edges), "ms_per_traversal": 1e3 * float(np.mean(ts)),
+                         "us_per_level": 1e6 * sum(ts) / sum(levels)}
+        k = 4
+        fixed = {}
+        for v, vname in enumerate(bfs.VARIANTS):
+            fixed[vname] = harmonic_gteps(timed(roots[:k], mode=bfs.MODE_PERSISTENT, forced_variant=v), edges[:k])
+        switched = harmonic_gteps(timed(roots[:k], mode=bfs.MODE_PERSISTENT), edges[:k])
+        best = max(fixed, key=fixed.get)
+        out["fixed_variants_gteps"] = fixed
+        out["best_fixed"] = {"variant": best, "gteps": fixed[best], "roots": k,
+                             "switched_over_best_fixed": switched / fixed[best]}
     return out
 
 
@@ -564,7 +581,40 @@ def run_ours(args):
     # on the launching stream (per-level harness, same state for every variant)
     if not args.no_roofline:
         hbm, src = peaks()
+        # The timed region runs one kernel per traversal, k_bfs_persistent (plus a
+        # one-thread state reset), so that launch is the dominant kernel. Its
+        # algorithmic bytes are the schedule-exact bytes of the traversal (every
+        # level's bytes for the variant the tree ran there), replayed on the host
+        # for a sample of roots; its duration is the CUDA-event time of the same
+        # roots in the timed steps above (mean over steps).
+        per_root_s = np.array(times, dtype=np.float64).reshape(args.steps, R).mean(axis=0)
+        sample = list(range(min(4, R)))
+        b_sched, b_td, t_sum = [], [], 0.0
+        for i in sample:
+            r = int(roots[i])
+            st = bfs.bfs_run_ex(G.handle, r, depth[0], stream, stats=True, log_capacity=4096)
+            dep = depth[0].cpu().numpy()
+            nl = st["levels"]
+            feats = np.zeros((nl, 13), dtype=np.int64)
+            feats[:, 8] = st["frontier"][:nl]
+            feats[:, 12] = st["frontier_edges"][:nl]
+            # depth init (4 n) plus every level's bytes for the variant that ran it
+            b_sched.append(4 * g.n + sum(algorithmic_bytes(g, dep, feats, L, int(st["variant"][L])) for L in range(nl)))
+            n_r = st["vertices_reached"]
+            b_td.append(4 * st["edges_reached"] + 8 * n_r + 4 * g.n + 4 * n_r + 8 * n_r)
+            t_sum += float(per_root_s[i])
+        achieved = sum(b_sched) / t_sum / 1e9
         r0 = int(roots[0])
+        line["roofline"] = {
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic_for(f"persistent_root_{r0}"), "peak_source": src,
+            "kernel": "k_bfs_persistent (one launch = one switched traversal; the timed region's only level kernel)",
+            "algorithmic_bytes": int(b_sched[0]), "launch_ms": 1e3 * float(per_root_s[0]),
+            "sample": f"roots {[int(roots[i]) for i in sample]}; algorithmic_bytes, launch_ms and traffic "
+                      f"are those of root {r0}",
+            "top_down_bytes": int(b_td[0]), "frac_top_down": sum(b_td) / t_sum / 1e9 / hbm}
+        # the dominant level, kernel by kernel: the timing harness runs every
+        # variant from the same snapshot of every level (CUDA events per launch)
         feats, ms, tv = bfs.bfs_profile_levels(G.handle, r0, reps=5, stream=stream)
         chosen = np.array([ms[L, tv[L]] for L in range(len(tv))])
         L = int(np.argmax(chosen))
@@ -574,21 +624,32 @@ def run_ours(args):
         dep = depth[0].cpu().numpy()
         nbytes = algorithmic_bytes(g, dep, feats, L, v)
         t = float(chosen[L]) * 1e-3
-        achieved = nbytes / t / 1e9
-        key = f"{bfs.VARIANTS[v]}"
-        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                            "traffic": traffic_for(key), "peak_source": src,
-                            "kernel": f"{bfs.VARIANTS[v]} at level {L} of root {r0}",
-                            "algorithmic_bytes": int(nbytes), "launch_ms": float(chosen[L]),
-                            "share_of_traversal": float(chosen[L] / chosen.sum()),
-                            "per_level_ms_chosen": [round(float(x), 4) for x in chosen],
-                            "per_level_optimal_ms": float(ms.min(axis=1).sum()),
-                            "per_level_tree_ms": float(chosen.sum())}
+        line["roofline"]["dominant_level"] = {
+            "kernel": f"{bfs.VARIANTS[v]} at level {L} of root {r0}", "algorithmic_bytes": int(nbytes),
+            "launch_ms": float(chosen[L]), "achieved": nbytes / t / 1e9, "frac": nbytes / t / 1e9 / hbm,
+            "traffic": traffic_for(bfs.VARIANTS[v]), "share_of_traversal": float(chosen[L] / chosen.sum()),
+            "per_level_ms_chosen": [round(float(x), 4) for x in chosen],
+            "per_level_optimal_ms": float(ms.min(axis=1).sum()), "per_level_tree_ms": float(chosen.sum())}
         # the same traversal inside the real drivers: device timestamps per level
         for name, mode in (("persistent", bfs.MODE_PERSISTENT), ("graph", bfs.MODE_GRAPH)):
             st = bfs.bfs_run_ex(G.handle, r0, depth[0], stream, stats=True, log_capacity=64, mode=mode)
             if "level_ns" in st:
-                line["roofline"][f"per_level_ms_in_{name}"] = [round(float(x) / 1e6, 4) for x in st["level_ns"]]
+                line["roofline"]["dominant_level"][f"per_level_ms_in_{name}"] = \
+                    [round(float(x) / 1e6, 4) for x in st["level_ns"]]
+        # tree schedule against the per-level optimal schedule over 16 roots
+        tree_ms = opt_ms = 0.0
+        fixed_ms = np.zeros(bfs.NUM_VARIANTS)
+        k16 = min(16, R)
+        for r in roots[:k16]:
+            _, ms_r, tv_r = bfs.bfs_profile_levels(G.handle, int(r), reps=3, stream=stream)
+            tree_ms += float(sum(ms_r[L, tv_r[L]] for L in range(len(tv_r))))
+            opt_ms += float(ms_r.min(axis=1).sum())
+            fixed_ms += ms_r.sum(axis=0)
+        line["schedule_vs_optimal"] = {
+            "roots": k16, "tree_level_ms": tree_ms, "optimal_level_ms": opt_ms, "tree_over_optimal": tree_ms / opt_ms,
+            "best_fixed_over_optimal": float(fixed_ms.min()) / opt_ms,
+            "note": "sums of per-level kernel times from the timing harness (each variant from the same snapshot); "
+                    "init and driver overheads excluded"}
 
     G.close()
     del depth
@@ -619,6 +680,19 @@ def run_ours(args):
                 break
         line["cpu_baseline"] = {"value": harmonic_gteps(ts, es), "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{len(ts)} of the {R} roots, single-threaded FIFO BFS on the same graph"}
+        # throughput mode: independent roots at once, one oracle call per host core
+        # (the C oracle runs outside the GIL)
+        from concurrent.futures import ThreadPoolExecutor
+        cores = os.cpu_count() or 1
+        sample = [int(r) for r in roots[:min(R, 2 * cores)]]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=cores) as ex:
+            done = list(ex.map(lambda r: oracle.bfs(g.off, g.idx, r).edges_reached, sample))
+        wall = time.perf_counter() - t0
+        line["cpu_baseline_throughput"] = {
+            "value": float(sum(done)) / 2 / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(sample)} of the {R} roots, {cores} concurrent single-threaded oracle runs; "
+                      "aggregate edges/2 over wall time"}
 
     G.close()
     if rank == 0:
