@@ -497,6 +497,47 @@ __device__ void body_pe_scan(const Buffers& b, int f) {
   }
 }
 
+// A frontier of at most kPeSmall vertices fits one scan tile: every block then
+// scans the frontier degrees itself, in shared memory, and the level needs no
+// grid-wide scan phases (no extra grid barriers in the persistent kernel, no
+// work in the reduce/top/scan launches of the other drivers).
+constexpr int kPeSmall = kPeTile - 1;
+
+// s_a, s_beg: kPeTile + 1 entries. On return s_a[1 + i] is the exclusive scan
+// of the frontier degrees at i (s_a[1 + f] their total) and s_beg[1 + i] the
+// row start of frontier entry i; entry 0 of both is 0, the value the expand
+// uses before the first frontier entry. f <= kPeSmall.
+__device__ void pe_small_scan(const DevGraph& g, const Level& lv, int32_t* s_a, int32_t* s_beg) {
+  const int f = lv.frontier;
+  const int base = (int)threadIdx.x * kPeItems;
+  int32_t d[kPeItems];
+  int32_t run = 0;
+#pragma unroll
+  for (int k = 0; k < kPeItems; ++k) {
+    const int i = base + k;
+    int32_t deg = 0;
+    if (i < f) {
+      const int32_t u = lv.qin[i];
+      const int32_t b0 = g.off[u];
+      deg = g.off[u + 1] - b0;
+      s_beg[1 + i] = b0;
+    }
+    d[k] = run;
+    run += deg;
+  }
+  long long tot;
+  const long long ex = block_exclusive_scan<long long>((long long)run, &tot);
+#pragma unroll
+  for (int k = 0; k < kPeItems; ++k)
+    if (base + k < f) s_a[1 + base + k] = (int32_t)(ex + d[k]);
+  if (threadIdx.x == 0) {
+    s_a[0] = 0;
+    s_beg[0] = 0;
+    if (f <= kPeSmall) s_a[1 + f] = (int32_t)tot;  // callers guarantee it; the check keeps s_a in bounds
+  }
+  __syncthreads();
+}
+
 // Merge-path split: how many of the first d items of merge(A[0..na), j0+[0..nb))
 // are A items, with A first on ties (A[i] <= edge index => boundary first).
 __device__ __forceinline__ int merge_split(const int32_t* a, int na, long long j0, int nb, long long d) {
@@ -512,16 +553,19 @@ __device__ __forceinline__ int merge_split(const int32_t* a, int na, long long j
 }
 
 // s_a, s_beg: kPeTile + 1 entries of shared memory each; s_split: 2 ints.
-__device__ void body_pe_expand(const DevGraph& g, const Level& lv, const Buffers& b, const Stage& stage, int32_t* s_a,
-                               int32_t* s_beg, int* s_split, unsigned long long& edges) {
+// kSmall: the scan is already in s_a / s_beg (pe_small_scan), not in b.
+template <bool kSmall>
+__device__ void body_pe_expand(const DevGraph& g, const Level& lv, const Buffers& b, const Stage& stage,
+                               int32_t* s_a_buf, int32_t* s_beg_buf, int* s_split, unsigned long long& edges) {
   const int f = lv.frontier;
-  const int32_t E = b.pe_scan[f];
+  const int32_t* scan = kSmall ? s_a_buf + 1 : b.pe_scan;
+  const int32_t E = scan[f];
   const long long total = (long long)f + E;
   const long long ntiles = (total + kPeTile - 1) / kPeTile;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const long long d0 = t * kPeTile;
     const long long d1 = min(d0 + kPeTile, total);
-    if (threadIdx.x < 2) s_split[threadIdx.x] = merge_split(b.pe_scan, f, 0, E, threadIdx.x ? d1 : d0);
+    if (threadIdx.x < 2) s_split[threadIdx.x] = merge_split(scan, f, 0, E, threadIdx.x ? d1 : d0);
     __syncthreads();
     const int i0 = s_split[0], i1 = s_split[1];
     const int na = i1 - i0;
@@ -529,12 +573,19 @@ __device__ void body_pe_expand(const DevGraph& g, const Level& lv, const Buffers
     const int nb = tl - na;
     const long long j0 = d0 - i0;
     // s index k <-> frontier entry i0 - 1 + k (the vertex owning edge j0 may precede the tile)
-    for (int k = threadIdx.x; k <= na; k += blockDim.x) {
-      const int gi = i0 - 1 + k;
-      s_a[k] = gi >= 0 ? b.pe_scan[gi] : 0;
-      s_beg[k] = gi >= 0 ? b.pe_beg[gi] : 0;
+    const int32_t* s_a = s_a_buf;
+    const int32_t* s_beg = s_beg_buf;
+    if (kSmall) {
+      s_a = s_a_buf + i0;  // s_a_buf[1 + i] holds entry i, s_a_buf[0] the 0 before entry 0
+      s_beg = s_beg_buf + i0;
+    } else {
+      for (int k = threadIdx.x; k <= na; k += blockDim.x) {
+        const int gi = i0 - 1 + k;
+        s_a_buf[k] = gi >= 0 ? b.pe_scan[gi] : 0;
+        s_beg_buf[k] = gi >= 0 ? b.pe_beg[gi] : 0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     const int td0 = min((int)threadIdx.x * kPeItems, tl);
     const int td1 = min(td0 + kPeItems, tl);
     const int ti = merge_split(s_a + 1, na, j0, nb, td0);
@@ -807,18 +858,26 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
   block_add_u64(edges, &st->next_edges);
 }
 
+// (A frontier of at most kPeSmall vertices is scanned by k_pe_expand itself:
+// the three scan launches then return at once.)
 __global__ void __launch_bounds__(kThreads) k_pe_reduce(DevGraph g, Buffers b, RunState* st) {
-  body_pe_reduce(g, load_level(b, st), b);
+  const Level lv = load_level(b, st);
+  if (lv.frontier <= kPeSmall) return;
+  body_pe_reduce(g, lv, b);
 }
 
 __global__ void __launch_bounds__(kThreads) k_pe_top(DevGraph g, Buffers b, RunState* st) {
   (void)g;
-  body_pe_top(b, st->frontier);
+  const int f = st->frontier;
+  if (f <= kPeSmall) return;
+  body_pe_top(b, f);
 }
 
 __global__ void __launch_bounds__(kThreads) k_pe_scan(DevGraph g, Buffers b, RunState* st) {
   (void)g;
-  body_pe_scan(b, st->frontier);
+  const int f = st->frontier;
+  if (f <= kPeSmall) return;
+  body_pe_scan(b, f);
 }
 
 __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, RunState* st) {
@@ -828,7 +887,12 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
   BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(b, st);
   unsigned long long edges = 0;
-  body_pe_expand(g, lv, b, stage, s_a, s_beg, s_split, edges);
+  if (lv.frontier <= kPeSmall) {
+    pe_small_scan(g, lv, s_a, s_beg);
+    body_pe_expand<true>(g, lv, b, stage, s_a, s_beg, s_split, edges);
+  } else {
+    body_pe_expand<false>(g, lv, b, stage, s_a, s_beg, s_split, edges);
+  }
   block_add_u64(edges, &st->next_edges);
 }
 
@@ -945,13 +1009,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
       case V_PUSH_WARP: body_push_warp(g, lv, stage, vw, edges); break;
       case V_PUSH_CTA: body_push_cta(g, lv, stage, pp, &st->status, edges); break;
       case V_PUSH_EDGE:
+        if ((int)f <= kPeSmall) {
+          pe_small_scan(g, lv, ubuf, ubuf + kPeSlot);
+          body_pe_expand<true>(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
+          break;
+        }
         body_pe_reduce(g, lv, b);
         if (!grid_sync(st)) break;
         if (blockIdx.x == 0) body_pe_top(b, (int)f);
         if (!grid_sync(st)) break;
         body_pe_scan(b, (int)f);
         if (!grid_sync(st)) break;
-        body_pe_expand(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
+        body_pe_expand<false>(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
         break;
       default: body_pull<false, kPullWordsPersistent>(g, lv, stage, edges); break;
     }
