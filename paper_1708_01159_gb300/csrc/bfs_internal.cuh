@@ -98,6 +98,7 @@ struct RunState {
   unsigned long long edg3[3];
   unsigned int bar_gen;
   int32_t pad2_;
+  unsigned long long lvl_word;  // persistent driver: level barrier word (phase, next f and e)
   int32_t log_cap;
   int32_t pad_;
   int32_t* log_variant;
@@ -299,6 +300,62 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* 
     }
   }
   return __syncthreads_and(ok) != 0;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// The grid barrier that ends a level of the persistent kernel, carrying the
+// next level's frontier size f and frontier edge count e to every block: the
+// last arrival reads the two counters (every other block's appends were
+// released by its arrival and acquired by the last one's) and publishes them
+// with a flipped phase bit in one 64-bit release store, so the waiting blocks
+// get them with the poll that ends their wait instead of one more round trip
+// to the counters. Layout of *word: bit 63 phase, bits 31-61 e, bits 0-30 f
+// (both below 2^31: f <= n and e <= m). Bounded like grid_barrier.
+__device__ __forceinline__ bool level_barrier(unsigned int* count, unsigned long long* word, int32_t* status,
+                                              const unsigned int* next_f, const unsigned long long* next_e,
+                                              unsigned int* f_out, unsigned long long* e_out) {
+  __shared__ unsigned long long s_word;
+  constexpr unsigned long long kMask31 = (1ull << 31) - 1ull;
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    const unsigned long long w0 = ld_acquire_u64(word);
+    const unsigned long long phase = w0 >> 63;
+    const unsigned int arrived = atom_add_acq_rel_u32(count, 1u);
+    unsigned long long w = w0;
+    if (arrived == gridDim.x - 1) {
+      *count = 0;
+      const unsigned long long f = *reinterpret_cast<const volatile unsigned int*>(next_f);
+      const unsigned long long e = *reinterpret_cast<const volatile unsigned long long*>(next_e);
+      w = ((phase ^ 1ull) << 63) | (min(e, kMask31) << 31) | min(f, kMask31);
+      st_release_u64(word, w);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (((w = ld_acquire_u64(word)) >> 63) == phase) {
+        if (*reinterpret_cast<volatile int32_t*>(status) != ST_OK || global_ns() - t0 > kWaitLimitNs) {
+          *status = ST_TIMEOUT;
+          ok = false;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    s_word = w;
+  }
+  ok = __syncthreads_and(ok) != 0;
+  const unsigned long long w = s_word;
+  *f_out = (unsigned int)(w & kMask31);
+  *e_out = (w >> 31) & kMask31;
+  return ok;
 }
 
 // Try to claim vertex v: set its visited bit. True only for the one thread

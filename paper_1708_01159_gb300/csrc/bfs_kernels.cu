@@ -970,10 +970,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   long long discovered = 0, reached = 0;
   int32_t prev = -1;
   uint32_t vsel = 0;
+  // level 0's frontier is the root; later levels' f and e arrive with the barrier
+  unsigned int f = 1;
+  unsigned long long e = (unsigned long long)(g.off[root + 1] - g.off[root]);
   bool ok = grid_sync(st);
   for (; ok; ++L) {
-    const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&st->cnt3[L % 3]);
-    const unsigned long long e = *reinterpret_cast<volatile unsigned long long*>(&st->edg3[L % 3]);
     discovered += f;
     reached += (long long)e;
     if (f == 0) break;
@@ -1028,7 +1029,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     block_add_u64(edges, &st->edg3[(L + 1) % 3]);
     if (v == V_PULL) vsel ^= 1u;
     prev = v;
-    ok = grid_sync(st);
+    ok = level_barrier(&st->bar_count, &st->lvl_word, &st->status, &st->cnt3[(L + 1) % 3], &st->edg3[(L + 1) % 3],
+                       &f, &e);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->levels = L;
