@@ -211,18 +211,35 @@ __device__ __forceinline__ void init_fill(const DevGraph& g, uint32_t* vis0, int
 // Tree evaluation (Section 2.1 walk over the Section 4.1 features, with the
 // Section 4.1 unknown-prediction rule). Returns the variant; fills feat[].
 // ---------------------------------------------------------------------------
+// Value of feature fi at this level, computed on demand: a walk reads at most
+// the tree's depth of them, and each ppm share costs a 64-bit division.
+__device__ __forceinline__ long long feature_value(const DevGraph& g, int32_t fi, int32_t L, long long f, long long e,
+                                                   long long discovered) {
+  switch (fi) {
+    case 0: return g.gfeat[0];
+    case 1: return g.gfeat[1];
+    case 2: return g.gfeat[2];
+    case 3: return g.gfeat[3];
+    case 4: return g.gfeat[4];
+    case 5: return g.gfeat[5];
+    case 6: return g.gfeat[6];
+    case 7: return g.gfeat[7];
+    case F_FRONTIER: return f;
+    case F_FRONTIER_PPM: return (1000000ll * f) / g.n;
+    case F_DISCOVERED: return discovered;
+    case F_DISCOVERED_PPM: return (1000000ll * discovered) / g.n;
+    case F_FRONTIER_EDGES: return e;
+    default: return L;  // F_LEVEL
+  }
+}
+
+// x: when not null, receives every feature (for the per-level log).
 __device__ int32_t decide_variant(const DevGraph& g, const TreeNode* tree, int32_t nodes, int32_t forced, int32_t L,
                                   long long f, long long e, long long discovered, int32_t prev, long long* x,
                                   int32_t* vw) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i) x[i] = g.gfeat[i];
-  const long long n = g.n;
-  x[F_FRONTIER] = f;
-  x[F_FRONTIER_PPM] = (1000000ll * f) / n;
-  x[F_DISCOVERED] = discovered;
-  x[F_DISCOVERED_PPM] = (1000000ll * discovered) / n;
-  x[F_FRONTIER_EDGES] = e;
-  x[F_LEVEL] = L;
+  if (x) {
+    for (int i = 0; i < F_NUM; ++i) x[i] = feature_value(g, i, L, f, e, discovered);
+  }
   int32_t v = forced;
   if (v < 0) {
     v = -1;
@@ -234,16 +251,15 @@ __device__ int32_t decide_variant(const DevGraph& g, const TreeNode* tree, int32
           v = nd.v;
           break;
         }
-        i = (x[nd.f] <= nd.t) ? nd.l : nd.r;
+        i = (feature_value(g, nd.f, L, f, e, discovered) <= nd.t) ? nd.l : nd.r;
       }
     }
     if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : prev;  // unknown prediction
     if (v < 0 || v >= V_NUM) v = kLevel0Default;
   }
   // virtual-warp width: the power of two nearest above the frontier's mean
-  // degree, clamped to [4, 32]
-  const long long avg = f > 0 ? e / f : 0;
-  *vw = avg <= 4 ? 4 : avg <= 8 ? 8 : avg <= 16 ? 16 : 32;
+  // degree floor(e / f), clamped to [4, 32]; floor(e / f) <= k is e < (k + 1) f
+  *vw = (f <= 0 || e < 5 * f) ? 4 : e < 9 * f ? 8 : e < 17 * f ? 16 : 32;
   return v;
 }
 
@@ -982,9 +998,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
       if (blockIdx.x == 0 && threadIdx.x == 0) st->status = ST_TIMEOUT;
       break;
     }
-    long long x[F_NUM];
     int32_t vw = 32;
-    const int32_t v = decide_variant(g, walk_tree, tree_nodes, forced, L, f, (long long)e, discovered, prev, x, &vw);
+    const int32_t v =
+        decide_variant(g, walk_tree, tree_nodes, forced, L, f, (long long)e, discovered, prev, nullptr, &vw);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->cnt3[(L + 2) % 3] = 0;  // last read by level L - 1, which every block has finished
       st->edg3[(L + 2) % 3] = 0;
