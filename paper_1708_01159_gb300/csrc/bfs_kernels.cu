@@ -233,6 +233,73 @@ __device__ __forceinline__ long long feature_value(const DevGraph& g, int32_t fi
   }
 }
 
+// The split test x_fi <= t of a tree node, without dividing for the ppm
+// shares: floor(1e6 c / n) <= t is 1e6 c < (t + 1) n for 0 <= t < 1e6, always
+// true for t >= 1e6 (c <= n) and never for t < 0.
+__device__ __forceinline__ bool feature_le(const DevGraph& g, int32_t fi, long long t, int32_t L, long long f,
+                                          long long e, long long discovered) {
+  if (fi == F_FRONTIER_PPM || fi == F_DISCOVERED_PPM) {
+    const long long c = fi == F_FRONTIER_PPM ? f : discovered;
+    if (t < 0) return false;
+    if (t >= 1000000) return true;
+    return 1000000ll * c < (t + 1) * (long long)g.n;
+  }
+  return feature_value(g, fi, L, f, e, discovered) <= t;
+}
+
+// Section 2.1 walk of an integer tree; -1 for an unknown leaf.
+__device__ __forceinline__ int32_t walk_tree(const DevGraph& g, const TreeNode* tree, int32_t nodes, int32_t L,
+                                             long long f, long long e, long long discovered) {
+  int32_t i = 0;
+  for (int32_t step = 0; step <= nodes; ++step) {
+    const TreeNode nd = tree[i];
+    if (nd.f < 0) return nd.v;
+    i = feature_le(g, nd.f, nd.t, L, f, e, discovered) ? nd.l : nd.r;
+  }
+  return -1;
+}
+
+// A tree node packed in 16 bytes for the shared-memory copy in the persistent
+// kernel (one vector load per step): the threshold, then f | l << 16 and
+// r | v << 16 as 16-bit fields (trees kept there have at most 255 nodes).
+struct __align__(16) PackedNode {
+  long long t;
+  int32_t fl;
+  int32_t rv;
+};
+
+__device__ __forceinline__ PackedNode pack_node(const TreeNode& nd) {
+  PackedNode p;
+  p.t = nd.t;
+  p.fl = (int32_t)(((uint32_t)nd.f & 0xffffu) | ((uint32_t)nd.l << 16));
+  p.rv = (int32_t)(((uint32_t)nd.r & 0xffffu) | ((uint32_t)nd.v << 16));
+  return p;
+}
+
+__device__ __forceinline__ int32_t walk_packed(const DevGraph& g, const PackedNode* tree, int32_t nodes, int32_t L,
+                                               long long f, long long e, long long discovered) {
+  int32_t i = 0;
+  for (int32_t step = 0; step <= nodes; ++step) {
+    const PackedNode nd = tree[i];
+    const int32_t fi = (int16_t)(nd.fl & 0xffff);
+    if (fi < 0) return nd.rv >> 16;
+    i = feature_le(g, fi, nd.t, L, f, e, discovered) ? (nd.fl >> 16) : (int32_t)(int16_t)(nd.rv & 0xffff);
+  }
+  return -1;
+}
+
+// Section 4.1 unknown-prediction rule on a walk's result (or the forced
+// variant), and the virtual-warp width: the power of two nearest above the
+// frontier's mean degree floor(e / f), clamped to [4, 32] (floor(e / f) <= k is
+// e < (k + 1) f).
+__device__ __forceinline__ int32_t finish_variant(int32_t v, int32_t L, int32_t prev, long long f, long long e,
+                                                  int32_t* vw) {
+  if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : prev;  // unknown prediction
+  if (v < 0 || v >= V_NUM) v = kLevel0Default;
+  *vw = (f <= 0 || e < 5 * f) ? 4 : e < 9 * f ? 8 : e < 17 * f ? 16 : 32;
+  return v;
+}
+
 // x: when not null, receives every feature (for the per-level log).
 __device__ int32_t decide_variant(const DevGraph& g, const TreeNode* tree, int32_t nodes, int32_t forced, int32_t L,
                                   long long f, long long e, long long discovered, int32_t prev, long long* x,
@@ -241,26 +308,8 @@ __device__ int32_t decide_variant(const DevGraph& g, const TreeNode* tree, int32
     for (int i = 0; i < F_NUM; ++i) x[i] = feature_value(g, i, L, f, e, discovered);
   }
   int32_t v = forced;
-  if (v < 0) {
-    v = -1;
-    if (tree != nullptr && nodes > 0) {
-      int32_t i = 0;
-      for (int32_t step = 0; step <= nodes; ++step) {
-        const TreeNode nd = tree[i];
-        if (nd.f < 0) {
-          v = nd.v;
-          break;
-        }
-        i = (feature_value(g, nd.f, L, f, e, discovered) <= nd.t) ? nd.l : nd.r;
-      }
-    }
-    if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : prev;  // unknown prediction
-    if (v < 0 || v >= V_NUM) v = kLevel0Default;
-  }
-  // virtual-warp width: the power of two nearest above the frontier's mean
-  // degree floor(e / f), clamped to [4, 32]; floor(e / f) <= k is e < (k + 1) f
-  *vw = (f <= 0 || e < 5 * f) ? 4 : e < 9 * f ? 8 : e < 17 * f ? 16 : 32;
-  return v;
+  if (v < 0) v = (tree != nullptr && nodes > 0) ? walk_tree(g, tree, nodes, L, f, e, discovered) : -1;
+  return finish_variant(v, L, prev, f, e, vw);
 }
 
 // ---------------------------------------------------------------------------
@@ -960,11 +1009,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   __shared__ int s_split[2];
   // the tree is walked by every block every level: keep it in shared memory
   constexpr int kSmemTree = 255;
-  __shared__ TreeNode s_tree[kSmemTree];
+  __shared__ PackedNode s_tree[kSmemTree];
   const bool tree_in_smem = tree != nullptr && tree_nodes > 0 && tree_nodes <= kSmemTree;
   if (tree_in_smem)
-    for (int i = threadIdx.x; i < tree_nodes; i += blockDim.x) s_tree[i] = tree[i];
-  const TreeNode* walk_tree = tree_in_smem ? s_tree : tree;
+    for (int i = threadIdx.x; i < tree_nodes; i += blockDim.x) s_tree[i] = pack_node(tree[i]);
   BFS_DECLARE_STAGE(stage);
   init_fill(g, b.vis[0], depth, root);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -999,8 +1047,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
       break;
     }
     int32_t vw = 32;
-    const int32_t v =
-        decide_variant(g, walk_tree, tree_nodes, forced, L, f, (long long)e, discovered, prev, nullptr, &vw);
+    int32_t v = forced;
+    if (v < 0 && tree != nullptr && tree_nodes > 0)
+      v = tree_in_smem ? walk_packed(g, s_tree, tree_nodes, L, f, (long long)e, discovered)
+                       : walk_tree(g, tree, tree_nodes, L, f, (long long)e, discovered);
+    v = finish_variant(v, L, prev, f, (long long)e, &vw);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->cnt3[(L + 2) % 3] = 0;  // last read by level L - 1, which every block has finished
       st->edg3[(L + 2) % 3] = 0;
