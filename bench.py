@@ -474,7 +474,7 @@ def run_ours(args):
         st = bfs.bfs_run_ex(G.handle, int(r), depth[0], stats=True, log_capacity=4096)
         edges.append(st["edges_reached"])
         if args.mode in ("default", "persistent"):
-            launches += 2  # state reset + one cooperative persistent kernel per traversal
+            launches += 1  # one cooperative persistent kernel per traversal
         else:  # init, (graph: loop start), per level decide + the variant's kernels, final decide
             kern = {0: 1, 1: 1, 2: 1, 3: 4, 4: 1}
             launches += 2 + (args.mode == "graph") + sum(1 + kern[int(v)] for v in st["variant"])
@@ -581,8 +581,8 @@ def run_ours(args):
     # on the launching stream (per-level harness, same state for every variant)
     if not args.no_roofline:
         hbm, src = peaks()
-        # The timed region runs one kernel per traversal, k_bfs_persistent (plus a
-        # one-thread state reset), so that launch is the dominant kernel. Its
+        # The timed region runs one kernel per traversal, k_bfs_persistent, so
+        # that launch is the dominant kernel. Its
         # algorithmic bytes are the schedule-exact bytes of the traversal (every
         # level's bytes for the variant the tree ran there), replayed on the host
         # for a sample of roots; its duration is the CUDA-event time of the same

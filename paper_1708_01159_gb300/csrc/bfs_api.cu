@@ -169,6 +169,7 @@ struct Workspace {
   cudaGraphNode_t start_node = nullptr;
   cudaEvent_t done = nullptr;
   cudaStream_t last_stream = nullptr;
+  uint32_t epoch = 0;  // persistent launches so far (the kernel's barrier-state reset handshake)
   bool in_use = false;
   size_t bytes = 0;
   std::vector<void*> allocs;
@@ -457,14 +458,13 @@ int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int3
 // barrier counts gridDim), so several traversals can be resident at once.
 int launch_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced,
                       cudaStream_t stream, int32_t grid_blocks) {
-  k_persist_reset<<<1, 1, 0, stream>>>(ws->st);
-  CU(cudaGetLastError());
   DevGraph dg = g->dg;
   Buffers b = ws->b;
   RunState* st = ws->st;
   const TreeNode* tree = g->tree;
   int32_t nodes = g->tree_nodes;
-  void* args[] = {&dg, &b, &st, &depth, &root, &forced, &tree, &nodes};
+  uint32_t epoch = ++ws->epoch;  // runs on one workspace are ordered, so consecutive launches differ
+  void* args[] = {&dg, &b, &st, &depth, &root, &forced, &tree, &nodes, &epoch};
   const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->shapes.persist) : g->shapes.persist;
   CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_bfs_persistent), dim3(grid), dim3(kThreads), args, 0,
                                  stream));

@@ -99,6 +99,8 @@ struct RunState {
   unsigned int bar_gen;
   int32_t pad2_;
   unsigned long long lvl_word;  // persistent driver: level barrier word (phase, next f and e)
+  unsigned int run_epoch;       // persistent driver: epoch of the launch whose block 0 reset the barrier state
+  int32_t pad3_;
   int32_t log_cap;
   int32_t pad_;
   int32_t* log_variant;

@@ -993,14 +993,20 @@ __global__ void k_undo_level(Buffers b, RunState* st) {
   }
 }
 
-__global__ void k_persist_reset(RunState* st) {
-  st->status = ST_OK;
-  st->bar_count = 0;
-}
 
+// epoch: a number the host changes on every launch on this workspace. Block 0
+// clears the barrier counter and the status word left by the previous run
+// (which a failed run may leave set) and then publishes epoch; every other
+// block waits for it before its first barrier, so no separate reset launch is
+// needed.
 __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth,
                                                              int32_t root, int32_t forced, const TreeNode* tree,
-                                                             int32_t tree_nodes) {
+                                                             int32_t tree_nodes, uint32_t epoch) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->bar_count = 0;
+    st->status = ST_OK;
+    st_release_u32(&st->run_epoch, epoch);
+  }
   // one shared buffer serves the CTA variant's copy stage or the edge-centric tile
   constexpr int kPeSlot = kPeTile + 32;
   static_assert(2 * kCtaChunk <= 2 * kPeSlot, "union sizing");
@@ -1019,7 +1025,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     st->depth = depth;
     st->root = root;
     st->forced = forced;
-    st->status = ST_OK;
     st->cnt3[0] = 1;
     st->cnt3[1] = 0;
     st->cnt3[2] = 0;
@@ -1030,6 +1035,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   }
   cta_pipe_init(bar);
   CtaPipe pp{ubuf, bar, 0u, 0u};
+  // the previous run's barrier state is cleared before any block arrives
+  if (blockIdx.x != 0 && threadIdx.x == 0) {
+    const unsigned long long t0 = global_ns();
+    while (ld_acquire_u32(&st->run_epoch) != epoch)
+      if (global_ns() - t0 > kWaitLimitNs) break;  // the first barrier then times out and reports it
+  }
   int32_t L = 0;
   long long discovered = 0, reached = 0;
   int32_t prev = -1;
