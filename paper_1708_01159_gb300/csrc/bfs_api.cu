@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <sstream>
@@ -199,6 +200,7 @@ struct bfs_graph {
   // still be read by runs in flight, so they live until destroy)
   std::vector<TreeNode*> trees;
   TreeNode* tree = nullptr;
+  QsTree* tree_qs = nullptr;  // bit-parallel form of the same tree (inside the same allocation), or null
   int32_t tree_nodes = 0;
   uint64_t tree_version = 0;
   // multi-source buffers (allocated on the first batch; batches on one graph
@@ -424,20 +426,79 @@ int release(bfs_graph* g, Workspace* ws, cudaStream_t stream) {
   return BFS_OK;
 }
 
+// Bit-parallel form of a tree (QsTree): leaves numbered by a left-first
+// depth-first walk from node 0, each internal node's mask clearing its left
+// subtree's leaves. False when the tree is too large for it or node 0 does not
+// root a tree (a node reached twice).
+bool build_qs(const std::vector<TreeNode>& t, QsTree* q) {
+  if (t.empty() || t.size() > 1024) return false;
+  std::memset(q, 0, sizeof *q);
+  std::vector<int> lo(t.size(), 0), hi(t.size(), 0);
+  std::vector<char> seen(t.size(), 0);
+  int nleaf = 0, nint = 0;
+  bool ok = true;
+  std::function<void(int)> dfs = [&](int i) {
+    if (!ok || i < 0 || i >= (int)t.size() || seen[i]) {
+      ok = false;
+      return;
+    }
+    seen[i] = 1;
+    const TreeNode& nd = t[i];
+    if (nd.f < 0) {
+      if (nleaf >= kQsMax) {
+        ok = false;
+        return;
+      }
+      q->leaf[nleaf] = nd.v;
+      lo[i] = nleaf;
+      hi[i] = ++nleaf;
+      return;
+    }
+    dfs(nd.l);
+    dfs(nd.r);
+    if (!ok || nint >= kQsMax) {
+      ok = false;
+      return;
+    }
+    lo[i] = lo[nd.l];
+    hi[i] = hi[nd.r];
+    QsNode& qn = q->node[nint++];
+    qn.t = nd.t;
+    qn.f = nd.f;
+    unsigned long long m = ~0ull;
+    for (int b = lo[nd.l]; b < hi[nd.l]; ++b) m &= ~(1ull << b);
+    qn.mask = m;
+  };
+  dfs(0);
+  if (!ok) return false;
+  q->n_int = nint;
+  q->n_leaf = nleaf;
+  return true;
+}
+
 int sync_tree(bfs_graph* g) {
   TreeStore& ts = tree_store();
   std::lock_guard<std::mutex> lk(ts.mu);
   std::lock_guard<std::mutex> lk2(g->mu);
   if (g->tree_version == ts.version && g->tree) return BFS_OK;
+  // one device block: the node array, then the bit-parallel form when it exists
+  const size_t tree_bytes = ts.nodes.size() * sizeof(TreeNode);
+  const size_t qs_off = (tree_bytes + 15) & ~size_t(15);
+  QsTree qs;
+  const bool has_qs = build_qs(ts.nodes, &qs);
+  std::vector<char> host(qs_off + sizeof(QsTree), 0);
+  std::memcpy(host.data(), ts.nodes.data(), tree_bytes);
+  if (has_qs) std::memcpy(host.data() + qs_off, &qs, sizeof qs);
   void* p = nullptr;
-  TRY(dmalloc(&p, ts.nodes.size() * sizeof(TreeNode)));
-  const int r = upload_now(p, ts.nodes.data(), ts.nodes.size() * sizeof(TreeNode));
+  TRY(dmalloc(&p, host.size()));
+  const int r = upload_now(p, host.data(), host.size());
   if (r != BFS_OK) {
     cudaFree(p);
     return r;
   }
   g->trees.push_back(static_cast<TreeNode*>(p));
   g->tree = static_cast<TreeNode*>(p);
+  g->tree_qs = has_qs ? reinterpret_cast<QsTree*>(static_cast<char*>(p) + qs_off) : nullptr;
   g->tree_nodes = (int32_t)ts.nodes.size();
   g->tree_version = ts.version;
   return BFS_OK;
@@ -463,8 +524,9 @@ int launch_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth,
   RunState* st = ws->st;
   const TreeNode* tree = g->tree;
   int32_t nodes = g->tree_nodes;
+  const QsTree* qs = g->tree_qs;
   uint32_t epoch = ++ws->epoch;  // runs on one workspace are ordered, so consecutive launches differ
-  void* args[] = {&dg, &b, &st, &depth, &root, &forced, &tree, &nodes, &epoch};
+  void* args[] = {&dg, &b, &st, &depth, &root, &forced, &tree, &nodes, &qs, &epoch};
   const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->shapes.persist) : g->shapes.persist;
   CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_bfs_persistent), dim3(grid), dim3(kThreads), args, 0,
                                  stream));

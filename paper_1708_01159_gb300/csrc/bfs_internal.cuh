@@ -52,6 +52,28 @@ struct TreeNode {
 };
 static_assert(sizeof(TreeNode) == 24, "TreeNode layout");
 
+// Bit-parallel form of a small tree (the QuickScorer evaluation of Lucchese et
+// al., SIGIR 2015): the leaves are numbered left to right; internal node k,
+// when its test x[f] <= t fails, clears the bits of the leaves of its left
+// subtree; after every failed test has cleared its bits, the lowest bit left
+// is the leaf the walk from the root reaches. All tests are independent, so a
+// block evaluates one per thread and ANDs the masks, instead of a chain of
+// dependent steps. Built on the host for trees of at most kQsMax internal
+// nodes and kQsMax leaves.
+constexpr int kQsMax = 64;
+struct QsNode {
+  long long t;
+  unsigned long long mask;  // all ones except the bits of the left subtree's leaves
+  int32_t f;
+  int32_t pad;
+};
+struct QsTree {
+  int32_t n_int;   // internal nodes
+  int32_t n_leaf;  // leaves
+  QsNode node[kQsMax];
+  int32_t leaf[kQsMax];  // class of each leaf, left to right (-1: unknown)
+};
+
 struct DevGraph {
   const int32_t* off;
   const int32_t* idx;

@@ -259,33 +259,26 @@ __device__ __forceinline__ int32_t walk_tree(const DevGraph& g, const TreeNode* 
   return -1;
 }
 
-// A tree node packed in 16 bytes for the shared-memory copy in the persistent
-// kernel (one vector load per step): the threshold, then f | l << 16 and
-// r | v << 16 as 16-bit fields (trees kept there have at most 255 nodes).
-struct __align__(16) PackedNode {
-  long long t;
-  int32_t fl;
-  int32_t rv;
-};
-
-__device__ __forceinline__ PackedNode pack_node(const TreeNode& nd) {
-  PackedNode p;
-  p.t = nd.t;
-  p.fl = (int32_t)(((uint32_t)nd.f & 0xffffu) | ((uint32_t)nd.l << 16));
-  p.rv = (int32_t)(((uint32_t)nd.r & 0xffffu) | ((uint32_t)nd.v << 16));
-  return p;
-}
-
-__device__ __forceinline__ int32_t walk_packed(const DevGraph& g, const PackedNode* tree, int32_t nodes, int32_t L,
-                                               long long f, long long e, long long discovered) {
-  int32_t i = 0;
-  for (int32_t step = 0; step <= nodes; ++step) {
-    const PackedNode nd = tree[i];
-    const int32_t fi = (int16_t)(nd.fl & 0xffff);
-    if (fi < 0) return nd.rv >> 16;
-    i = feature_le(g, fi, nd.t, L, f, e, discovered) ? (nd.fl >> 16) : (int32_t)(int16_t)(nd.rv & 0xffff);
+// The tree's prediction by the bit-parallel form: thread k tests internal
+// node k, the warps AND their masks, the lowest surviving bit names the leaf.
+// Every thread of the block calls it (it synchronises); s_and: one word per
+// warp of shared memory.
+__device__ __forceinline__ int32_t qs_eval(const DevGraph& g, const QsTree& q, int32_t L, long long f, long long e,
+                                           long long discovered, unsigned long long* s_and) {
+  unsigned long long m = ~0ull;
+  if ((int)threadIdx.x < q.n_int) {
+    const QsNode nd = q.node[threadIdx.x];
+    if (!feature_le(g, nd.f, nd.t, L, f, e, discovered)) m = nd.mask;
   }
-  return -1;
+  const uint32_t lo = __reduce_and_sync(kFull, (uint32_t)m);
+  const uint32_t hi = __reduce_and_sync(kFull, (uint32_t)(m >> 32));
+  const int nw = (q.n_int + 31) >> 5;
+  if (lane_id() == 0 && (int)(threadIdx.x >> 5) < nw) s_and[threadIdx.x >> 5] = ((unsigned long long)hi << 32) | lo;
+  __syncthreads();
+  unsigned long long all = ~0ull;
+  for (int k = 0; k < nw; ++k) all &= s_and[k];
+  const int leaf = __ffsll((long long)all) - 1;
+  return (leaf >= 0 && leaf < q.n_leaf) ? q.leaf[leaf] : -1;
 }
 
 // Section 4.1 unknown-prediction rule on a walk's result (or the forced
@@ -1001,7 +994,7 @@ __global__ void k_undo_level(Buffers b, RunState* st) {
 // needed.
 __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth,
                                                              int32_t root, int32_t forced, const TreeNode* tree,
-                                                             int32_t tree_nodes, uint32_t epoch) {
+                                                             int32_t tree_nodes, const QsTree* qs, uint32_t epoch) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->bar_count = 0;
     st->status = ST_OK;
@@ -1013,12 +1006,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   __shared__ alignas(128) int32_t ubuf[2 * kPeSlot];
   __shared__ alignas(8) uint64_t bar[2];
   __shared__ int s_split[2];
-  // the tree is walked by every block every level: keep it in shared memory
-  constexpr int kSmemTree = 255;
-  __shared__ PackedNode s_tree[kSmemTree];
-  const bool tree_in_smem = tree != nullptr && tree_nodes > 0 && tree_nodes <= kSmemTree;
-  if (tree_in_smem)
-    for (int i = threadIdx.x; i < tree_nodes; i += blockDim.x) s_tree[i] = pack_node(tree[i]);
+  // the tree is evaluated by every block every level: its bit-parallel form
+  // (trees of up to 64 leaves) is kept in shared memory; larger trees are
+  // walked in global memory
+  __shared__ QsTree s_qs;
+  __shared__ unsigned long long s_and[kThreads / 32];
+  const bool use_qs = qs != nullptr;
+  if (use_qs) {
+    static_assert(sizeof(QsTree) % 4 == 0, "QsTree copy");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(qs);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&s_qs);
+    for (int i = threadIdx.x; i < (int)(sizeof(QsTree) / 4); i += blockDim.x) dst[i] = src[i];
+  }
   BFS_DECLARE_STAGE(stage);
   init_fill(g, b.vis[0], depth, root);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1059,9 +1058,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     }
     int32_t vw = 32;
     int32_t v = forced;
-    if (v < 0 && tree != nullptr && tree_nodes > 0)
-      v = tree_in_smem ? walk_packed(g, s_tree, tree_nodes, L, f, (long long)e, discovered)
-                       : walk_tree(g, tree, tree_nodes, L, f, (long long)e, discovered);
+    if (v < 0 && use_qs)
+      v = qs_eval(g, s_qs, L, f, (long long)e, discovered, s_and);
+    else if (v < 0 && tree != nullptr && tree_nodes > 0)
+      v = walk_tree(g, tree, tree_nodes, L, f, (long long)e, discovered);
     v = finish_variant(v, L, prev, f, (long long)e, &vw);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->cnt3[(L + 2) % 3] = 0;  // last read by level L - 1, which every block has finished

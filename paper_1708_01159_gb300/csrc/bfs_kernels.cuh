@@ -25,7 +25,7 @@ __global__ void k_pe_expand(DevGraph g, Buffers b, RunState* st);
 __global__ void k_pull(DevGraph g, Buffers b, RunState* st);
 __global__ void k_undo_level(Buffers b, RunState* st);
 __global__ void k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root, int32_t forced,
-                                 const TreeNode* tree, int32_t tree_nodes, uint32_t epoch);
+                                 const TreeNode* tree, int32_t tree_nodes, const QsTree* qs, uint32_t epoch);
 
 // graph creation
 __global__ void k_validate(const int32_t* off, const int32_t* idx, int32_t n, int32_t m, int32_t* bad);

@@ -267,6 +267,58 @@ def test_custom_tree_file_with_unknown_leaves(tmp_path):
         bfs.bfs_load_tree(None)
 
 
+def _random_tree(rng, depth, feats_pool, node_limit=None):
+    """A random integer tree (breadth-first numbering, children after parents)
+    whose thresholds are drawn from observed feature values, so both branches
+    of most nodes are taken; some leaves unknown (-1)."""
+    nodes = [None]
+    frontier = [(0, 0)]
+    while frontier:
+        i, d = frontier.pop(0)
+        if d == depth or (node_limit and len(nodes) + 2 > node_limit):
+            nodes[i] = {"f": -1, "t": 0, "l": -1, "r": -1, "v": int(rng.integers(-1, V))}
+            continue
+        f = int(rng.integers(0, len(oracle.FEATURES)))
+        vals = [row[f] for row in feats_pool]
+        t = int(rng.choice(vals)) if vals else 0
+        l, r = len(nodes), len(nodes) + 1
+        nodes += [None, None]
+        nodes[i] = {"f": f, "t": t, "l": l, "r": r, "v": -1}
+        frontier += [(l, d + 1), (r, d + 1)]
+    return {"nodes": nodes}
+
+
+@pytest.mark.parametrize("depth", [1, 4, 6, 7])
+def test_random_trees_schedule_matches_oracle_walk(tmp_path, depth):
+    """Random trees of depth 1-7: up to 64 leaves use the persistent kernel's
+    bit-parallel evaluation, 128 leaves its walk; every driver's schedule equals
+    the oracle's walk of the tree over the oracle's per-level features."""
+    rng = np.random.default_rng(100 + depth)
+    gs = [gg.rmat(13, 16, seed=43), gg.grid(50, 40, 0.1, seed=44), gg.erdos_renyi(8000, 5.0, seed=45)]
+    pool = []
+    refs = []
+    for g in gs:
+        for r in gg.sample_roots(g, 2, seed=depth):
+            ref = oracle.bfs(g.off, g.idx, int(r))
+            refs.append((g, int(r), ref))
+            pool += oracle.level_features(g.off, ref)
+    for k in range(3):
+        tree = _random_tree(rng, depth, pool)
+        p = tmp_path / f"r{k}.tree"
+        p.write_text(f"bfs-tree 1 {len(tree['nodes'])}\n" + "".join(
+            f"{n['f']} {n['t']} {n['l']} {n['r']} {n['v']}\n" for n in tree["nodes"]))
+        bfs.bfs_load_tree(str(p))
+        try:
+            for g, r, ref in refs:
+                want = oracle.predict_schedule(tree, oracle.level_features(g.off, ref))
+                with make(g) as G:
+                    for mode in (bfs.MODE_PERSISTENT, bfs.MODE_GRAPH):
+                        _, st = assert_parity(g, G, r, mode=mode)
+                        assert st["variant"][:len(want)].tolist() == want, (depth, k, mode)
+        finally:
+            bfs.bfs_load_tree(None)
+
+
 def test_profile_levels_features_match_oracle():
     g = gg.rmat(13, 16, seed=51)
     r = int(gg.sample_roots(g, 1, seed=8)[0])
