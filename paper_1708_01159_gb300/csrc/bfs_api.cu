@@ -303,7 +303,7 @@ int build_graph(bfs_graph* g, Workspace* ws) {
   cudaGraph_t body = wp.conditional.phGraph_out[0];
 
   cudaGraphNode_t decide;
-  TRY(add_kernel(body, &decide, nullptr, reinterpret_cast<const void*>(&k_decide), 1, 32, ka));
+  TRY(add_kernel(body, &decide, nullptr, reinterpret_cast<const void*>(&k_decide), 1, kDecideThreads, ka));
 
   cudaGraphConditionalHandle hs;
   CU(cudaGraphConditionalHandleCreate(&hs, body, 0, 0));
@@ -508,7 +508,7 @@ int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s);
 
 int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
   k_init<<<g->shapes.init, kThreads, 0, stream>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes,
-                                                  1);
+                                                  g->tree_qs, 1);
   CU(cudaGetLastError());
   CU(cudaGraphLaunch(ws->exec, stream));
   return BFS_OK;
@@ -536,11 +536,12 @@ int launch_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth,
 // The graph's kernels launched level by level from the host, reading each
 // level's decision back (synchronous). Profilers can see every kernel here.
 int launch_host_loop(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t s) {
-  k_init<<<g->shapes.init, kThreads, 0, s>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes, 0);
+  k_init<<<g->shapes.init, kThreads, 0, s>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes,
+                                             g->tree_qs, 0);
   CU(cudaGetLastError());
   RunState hs{};
   for (;;) {
-    k_decide<<<1, 32, 0, s>>>(g->dg, ws->b, ws->st);
+    k_decide<<<1, kDecideThreads, 0, s>>>(g->dg, ws->b, ws->st);
     CU(cudaMemcpyAsync(&hs, ws->st, sizeof hs, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (hs.frontier == 0 || hs.status != ST_OK) break;
@@ -1142,11 +1143,12 @@ int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advanc
   int32_t L = 0;
   std::vector<float> t(reps);
   auto body = [&]() -> int {
-    k_init<<<g->shapes.init, kThreads, 0, s>>>(g->dg, ws->b, ws->st, depth, root, -1, g->tree, g->tree_nodes, 0);
+    k_init<<<g->shapes.init, kThreads, 0, s>>>(g->dg, ws->b, ws->st, depth, root, -1, g->tree, g->tree_nodes,
+                                               g->tree_qs, 0);
     CU(cudaGetLastError());
     RunState hs{};
     for (;;) {
-      k_decide<<<1, 32, 0, s>>>(g->dg, ws->b, ws->st);
+      k_decide<<<1, kDecideThreads, 0, s>>>(g->dg, ws->b, ws->st);
       CU(cudaMemcpyAsync(&hs, ws->st, sizeof hs, cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
       if (hs.frontier == 0 || hs.status != ST_OK) break;

@@ -92,6 +92,7 @@ struct DevGraph {
 struct RunState {
   int32_t* depth;            // caller's output
   const TreeNode* tree;      // device tree
+  const QsTree* tree_qs;     // its bit-parallel form, or null
   int32_t tree_nodes;
   int32_t root;
   int32_t forced;            // -1: tree

@@ -293,18 +293,6 @@ __device__ __forceinline__ int32_t finish_variant(int32_t v, int32_t L, int32_t 
   return v;
 }
 
-// x: when not null, receives every feature (for the per-level log).
-__device__ int32_t decide_variant(const DevGraph& g, const TreeNode* tree, int32_t nodes, int32_t forced, int32_t L,
-                                  long long f, long long e, long long discovered, int32_t prev, long long* x,
-                                  int32_t* vw) {
-  if (x) {
-    for (int i = 0; i < F_NUM; ++i) x[i] = feature_value(g, i, L, f, e, discovered);
-  }
-  int32_t v = forced;
-  if (v < 0) v = (tree != nullptr && nodes > 0) ? walk_tree(g, tree, nodes, L, f, e, discovered) : -1;
-  return finish_variant(v, L, prev, f, e, vw);
-}
-
 // ---------------------------------------------------------------------------
 // Push, one thread per frontier vertex (Section 3.1.2 vertex push, over an
 // explicit queue instead of a scan of all vertices). Each thread walks its
@@ -801,11 +789,12 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
 // ===========================================================================
 __global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root,
                                                    int32_t forced, const TreeNode* tree, int32_t tree_nodes,
-                                                   int32_t use_handles) {
+                                                   const QsTree* tree_qs, int32_t use_handles) {
   init_fill(g, b.vis[0], depth, root);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->depth = depth;
     st->tree = tree;
+    st->tree_qs = tree_qs;
     st->tree_nodes = tree_nodes;
     st->root = root;
     st->forced = forced;
@@ -840,47 +829,66 @@ __global__ void k_loop_start(DevGraph g, Buffers b, RunState* st) {
 }
 
 // Level end + tree evaluation, between levels on the device (one thread).
-__global__ void k_decide(DevGraph g, Buffers b, RunState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Launched with kDecideThreads threads (one block): thread 0 closes the level
+// and keeps the state; all of them evaluate a tree that has a bit-parallel form
+// (one thread per internal node), else thread 0 walks it.
+__global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b, RunState* st) {
   (void)b;
+  __shared__ long long s_in[3];  // f, e, discovered
+  __shared__ int32_t s_go;       // 1: evaluate the tree this level
+  __shared__ unsigned long long s_and[kDecideThreads / 32];
   RunState& s = *st;
-  // close level L-1: its output queue becomes the frontier of level L
-  const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&s.next_count);
-  const unsigned long long e = *reinterpret_cast<volatile unsigned long long*>(&s.next_edges);
-  s.next_count = 0;
-  s.next_edges = 0;
-  if (s.level >= 0 && s.variant == V_PULL) s.vsel ^= 1u;  // pull wrote the other bitmap
-  s.qsel ^= 1u;
-  const int32_t L = s.level + 1;
-  s.level = L;
-  s.frontier = (int32_t)f;
-  s.frontier_edges = (long long)e;
-  s.discovered += f;
-  s.edges_reached += (long long)e;
-  // a traversal has at most n nonempty levels; more means corrupted state, so
-  // end the loop with an error instead of iterating on
-  if (L > g.n || s.discovered > g.n) s.status = ST_TIMEOUT;
-  if (L < s.log_cap) s.log_time[L] = (long long)global_ns();
-  if (f == 0 || s.status != ST_OK) {
-    s.levels = L;
-    if (s.use_handles) {
-      cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_while, 0u);
-      cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)V_NUM);
+  int32_t L = 0;
+  if (threadIdx.x == 0) {
+    // close level L-1: its output queue becomes the frontier of level L
+    const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&s.next_count);
+    const unsigned long long e = *reinterpret_cast<volatile unsigned long long*>(&s.next_edges);
+    s.next_count = 0;
+    s.next_edges = 0;
+    if (s.level >= 0 && s.variant == V_PULL) s.vsel ^= 1u;  // pull wrote the other bitmap
+    s.qsel ^= 1u;
+    L = s.level + 1;
+    s.level = L;
+    s.frontier = (int32_t)f;
+    s.frontier_edges = (long long)e;
+    s.discovered += f;
+    s.edges_reached += (long long)e;
+    // a traversal has at most n nonempty levels; more means corrupted state, so
+    // end the loop with an error instead of iterating on
+    if (L > g.n || s.discovered > g.n) s.status = ST_TIMEOUT;
+    if (L < s.log_cap) s.log_time[L] = (long long)global_ns();
+    s_go = 1;
+    if (f == 0 || s.status != ST_OK) {
+      s.levels = L;
+      if (s.use_handles) {
+        cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_while, 0u);
+        cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)V_NUM);
+      }
+      s_go = 0;
     }
-    return;
+    s_in[0] = f;
+    s_in[1] = (long long)e;
+    s_in[2] = s.discovered;
   }
-  long long x[F_NUM];
+  __syncthreads();
+  if (!s_go) return;  // uniform
+  const long long f = s_in[0], e = s_in[1], discovered = s_in[2];
+  L = st->level;
+  int32_t v = s.forced;
+  const QsTree* qs = s.tree_qs;
+  if (v < 0 && qs != nullptr) v = qs_eval(g, *qs, L, f, e, discovered, s_and);  // all threads
+  if (threadIdx.x != 0) return;
+  if (v < 0 && qs == nullptr && s.tree != nullptr && s.tree_nodes > 0)
+    v = walk_tree(g, s.tree, s.tree_nodes, L, f, e, discovered);
   int32_t vw = 32;
-  const int32_t v = decide_variant(g, s.tree, s.tree_nodes, s.forced, L, f, (long long)e, s.discovered, s.variant, x,
-                                   &vw);
-#pragma unroll
-  for (int i = 0; i < F_NUM; ++i) s.feat[i] = x[i];
+  v = finish_variant(v, L, s.variant, f, e, &vw);
+  for (int i = 0; i < F_NUM; ++i) s.feat[i] = feature_value(g, i, L, f, e, discovered);
   s.variant = v;
   s.vw = vw;
   if (L < s.log_cap) {
     s.log_variant[L] = v;
     s.log_frontier[L] = f;
-    s.log_edges[L] = (long long)e;
+    s.log_edges[L] = e;
   }
   if (s.use_handles) cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)v);
 }

@@ -6,13 +6,14 @@
 namespace bfs {
 
 constexpr int kThreads = 256;     // block size of the level kernels
+constexpr int kDecideThreads = 64;  // block size of k_decide: one thread per node of a bit-parallel tree (kQsMax)
 constexpr int kCtaChunk = 2048;   // int32 per shared-memory stage of the CTA variant (8 KB)
 constexpr int kCtaDirect = 512;   // adjacency shorter than this is read directly, not staged
 constexpr int kPeItems = 8;       // items per thread in the edge-centric scan / expand
 constexpr int kPeTile = kThreads * kPeItems;  // frontier entries per scan block, items per expand tile
 
 __global__ void k_init(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root, int32_t forced,
-                       const TreeNode* tree, int32_t tree_nodes, int32_t use_handles);
+                       const TreeNode* tree, int32_t tree_nodes, const QsTree* tree_qs, int32_t use_handles);
 __global__ void k_decide(DevGraph g, Buffers b, RunState* st);
 __global__ void k_loop_start(DevGraph g, Buffers b, RunState* st);
 __global__ void k_push_thread(DevGraph g, Buffers b, RunState* st);
