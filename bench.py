@@ -363,7 +363,7 @@ def bench_grid(bfs, torch, stream):
                          "us_per_level": 1e6 * sum(ts) / sum(levels)}
         k = 4
         fixed = {}
-        for v, vname in enumerate(bfs.VARIANTS):
+        for v, vname in enumerate(bfs.FORCED_VARIANTS):
             fixed[vname] = harmonic_gteps(timed(roots[:k], mode=bfs.MODE_PERSISTENT, forced_variant=v), edges[:k])
         switched = harmonic_gteps(timed(roots[:k], mode=bfs.MODE_PERSISTENT), edges[:k])
         best = max(fixed, key=fixed.get)
@@ -547,7 +547,7 @@ def run_ours(args):
     # every fixed variant on the same roots (the "best fixed kernel" comparison)
     if not args.no_fixed:
         fixed = {}
-        for v, name in enumerate(bfs.VARIANTS):
+        for v, name in enumerate(bfs.FORCED_VARIANTS):
             step(v)
             torch.cuda.synchronize()
             evs = step(v)

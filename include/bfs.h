@@ -52,15 +52,25 @@ enum bfs_status {
   BFS_ERR_NOT_FOUND = 8,   /* unknown ticket, graph id or file */
 };
 
-/* Variants a level can run (the classes the decision tree predicts). */
+/* Variants a level can run. The first BFS_NUM_VARIANTS are the classes the
+ * decision tree predicts; the two edge-list kernels of Section 3.1.1 that scan
+ * every edge of the graph each level can only be forced (bfs_options). */
 enum bfs_variant {
   BFS_VARIANT_TREE = -1,        /* let the decision tree choose per level (default) */
   BFS_VARIANT_PUSH_THREAD = 0,  /* top-down, one thread per frontier vertex (Section 3.1.2, vertex push) */
   BFS_VARIANT_PUSH_WARP = 1,    /* top-down, virtual warp per frontier vertex (Section 3.1.3) */
   BFS_VARIANT_PUSH_CTA = 2,     /* top-down, one CTA per frontier vertex, adjacency staged in shared memory */
-  BFS_VARIANT_PUSH_EDGE = 3,    /* top-down, one thread per frontier edge (Section 3.1.1, edge list) */
+  BFS_VARIANT_PUSH_EDGE = 3,    /* top-down, one thread per frontier edge (Section 3.1.1, edge list
+                                   restricted to the frontier's edges) */
   BFS_VARIANT_PULL = 4,         /* bottom-up over the visited bitmap, early exit (Section 3.1.2, vertex pull) */
   BFS_NUM_VARIANTS = 5,
+  BFS_VARIANT_EDGE_LIST = 5,    /* every edge u->v of the graph, each level: v is reached when u is in the
+                                   frontier (Section 3.1.1, edge list); builds a per-edge origin array
+                                   (m int32) on first use */
+  BFS_VARIANT_REVERSE_EDGE_LIST = 6, /* every edge by destination (the transpose), each level: an unreached v
+                                   is reached when its source is in the frontier (Section 3.1.1, reverse
+                                   edge list); origin array of the transpose on first use */
+  BFS_NUM_FORCED_VARIANTS = 7,
 };
 
 /* Flags of bfs_graph_create. */
@@ -97,7 +107,8 @@ enum bfs_mode {
 };
 
 typedef struct bfs_options {
-  int32_t forced_variant;    /* BFS_VARIANT_TREE or a fixed bfs_variant for every level */
+  int32_t forced_variant;    /* BFS_VARIANT_TREE or a fixed bfs_variant (< BFS_NUM_FORCED_VARIANTS) for
+                                every level */
   int32_t depth_on_host;     /* 1: depth_out is host memory; the library copies the result there */
   int32_t mode;              /* enum bfs_mode */
   int32_t grid_blocks;       /* persistent driver: blocks of the cooperative grid, 0 for one full

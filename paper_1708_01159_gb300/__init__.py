@@ -46,8 +46,13 @@ MODE_HOST_LOOP = 3
 MODES = {"default": MODE_DEFAULT, "persistent": MODE_PERSISTENT, "graph": MODE_GRAPH, "host_loop": MODE_HOST_LOOP}
 
 VARIANT_TREE = -1
-VARIANTS = ("push_thread", "push_warp", "push_cta", "push_edge", "pull")
+VARIANTS = ("push_thread", "push_warp", "push_cta", "push_edge", "pull")  # the tree's classes
 NUM_VARIANTS = len(VARIANTS)
+VARIANT_EDGE_LIST = 5
+VARIANT_REVERSE_EDGE_LIST = 6
+# every variant a run can be forced to: the tree's classes plus the whole-edge-list kernels
+FORCED_VARIANTS = VARIANTS + ("edge_list", "reverse_edge_list")
+NUM_FORCED_VARIANTS = len(FORCED_VARIANTS)
 FEATURES = ("n", "m", "deg_min", "deg_q1", "deg_med", "deg_q3", "deg_max", "deg_sd256",
             "frontier", "frontier_ppm", "discovered", "discovered_ppm", "frontier_edges", "level")
 NUM_FEATURES = len(FEATURES)

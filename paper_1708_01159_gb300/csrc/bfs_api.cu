@@ -179,7 +179,7 @@ struct Workspace {
 constexpr int kMaxWorkspaces = 64;
 
 struct Shapes {
-  int init, push_thread, push_warp, push_cta, pe, pull;
+  int init, push_thread, push_warp, push_cta, pe, pull, edge_list;
   int persist;  // cooperative grid of the persistent kernel (0: not supported)
 };
 
@@ -201,6 +201,9 @@ struct bfs_graph {
   std::vector<TreeNode*> trees;
   TreeNode* tree = nullptr;
   QsTree* tree_qs = nullptr;  // bit-parallel form of the same tree (inside the same allocation), or null
+  // edge-list variants: the device GraphAux block and whether it has been filled
+  GraphAux* aux = nullptr;
+  bool has_origin = false;
   int32_t tree_nodes = 0;
   uint64_t tree_version = 0;
   // multi-source buffers (allocated on the first batch; batches on one graph
@@ -311,7 +314,7 @@ int build_graph(bfs_graph* g, Workspace* ws) {
   sp.type = cudaGraphNodeTypeConditional;
   sp.conditional.handle = hs;
   sp.conditional.type = cudaGraphCondTypeSwitch;
-  sp.conditional.size = V_NUM;
+  sp.conditional.size = V_FORCED_NUM;
   cudaGraphNode_t snode;
   CU(cudaGraphAddNode(&snode, body, &decide, nullptr, 1, &sp));
   cudaGraph_t* vb = sp.conditional.phGraph_out;
@@ -328,6 +331,10 @@ int build_graph(bfs_graph* g, Workspace* ws) {
   TRY(add_kernel(vb[V_PUSH_EDGE], &n2, &n1, reinterpret_cast<const void*>(&k_pe_scan), s.pe, kThreads, ka));
   TRY(add_kernel(vb[V_PUSH_EDGE], &n3, &n2, reinterpret_cast<const void*>(&k_pe_expand), s.pe, kThreads, ka));
   TRY(add_kernel(vb[V_PULL], &n0, nullptr, reinterpret_cast<const void*>(&k_pull), s.pull, kThreads, ka));
+  TRY(add_kernel(vb[V_EDGE_LIST], &n0, nullptr, reinterpret_cast<const void*>(&k_edge_list), s.edge_list, kThreads,
+                 ka));
+  TRY(add_kernel(vb[V_REV_EDGE_LIST], &n0, nullptr, reinterpret_cast<const void*>(&k_rev_edge_list), s.edge_list,
+                 kThreads, ka));
   CU(cudaGraphInstantiate(&ws->exec, ws->graph, 0));
 
   // the handles live in the device state, where decide sets them each level
@@ -504,6 +511,40 @@ int sync_tree(bfs_graph* g) {
   return BFS_OK;
 }
 
+// The edge-list variants' origin arrays, built on their first use (m int32
+// each; one array for a symmetric graph) and published through the graph's
+// GraphAux block, which the kernels read at run time.
+int ensure_origin(bfs_graph* g) {
+  std::lock_guard<std::mutex> lk(g->mu);
+  if (g->has_origin) return BFS_OK;
+  const int64_t m = g->dg.m;
+  int32_t* out = nullptr;
+  int32_t* in = nullptr;
+  TRY(dmalloc(reinterpret_cast<void**>(&out), (size_t)std::max<int64_t>(m, 1) * 4));
+  g->allocs.push_back(out);
+  g->bytes += (size_t)std::max<int64_t>(m, 1) * 4;
+  if (g->symmetric) {
+    in = out;
+  } else {
+    TRY(dmalloc(reinterpret_cast<void**>(&in), (size_t)std::max<int64_t>(m, 1) * 4));
+    g->allocs.push_back(in);
+    g->bytes += (size_t)std::max<int64_t>(m, 1) * 4;
+  }
+  cudaStream_t s;
+  CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  const int blocks = g->sms * 4;
+  k_build_origin<<<blocks, kThreads, 0, s>>>(g->dg.off, g->dg.n, out);
+  if (!g->symmetric) k_build_origin<<<blocks, kThreads, 0, s>>>(g->dg.in_off, g->dg.n, in);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "origin arrays: %s", cudaGetErrorString(e));
+  const GraphAux aux{out, in};
+  TRY(upload_now(g->aux, &aux, sizeof aux));
+  g->has_origin = true;
+  return BFS_OK;
+}
+
 int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s);
 
 int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
@@ -579,6 +620,8 @@ int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s) {
       k_pe_expand<<<sh.pe, kThreads, 0, s>>>(dg, ws->b, ws->st);
       break;
     case V_PULL: k_pull<<<sh.pull, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
+    case V_EDGE_LIST: k_edge_list<<<sh.edge_list, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
+    case V_REV_EDGE_LIST: k_rev_edge_list<<<sh.edge_list, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
     default: return fail(BFS_ERR_INVALID_ARG, "variant %d", v);
   }
   CU(cudaGetLastError());
@@ -858,6 +901,11 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
   uint32_t* vis_init = nullptr;
   const int64_t words = (n + 31) / 32;
   r = galloc(reinterpret_cast<void**>(&vis_init), words * 4);
+  if (r == BFS_OK) r = galloc(reinterpret_cast<void**>(&g->aux), sizeof(GraphAux));
+  if (r == BFS_OK) {
+    const GraphAux none{nullptr, nullptr};
+    r = upload_now(g->aux, &none, sizeof none);
+  }
   if (r != BFS_OK) {
     cleanup();
     return r;
@@ -874,6 +922,7 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
   dg.in_off = in_off;
   dg.in_idx = in_idx;
   dg.vis_init = vis_init;
+  dg.aux = g->aux;
   dg.n = (int32_t)n;
   dg.m = (int32_t)m;
   dg.words = (int32_t)((n + 31) / 32);
@@ -888,6 +937,7 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
   s.push_cta = grid_for(reinterpret_cast<const void*>(&k_push_cta), g->sms, 8);
   s.pe = grid_for(reinterpret_cast<const void*>(&k_pe_expand), g->sms, 8);
   s.pull = grid_for(reinterpret_cast<const void*>(&k_pull), g->sms, 8);
+  s.edge_list = grid_for(reinterpret_cast<const void*>(&k_edge_list), g->sms, 8);
   // the persistent kernel needs every block resident: one full occupancy wave
   int coop = 0, per_sm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
@@ -957,7 +1007,7 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   int32_t forced = -1, mode = BFS_MODE_DEFAULT, grid_blocks = 0;
   bool host_out = false;
   if (opts) {
-    if (opts->forced_variant < -1 || opts->forced_variant >= V_NUM)
+    if (opts->forced_variant < -1 || opts->forced_variant >= V_FORCED_NUM)
       return fail(BFS_ERR_INVALID_ARG, "forced_variant %d out of range", opts->forced_variant);
     if (opts->mode < BFS_MODE_DEFAULT || opts->mode > BFS_MODE_HOST_LOOP)
       return fail(BFS_ERR_INVALID_ARG, "mode %d out of range", opts->mode);
@@ -973,6 +1023,7 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   }
   DeviceGuard dgd(g->device);
   TRY(sync_tree(g));
+  if (forced == V_EDGE_LIST || forced == V_REV_EDGE_LIST) TRY(ensure_origin(g));
   Workspace* ws = nullptr;
   TRY(acquire(g, stream, &ws));
   int32_t* dst = host_out ? ws->host_depth_stage : depth_out;

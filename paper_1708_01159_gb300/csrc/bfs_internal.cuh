@@ -26,7 +26,12 @@ enum Variant : int32_t {
   V_PUSH_CTA = 2,
   V_PUSH_EDGE = 3,
   V_PULL = 4,
-  V_NUM = 5,
+  V_NUM = 5,  // the variants the tree predicts
+  // Section 3.1.1's two kernels over the whole edge list, selectable as a
+  // forced variant (not predicted by the tree)
+  V_EDGE_LIST = 5,
+  V_REV_EDGE_LIST = 6,
+  V_FORCED_NUM = 7,
 };
 
 // Section 4.1 features, in the order the tree file indexes them.
@@ -74,6 +79,14 @@ struct QsTree {
   int32_t leaf[kQsMax];  // class of each leaf, left to right (-1: unknown)
 };
 
+// Origin of every CSR entry (the vertex whose row holds it) and of every
+// transpose entry, for the edge-list variants; null until first needed
+// (origin_in is origin_out for a symmetric graph).
+struct GraphAux {
+  const int32_t* origin_out;
+  const int32_t* origin_in;
+};
+
 struct DevGraph {
   const int32_t* off;
   const int32_t* idx;
@@ -82,6 +95,10 @@ struct DevGraph {
   // visited bitmap a traversal starts from (before the root's bit): bit v set
   // iff v has no edges at all, so no level reaches it and pull never scans it
   const uint32_t* vis_init;
+  // device block holding the edge-list variants' origin arrays (filled on
+  // their first use; kernels read it at run time, so CUDA graphs built before
+  // then see the arrays too)
+  const struct GraphAux* aux;
   int32_t n;
   int32_t m;
   int32_t words;  // ceil(n / 32)

@@ -286,9 +286,11 @@ __device__ __forceinline__ int32_t qs_eval(const DevGraph& g, const QsTree& q, i
 // frontier's mean degree floor(e / f), clamped to [4, 32] (floor(e / f) <= k is
 // e < (k + 1) f).
 __device__ __forceinline__ int32_t finish_variant(int32_t v, int32_t L, int32_t prev, long long f, long long e,
-                                                  int32_t* vw) {
-  if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : prev;  // unknown prediction
-  if (v < 0 || v >= V_NUM) v = kLevel0Default;
+                                                  int32_t* vw, bool forced) {
+  if (!forced) {
+    if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : prev;  // unknown prediction
+    if (v < 0 || v >= V_NUM) v = kLevel0Default;
+  }
   *vw = (f <= 0 || e < 5 * f) ? 4 : e < 9 * f ? 8 : e < 17 * f ? 16 : 32;
   return v;
 }
@@ -782,6 +784,43 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
   if (wcnt) warp_stage_flush(wbuf, wcnt, lv);
 }
 
+// ---------------------------------------------------------------------------
+// Edge list and reverse edge list (Section 3.1.1): one thread per edge of the
+// whole graph, every level, four edges per thread per step (coalesced). Edge
+// list: CSR entry e is the edge origin_out[e] -> idx[e], whose target is
+// reached when its source is in the frontier (depth L). Reverse edge list:
+// transpose entry e is in_idx[e] -> origin_in[e]; the destination's bitmap
+// bit is read first, so settled destinations cost no depth read. Targets are
+// claimed through the visited bitmap like the push variants', so frontier
+// counts and queues stay exact.
+// ---------------------------------------------------------------------------
+template <bool kReverse>
+__device__ void body_edge_list(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
+  const int32_t L = lv.next_depth - 1;
+  const long long m = g.m;
+  const int32_t* origin = kReverse ? g.aux->origin_in : g.aux->origin_out;
+  const int32_t* other = kReverse ? g.in_idx : g.idx;
+  const long long step = (long long)blockDim.x * 4;
+  for (long long base = (long long)blockIdx.x * step; base < m; base += (long long)gridDim.x * step) {
+    int32_t v[4] = {0, 0, 0, 0};
+    int nv = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long e = base + k * (long long)blockDim.x + threadIdx.x;
+      if (e < m) {
+        if (kReverse) {
+          const int32_t dst = origin[e];
+          if (!vis_bit<false>(lv.vis, dst) && lv.depth[other[e]] == L) v[nv++] = dst;
+        } else {
+          if (lv.depth[origin[e]] == L) v[nv++] = other[e];
+        }
+      }
+    }
+    visit_k<4>(g, lv, stage, v, nv, edges);
+    stage_flush(stage, lv, kStageCap / 2);
+  }
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -862,7 +901,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b
       s.levels = L;
       if (s.use_handles) {
         cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_while, 0u);
-        cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)V_NUM);
+        cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)V_FORCED_NUM);
       }
       s_go = 0;
     }
@@ -881,7 +920,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b
   if (v < 0 && qs == nullptr && s.tree != nullptr && s.tree_nodes > 0)
     v = walk_tree(g, s.tree, s.tree_nodes, L, f, e, discovered);
   int32_t vw = 32;
-  v = finish_variant(v, L, s.variant, f, e, &vw);
+  v = finish_variant(v, L, s.variant, f, e, &vw, s.forced >= 0);
   for (int i = 0; i < F_NUM; ++i) s.feat[i] = feature_value(g, i, L, f, e, discovered);
   s.variant = v;
   s.vw = vw;
@@ -960,6 +999,31 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
     body_pe_expand<false>(g, lv, b, stage, s_a, s_beg, s_split, edges);
   }
   block_add_u64(edges, &st->next_edges);
+}
+
+__global__ void __launch_bounds__(kThreads) k_edge_list(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  body_edge_list<false>(g, lv, stage, edges);
+  stage_flush(stage, lv, 1);
+  block_add_u64(edges, &st->next_edges);
+}
+
+__global__ void __launch_bounds__(kThreads) k_rev_edge_list(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  body_edge_list<true>(g, lv, stage, edges);
+  stage_flush(stage, lv, 1);
+  block_add_u64(edges, &st->next_edges);
+}
+
+// Origin of every CSR entry: the vertex whose row [off[v], off[v + 1]) holds it.
+__global__ void k_build_origin(const int32_t* off, int32_t n, int32_t* origin) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    for (int32_t e = off[v]; e < off[v + 1]; ++e) origin[e] = (int32_t)v;
 }
 
 __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunState* st) {
@@ -1070,7 +1134,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
       v = qs_eval(g, s_qs, L, f, (long long)e, discovered, s_and);
     else if (v < 0 && tree != nullptr && tree_nodes > 0)
       v = walk_tree(g, tree, tree_nodes, L, f, (long long)e, discovered);
-    v = finish_variant(v, L, prev, f, (long long)e, &vw);
+    v = finish_variant(v, L, prev, f, (long long)e, &vw, forced >= 0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->cnt3[(L + 2) % 3] = 0;  // last read by level L - 1, which every block has finished
       st->edg3[(L + 2) % 3] = 0;
@@ -1109,6 +1173,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
         if (!grid_sync(st)) break;
         body_pe_expand<false>(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
         break;
+      case V_EDGE_LIST: body_edge_list<false>(g, lv, stage, edges); break;
+      case V_REV_EDGE_LIST: body_edge_list<true>(g, lv, stage, edges); break;
       default: body_pull<false, kPullWordsPersistent>(g, lv, stage, edges); break;
     }
     stage_flush(stage, lv, 1);

@@ -75,6 +75,26 @@ def test_each_variant(which, variant):
 
 
 @pytest.mark.parametrize("mode", [bfs.MODE_PERSISTENT, bfs.MODE_GRAPH, bfs.MODE_HOST_LOOP])
+@pytest.mark.parametrize("variant", [bfs.VARIANT_EDGE_LIST, bfs.VARIANT_REVERSE_EDGE_LIST])
+def test_edge_list_variants(mode, variant):
+    """Section 3.1.1's whole-edge-list kernels (forced only): bit-exact on
+    skewed, high-diameter, directed (separate transpose origins) graphs and
+    closed forms, in every driver; the tree cannot predict them."""
+    rng = np.random.default_rng(5)
+    n = 2000
+    directed = gg.from_edges(n, rng.integers(0, n, 9000), rng.integers(0, n, 9000), symmetrize=False)
+    for g, flags in ((gg.rmat(12, 16, seed=61), bfs.BFS_SYMMETRIC), (gg.grid(40, 30, 0.1, seed=62), bfs.BFS_SYMMETRIC),
+                     (directed, 0), (cf.star(50)[0], bfs.BFS_SYMMETRIC)):
+        with make(g, flags) as G:
+            for r in gg.sample_roots(g, 2, seed=12):
+                assert_parity(g, G, r, variant, mode)
+    with pytest.raises(bfs.BFSError) as e:
+        with make(gg.rmat(8, 8, seed=1)) as G:
+            run(G, 0, bfs.NUM_FORCED_VARIANTS)
+    assert e.value.code == bfs.BFS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("mode", [bfs.MODE_PERSISTENT, bfs.MODE_GRAPH, bfs.MODE_HOST_LOOP])
 @pytest.mark.parametrize("variant", [bfs.VARIANT_TREE] + list(range(V)))
 def test_execution_modes_agree(mode, variant):
     """The persistent kernel, the CUDA graph and the host loop run the same level
