@@ -230,6 +230,40 @@ def progress(msg):
     print(f"[bench] {msg}", file=sys.stderr, flush=True)
 
 
+def bench_count_modes(bfs, torch, G, g, roots, edges, stream):
+    """Vertex push (push_thread forced) with each frontier-count mode, host-loop
+    driver (a host round trip per level, the same for every mode), on the
+    benchmark graph and on R-MAT scale 14 (16 roots)."""
+    import graphgen as gg
+    out = {"note": "push_thread forced, host-loop driver; harmonic-mean GTEPS"}
+
+    def measure(Gh, n, rs, es):
+        d = torch.empty(n, dtype=torch.int32, device="cuda")
+        res = {}
+        for name, cm in bfs.COUNT_MODES.items():
+            bfs.bfs_run_ex(Gh.handle, int(rs[0]), d, stream, forced_variant=0, mode=bfs.MODE_HOST_LOOP, count_mode=cm)
+            torch.cuda.synchronize()
+            ts = []
+            for r in rs:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                bfs.bfs_run_ex(Gh.handle, int(r), d, stream, forced_variant=0, mode=bfs.MODE_HOST_LOOP, count_mode=cm)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            res[name] = harmonic_gteps(ts, es)
+        return res
+
+    out["rmat22"] = measure(G, g.n, roots, edges)
+    g14 = gg.rmat_s14_ef16()
+    r14 = gg.sample_roots(g14, 16, seed=gg.SEED_ROOTS)
+    with bfs.Graph(g14.off, g14.idx) as G14:
+        d = torch.empty(g14.n, dtype=torch.int32, device="cuda")
+        e14 = [bfs.bfs_run_ex(G14.handle, int(r), d, stream, stats=True)["edges_reached"] for r in r14]
+        out["rmat14"] = measure(G14, g14.n, r14, e14)
+    return out
+
+
 def bench_batch(bfs, torch, stream):
     """Multi-source BFS: ER 2^22, average degree 8, 64 roots in one launch (tuned), against
     the same 64 roots as single-source switched traversals."""
@@ -650,6 +684,12 @@ def run_ours(args):
             "best_fixed_over_optimal": float(fixed_ms.min()) / opt_ms,
             "note": "sums of per-level kernel times from the timing harness (each variant from the same snapshot); "
                     "init and driver overheads excluded"}
+
+    # Section 3.1.4's frontier-count alternatives in the vertex push (host-loop
+    # driver, push_thread forced): block-staged appends (the kernels' own),
+    # one atomic per warp, one atomic per vertex
+    if not args.no_fixed:
+        line["count_modes"] = bench_count_modes(bfs, torch, G, g, roots[:8], edges[:8], stream)
 
     G.close()
     del depth

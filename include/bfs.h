@@ -116,7 +116,12 @@ typedef struct bfs_options {
                                 several traversals be resident at once and shorten the grid barrier
                                 (latency-bound, high-diameter graphs). Must be 0 for BFS_MODE_GRAPH
                                 and BFS_MODE_HOST_LOOP, and >= 0. */
-  int32_t reserved[4];       /* must be zero */
+  int32_t count_mode;        /* how the vertex-push variant appends reached vertices to the next queue,
+                                the Section 3.1.4 comparison: 0 block-local stage and one global atomic
+                                per flush (the default, and the only mode of the other variants), 1 one
+                                global atomic per warp, 2 one global atomic per vertex. Nonzero only
+                                with BFS_MODE_HOST_LOOP. */
+  int32_t reserved[3];       /* must be zero */
 } bfs_options;
 
 typedef struct bfs_run_stats {

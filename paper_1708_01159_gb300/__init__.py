@@ -53,6 +53,8 @@ VARIANT_REVERSE_EDGE_LIST = 6
 # every variant a run can be forced to: the tree's classes plus the whole-edge-list kernels
 FORCED_VARIANTS = VARIANTS + ("edge_list", "reverse_edge_list")
 NUM_FORCED_VARIANTS = len(FORCED_VARIANTS)
+# bfs_options.count_mode: how vertex push appends reached vertices (Section 3.1.4 comparison)
+COUNT_MODES = {"block": 0, "warp": 1, "atomic": 2}
 FEATURES = ("n", "m", "deg_min", "deg_q1", "deg_med", "deg_q3", "deg_max", "deg_sd256",
             "frontier", "frontier_ppm", "discovered", "discovered_ppm", "frontier_edges", "level")
 NUM_FEATURES = len(FEATURES)
@@ -72,7 +74,7 @@ class _GraphInfo(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("forced_variant", ctypes.c_int32), ("depth_on_host", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("grid_blocks", ctypes.c_int32), ("count_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Stats(ctypes.Structure):
@@ -247,13 +249,14 @@ def bfs_run(g: int, root: int, depth_out, stream=None) -> None:
 
 def bfs_run_ex(g: int, root: int, depth_out, stream=None, forced_variant: int = VARIANT_TREE,
                depth_on_host: Optional[bool] = None, stats: bool = False, log_capacity: int = 0,
-               mode: int = MODE_DEFAULT, grid_blocks: int = 0):
+               mode: int = MODE_DEFAULT, grid_blocks: int = 0, count_mode: int = 0):
     """BFS with options. Returns a stats dict when stats=True (then the stream is synchronised).
-    grid_blocks: persistent driver only, blocks of the cooperative grid (0: a full occupancy wave)."""
+    grid_blocks: persistent driver only, blocks of the cooperative grid (0: a full occupancy wave).
+    count_mode: host-loop driver only, how vertex push appends to the next queue (COUNT_MODES)."""
     p, dev, _ = _ptr(depth_out, what="depth_out")
     host = (not dev) if depth_on_host is None else bool(depth_on_host)
     opts = _Options(forced_variant=int(forced_variant), depth_on_host=int(host), mode=int(mode),
-                    grid_blocks=int(grid_blocks))
+                    grid_blocks=int(grid_blocks), count_mode=int(count_mode))
     st = None
     logs = None
     if stats:

@@ -545,7 +545,7 @@ int ensure_origin(bfs_graph* g) {
   return BFS_OK;
 }
 
-int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s);
+int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s, int32_t count_mode = CM_BLOCK);
 
 int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
   k_init<<<g->shapes.init, kThreads, 0, stream>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes,
@@ -576,7 +576,8 @@ int launch_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth,
 
 // The graph's kernels launched level by level from the host, reading each
 // level's decision back (synchronous). Profilers can see every kernel here.
-int launch_host_loop(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t s) {
+int launch_host_loop(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t s,
+                     int32_t count_mode) {
   k_init<<<g->shapes.init, kThreads, 0, s>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes,
                                              g->tree_qs, 0);
   CU(cudaGetLastError());
@@ -586,31 +587,38 @@ int launch_host_loop(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, 
     CU(cudaMemcpyAsync(&hs, ws->st, sizeof hs, cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     if (hs.frontier == 0 || hs.status != ST_OK) break;
-    TRY(launch_variant(g, ws, hs.variant, s));
+    TRY(launch_variant(g, ws, hs.variant, s, count_mode));
   }
   return BFS_OK;
 }
 
 int launch_run(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, int32_t mode,
-               cudaStream_t stream, int32_t grid_blocks = 0) {
+               cudaStream_t stream, int32_t grid_blocks = 0, int32_t count_mode = CM_BLOCK) {
   if (mode == BFS_MODE_DEFAULT) mode = g->shapes.persist > 0 ? BFS_MODE_PERSISTENT : BFS_MODE_GRAPH;
   switch (mode) {
     case BFS_MODE_PERSISTENT:
       if (g->shapes.persist <= 0) return fail(BFS_ERR_INVALID_ARG, "device lacks cooperative launch");
       return launch_persistent(g, ws, root, depth, forced, stream, grid_blocks);
     case BFS_MODE_GRAPH: return launch_graph(g, ws, root, depth, forced, stream);
-    case BFS_MODE_HOST_LOOP: return launch_host_loop(g, ws, root, depth, forced, stream);
+    case BFS_MODE_HOST_LOOP: return launch_host_loop(g, ws, root, depth, forced, stream, count_mode);
     default: return fail(BFS_ERR_INVALID_ARG, "mode %d", mode);
   }
 }
 
 // Launch the kernels of one variant for the current level directly on a
 // stream (the host-driven counterpart of one SWITCH body).
-int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s) {
+int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s, int32_t count_mode) {
   const Shapes& sh = g->shapes;
   const DevGraph& dg = g->dg;
   switch (v) {
-    case V_PUSH_THREAD: k_push_thread<<<sh.push_thread, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
+    case V_PUSH_THREAD:
+      if (count_mode == CM_WARP)
+        k_push_thread_warp_count<<<sh.push_thread, kThreads, 0, s>>>(dg, ws->b, ws->st);
+      else if (count_mode == CM_ATOMIC)
+        k_push_thread_atomic_count<<<sh.push_thread, kThreads, 0, s>>>(dg, ws->b, ws->st);
+      else
+        k_push_thread<<<sh.push_thread, kThreads, 0, s>>>(dg, ws->b, ws->st);
+      break;
     case V_PUSH_WARP: k_push_warp<<<sh.push_warp, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
     case V_PUSH_CTA: k_push_cta<<<sh.push_cta, kThreads, 0, s>>>(dg, ws->b, ws->st); break;
     case V_PUSH_EDGE:
@@ -1004,15 +1012,20 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (!depth_out) return fail(BFS_ERR_INVALID_ARG, "depth_out is null");
   if (root < 0 || root >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root %d not in [0, %d)", root, g->dg.n);
-  int32_t forced = -1, mode = BFS_MODE_DEFAULT, grid_blocks = 0;
+  int32_t forced = -1, mode = BFS_MODE_DEFAULT, grid_blocks = 0, count_mode = CM_BLOCK;
   bool host_out = false;
   if (opts) {
     if (opts->forced_variant < -1 || opts->forced_variant >= V_FORCED_NUM)
       return fail(BFS_ERR_INVALID_ARG, "forced_variant %d out of range", opts->forced_variant);
     if (opts->mode < BFS_MODE_DEFAULT || opts->mode > BFS_MODE_HOST_LOOP)
       return fail(BFS_ERR_INVALID_ARG, "mode %d out of range", opts->mode);
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < 3; ++k)
       if (opts->reserved[k]) return fail(BFS_ERR_INVALID_ARG, "reserved option fields must be zero");
+    if (opts->count_mode < 0 || opts->count_mode >= CM_NUM)
+      return fail(BFS_ERR_INVALID_ARG, "count_mode %d out of range", opts->count_mode);
+    if (opts->count_mode != CM_BLOCK && opts->mode != BFS_MODE_HOST_LOOP)
+      return fail(BFS_ERR_INVALID_ARG, "count_mode applies to the host-loop driver only");
+    count_mode = opts->count_mode;
     if (opts->grid_blocks < 0) return fail(BFS_ERR_INVALID_ARG, "grid_blocks < 0");
     if (opts->grid_blocks > 0 && (opts->mode == BFS_MODE_GRAPH || opts->mode == BFS_MODE_HOST_LOOP))
       return fail(BFS_ERR_INVALID_ARG, "grid_blocks applies to the persistent driver only");
@@ -1027,7 +1040,7 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   Workspace* ws = nullptr;
   TRY(acquire(g, stream, &ws));
   int32_t* dst = host_out ? ws->host_depth_stage : depth_out;
-  int r = launch_run(g, ws, root, dst, forced, mode, stream, grid_blocks);
+  int r = launch_run(g, ws, root, dst, forced, mode, stream, grid_blocks, count_mode);
   RunState hs{};
   if (r == BFS_OK && host_out) {
     cudaError_t e = cudaMemcpyAsync(depth_out, dst, (size_t)g->dg.n * 4, cudaMemcpyDeviceToHost, stream);

@@ -34,6 +34,17 @@ enum Variant : int32_t {
   V_FORCED_NUM = 7,
 };
 
+// How a push level appends the vertices it reaches to the next queue (whose
+// tail is the next frontier size). Section 3.1.4 compares a global atomic per
+// vertex with warp and block reductions in front of it; the level kernels use
+// CM_BLOCK, and the others exist for that comparison (vertex push, host loop).
+enum CountMode : int32_t {
+  CM_BLOCK = 0,   // block-local shared-memory stage, one global atomic per flush
+  CM_WARP = 1,    // one global atomic per group of converged lanes
+  CM_ATOMIC = 2,  // one global atomic per vertex
+  CM_NUM = 3,
+};
+
 // Section 4.1 features, in the order the tree file indexes them.
 enum Feature : int32_t {
   F_N = 0, F_M, F_DEG_MIN, F_DEG_Q1, F_DEG_MED, F_DEG_Q3, F_DEG_MAX, F_DEG_SD256,

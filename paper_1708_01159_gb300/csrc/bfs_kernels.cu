@@ -123,7 +123,7 @@ __device__ __forceinline__ void stage_flush(const Stage& s, const Level& lv, uns
 // winners' degrees read, so the K edges' memory round trips overlap instead of
 // forming one dependent chain per edge. The one thread whose atomicOr flips a
 // vertex's bit writes its depth, counts its out-degree and stages it.
-template <int K>
+template <int K, int kCount = CM_BLOCK>
 __device__ __forceinline__ void visit_k(const DevGraph& g, const Level& lv, const Stage& s, const int32_t (&v)[K],
                                         int nv, unsigned long long& edges) {
   uint32_t word[K];
@@ -144,7 +144,12 @@ __device__ __forceinline__ void visit_k(const DevGraph& g, const Level& lv, cons
     if (won[k]) {
       lv.depth[v[k]] = lv.next_depth;
       edges += (unsigned long long)d[k];
-      stage_push(s, lv, v[k]);
+      if (kCount == CM_BLOCK)
+        stage_push(s, lv, v[k]);
+      else if (kCount == CM_WARP)
+        queue_append(lv.qout, lv.tail, v[k]);
+      else
+        lv.qout[atomicAdd(lv.tail, 1u)] = v[k];
     }
 }
 
@@ -300,6 +305,7 @@ __device__ __forceinline__ int32_t finish_variant(int32_t v, int32_t L, int32_t 
 // explicit queue instead of a scan of all vertices). Each thread walks its
 // vertex's adjacency four edges at a time.
 // ---------------------------------------------------------------------------
+template <int kCount = CM_BLOCK>
 __device__ void body_push_thread(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
   const int stride = gridDim.x * blockDim.x;
   for (int base = blockIdx.x * blockDim.x; base < lv.frontier; base += stride) {
@@ -312,7 +318,7 @@ __device__ void body_push_thread(const DevGraph& g, const Level& lv, const Stage
         int32_t v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = k < nv ? g.idx[e + k] : 0;
-        visit_k<4>(g, lv, stage, v, nv, edges);
+        visit_k<4, kCount>(g, lv, stage, v, nv, edges);
       }
     }
     stage_flush(stage, lv, kStageCap / 2);
@@ -930,6 +936,23 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b
     s.log_edges[L] = e;
   }
   if (s.use_handles) cudaGraphSetConditional((cudaGraphConditionalHandle)s.h_switch, (unsigned)v);
+}
+
+// Vertex push with the other frontier-count modes (Section 3.1.4 comparison).
+__global__ void __launch_bounds__(kThreads) k_push_thread_warp_count(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  body_push_thread<CM_WARP>(g, lv, stage, edges);
+  block_add_u64(edges, &st->next_edges);
+}
+
+__global__ void __launch_bounds__(kThreads) k_push_thread_atomic_count(DevGraph g, Buffers b, RunState* st) {
+  BFS_DECLARE_STAGE(stage);
+  const Level lv = load_level(b, st);
+  unsigned long long edges = 0;
+  body_push_thread<CM_ATOMIC>(g, lv, stage, edges);
+  block_add_u64(edges, &st->next_edges);
 }
 
 __global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b, RunState* st) {

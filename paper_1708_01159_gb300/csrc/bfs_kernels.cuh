@@ -24,6 +24,9 @@ __global__ void k_pe_top(DevGraph g, Buffers b, RunState* st);
 __global__ void k_pe_scan(DevGraph g, Buffers b, RunState* st);
 __global__ void k_pe_expand(DevGraph g, Buffers b, RunState* st);
 __global__ void k_pull(DevGraph g, Buffers b, RunState* st);
+// Vertex push appending by CM_WARP or CM_ATOMIC (count-mode comparison)
+__global__ void k_push_thread_warp_count(DevGraph g, Buffers b, RunState* st);
+__global__ void k_push_thread_atomic_count(DevGraph g, Buffers b, RunState* st);
 __global__ void k_edge_list(DevGraph g, Buffers b, RunState* st);
 __global__ void k_rev_edge_list(DevGraph g, Buffers b, RunState* st);
 __global__ void k_build_origin(const int32_t* off, int32_t n, int32_t* origin);

@@ -94,6 +94,27 @@ def test_edge_list_variants(mode, variant):
     assert e.value.code == bfs.BFS_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("count_mode", [1, 2])
+def test_count_modes(count_mode):
+    """Section 3.1.4's frontier-count alternatives (warp-aggregated and
+    per-vertex atomics) in the vertex push: identical depths and per-level
+    counts; the other drivers reject them."""
+    for g in (gg.rmat(12, 16, seed=71), gg.grid(40, 30, 0.1, seed=72), gg.erdos_renyi(5000, 6.0, seed=73)):
+        with make(g) as G:
+            for r in gg.sample_roots(g, 2, seed=14):
+                ref = oracle.bfs(g.off, g.idx, int(r))
+                for v in (0, bfs.VARIANT_TREE):  # vertex push forced, and tree switching
+                    d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+                    st = bfs.bfs_run_ex(G.handle, int(r), d, forced_variant=v, mode=bfs.MODE_HOST_LOOP,
+                                        count_mode=count_mode, stats=True, log_capacity=ref.num_levels + 1)
+                    assert np.array_equal(d.cpu().numpy(), ref.depth)
+                    assert np.array_equal(st["frontier"][:ref.num_levels], ref.level_count)
+            for m in (bfs.MODE_PERSISTENT, bfs.MODE_GRAPH):
+                with pytest.raises(bfs.BFSError) as e:
+                    bfs.bfs_run_ex(G.handle, 0, d, mode=m, count_mode=count_mode)
+                assert e.value.code == bfs.BFS_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("mode", [bfs.MODE_PERSISTENT, bfs.MODE_GRAPH, bfs.MODE_HOST_LOOP])
 @pytest.mark.parametrize("variant", [bfs.VARIANT_TREE] + list(range(V)))
 def test_execution_modes_agree(mode, variant):
