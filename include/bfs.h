@@ -306,8 +306,9 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out);
  * reaching the most edges; it is timed on 8, 16, 32, 64 blocks, one per SM and
  * a full occupancy wave, and queries get the count with the least blocks x time
  * among those at most 4x slower than the fastest. One 64-root multi-source wave
- * (roots the probe reached; needs 256 n bytes of scratch, skipped if that does
- * not fit) decides whether queued queries are merged (merge_policy 0): when its
+ * (roots the probe reached, on the wave grid of at most two blocks per SM that
+ * merged queries run on; needs 256 n bytes of scratch, skipped if that does not
+ * fit) decides whether queued queries are merged (merge_policy 0): when its
  * blocks x time per root is below a single query's. Takes a few traversals'
  * time, up to about a second on a high-diameter graph of 16M vertices. */
 int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id);

@@ -69,6 +69,7 @@ struct bfs_server {
   std::vector<bfs_graph*> graphs;
   std::vector<int32_t> single_blocks;  // per graph: blocks of a single-query traversal
   std::vector<char> merge_ok;          // per graph: queued queries may be merged into waves
+  std::vector<int32_t> wave_blocks;    // per graph: blocks of a merged wave
   std::vector<cudaStream_t> streams;
   std::vector<int> stream_units;  // units in flight per stream (dispatcher thread only)
   std::vector<cudaEvent_t> free_events;
@@ -104,6 +105,10 @@ constexpr size_t kMaxGraphs = 256;
 constexpr int kScanDepth = 32;  // queue entries considered per admission pass
 // a query's block count may cost up to this factor in latency over the fastest
 constexpr float kLatencySlack = 4.0f;
+// a merged wave runs on at most this many blocks per SM, leaving room for the
+// single queries around it (a full-occupancy wave could only start on an idle
+// GPU and would hold all of it)
+constexpr int kWaveBlocksPerSm = 2;
 
 void finish_ticket(bfs_server* s, uint64_t t, int status) {
   auto it = s->tickets.find(t);
@@ -158,7 +163,8 @@ int launch_unit(bfs_server* s, Unit& u) {
       s->wave_staging[u.graph_id] = stage;
     }
     u.scratch = stage;
-    int rc = bfs::batch_async(g, roots, k, stage, u.stream, reinterpret_cast<unsigned long long*>(u.edges), 0);
+    int rc = bfs::batch_async(g, roots, k, stage, u.stream, reinterpret_cast<unsigned long long*>(u.edges),
+                              s->wave_blocks[u.graph_id]);
     if (rc != BFS_OK) return rc;
     for (int i = 0; i < k; ++i)
       if (u.reqs[i].depth_out &&
@@ -313,11 +319,13 @@ void dispatcher(bfs_server* s) {
 //     (the device share it holds) among those within kLatencySlack of the
 //     fastest, so latency-bound graphs run narrow and many of their queries
 //     share the GPU;
-//  3. one multi-source wave from 64 vertices the probe reached, on its full
-//     grid: same-graph queries are merged into waves only when a wave's
-//     blocks x time per root is below a single query's.
+//  3. one multi-source wave from 64 vertices the probe reached, on the grid
+//     waves get (at most kWaveBlocksPerSm blocks per SM): same-graph queries
+//     are merged into waves only when a wave's blocks x time per root is below
+//     a single query's.
 struct Shape {
   int32_t single_blocks = 0;
+  int32_t wave_blocks = 0;
   bool merge = false;
 };
 
@@ -394,12 +402,13 @@ int probe_shape(bfs_server* s, bfs_graph* g, Shape* out) {
     std::vector<int32_t> reached;
     for (int32_t v = 0; v < n && rc == BFS_OK; ++v)
       if (d[(size_t)v] >= 0) reached.push_back(v);
-    const int32_t wg = bfs::wave_grid(g);
+    const int32_t wg = std::min(bfs::wave_grid(g), kWaveBlocksPerSm * s->sms);
+    out->wave_blocks = std::max(wg, 1);
     if (rc == BFS_OK && wg > 0 && cudaMalloc(&wave_out, (size_t)64 * n * 4) == cudaSuccess) {
       int32_t roots[64];
       for (int i = 0; i < 64; ++i) roots[i] = reached[(size_t)i * reached.size() / 64];
       float wave_ms = 0;
-      rc = timed([&] { return bfs_run_batch(g, roots, 64, wave_out, stream, nullptr); }, &wave_ms);
+      rc = timed([&] { return bfs::batch_async(g, roots, 64, wave_out, stream, nullptr, wg); }, &wave_ms);
       if (rc == BFS_OK) out->merge = (double)wg * wave_ms / 64.0 < single_cost;
     }
     cudaGetLastError();  // a wave buffer that did not fit only disables merging
@@ -429,6 +438,7 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out) {
   s->graphs.reserve(kMaxGraphs);
   s->single_blocks.reserve(kMaxGraphs);
   s->merge_ok.reserve(kMaxGraphs);
+  s->wave_blocks.reserve(kMaxGraphs);
   s->free_depth.reserve(kMaxGraphs);
   s->wave_staging.reserve(kMaxGraphs);
   s->wave_busy.reserve(kMaxGraphs);
@@ -479,6 +489,7 @@ int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id) {
   s->graphs.push_back(g);
   s->single_blocks.push_back(shape.single_blocks);
   s->merge_ok.push_back(shape.merge ? 1 : 0);
+  s->wave_blocks.push_back(shape.wave_blocks);
   s->free_depth.emplace_back();
   s->wave_staging.push_back(nullptr);
   s->wave_busy.push_back(0);
