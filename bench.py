@@ -469,7 +469,8 @@ def bench_serve(bfs, torch, args):
                         break
                 st = bfs.bfs_serve_stats(s)
                 out["loads"].append({"offered_qps": rate, "achieved_qps": st["qps"], "p50_ms": st["p50_ms"],
-                                     "p99_ms": st["p99_ms"], "gteps": st["gteps"], "submitted": st["submitted"],
+                                     "p99_ms": st["p99_ms"], "wait_p50_ms": st["wait_p50_ms"],
+                                     "wait_p99_ms": st["wait_p99_ms"], "gteps": st["gteps"], "submitted": st["submitted"],
                                      "completed": st["completed"], "not_finished": st["submitted"] - st["completed"],
                                      "rejected": st["rejected"], "failed": st["failed"],
                                      "merged_waves": st["merged_waves"],

@@ -296,6 +296,7 @@ typedef struct bfs_serve_stats {
   double qps;                  /* completed / (last completion - first submission) */
   double p50_ms, p99_ms, max_ms; /* submission-to-completion latency */
   double gteps;                /* sum of edges_reached / 2 over completed queries / the same wall time / 1e9 */
+  double wait_p50_ms, wait_p99_ms; /* submission-to-admission part of the latency (time queued) */
 } bfs_serve_stats_t;
 
 /* Start a server (and its dispatcher thread) on the current device. */

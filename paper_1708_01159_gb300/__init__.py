@@ -95,7 +95,7 @@ class _ServeStats(ctypes.Structure):
                 ("rejected", ctypes.c_int64), ("failed", ctypes.c_int64), ("peak_bytes_inflight", ctypes.c_int64),
                 ("merged_waves", ctypes.c_int32), ("queued", ctypes.c_int32), ("qps", ctypes.c_double),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("gteps", ctypes.c_double)]
+                ("gteps", ctypes.c_double), ("wait_p50_ms", ctypes.c_double), ("wait_p99_ms", ctypes.c_double)]
 
 
 class _BatchConfig(ctypes.Structure):

@@ -91,7 +91,8 @@ struct bfs_server {
 
   // statistics (under mu)
   int64_t submitted = 0, admitted = 0, completed = 0, rejected = 0, failed = 0, waves = 0;
-  std::vector<double> latency_ms;
+  std::vector<double> latency_ms;  // submission to completion
+  std::vector<double> wait_ms;     // submission to admission
   double edges_half = 0;
   bool any_submit = false;
   Clock::time_point t_first, t_last;
@@ -275,9 +276,11 @@ void dispatcher(bfs_server* s) {
           s->wave_busy[gid] = 1;
           s->waves += 1;
         }
+        const auto t_admit = Clock::now();
         for (const Request& r : u.reqs) {
           auto t = s->tickets.find(r.ticket);
           if (t != s->tickets.end()) t->second.state = 2;
+          s->wait_ms.push_back(std::chrono::duration<double, std::milli>(t_admit - r.t_submit).count());
         }
         s->admitted += (int64_t)u.reqs.size();
         s->bytes_inflight += need;
@@ -570,16 +573,19 @@ int bfs_serve_stats(bfs_server_t s, bfs_serve_stats_t* out) {
   out->merged_waves = (int32_t)s->waves;
   out->peak_bytes_inflight = s->peak_bytes;
   out->queued = (int32_t)s->queue.size();
+  auto pct = [](std::vector<double> v, double p) {  // nearest rank
+    const size_t i = std::min(v.size() - 1, (size_t)(p * (double)(v.size() - 1) + 0.5));
+    std::nth_element(v.begin(), v.begin() + (long)i, v.end());
+    return v[i];
+  };
+  if (!s->wait_ms.empty()) {
+    out->wait_p50_ms = pct(s->wait_ms, 0.50);
+    out->wait_p99_ms = pct(s->wait_ms, 0.99);
+  }
   if (!s->latency_ms.empty()) {
-    std::vector<double> v = s->latency_ms;
-    auto pct = [&](double p) {
-      const size_t i = std::min(v.size() - 1, (size_t)(p * (double)(v.size() - 1) + 0.5));
-      std::nth_element(v.begin(), v.begin() + (long)i, v.end());
-      return v[i];
-    };
-    out->p50_ms = pct(0.50);
-    out->p99_ms = pct(0.99);
-    out->max_ms = *std::max_element(v.begin(), v.end());
+    out->p50_ms = pct(s->latency_ms, 0.50);
+    out->p99_ms = pct(s->latency_ms, 0.99);
+    out->max_ms = *std::max_element(s->latency_ms.begin(), s->latency_ms.end());
     const double wall = std::chrono::duration<double>(s->t_last - s->t_first).count();
     if (wall > 0) {
       out->qps = (double)s->completed / wall;

@@ -61,6 +61,7 @@ def test_mixed_results_equal_alone(graphs, merge, policy):
         st = bfs.bfs_serve_stats(s)
         assert st["completed"] == 240 and st["failed"] == 0 and st["admitted"] == 240
         assert st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"] and st["qps"] > 0 and st["gteps"] > 0
+        assert 0 <= st["wait_p50_ms"] <= st["wait_p99_ms"] <= st["max_ms"]
         if merge and policy == 1:
             assert st["merged_waves"] >= 1
         for gi in ids:
