@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <fstream>
 #include <functional>
 #include <memory>
@@ -195,7 +196,8 @@ struct bfs_graph {
   long long stats6[6] = {0, 0, 0, 0, 0, 0};
   Shapes shapes{};
   std::mutex mu;
-  std::vector<Workspace*> pool;
+  std::vector<Workspace*> pool;   // every workspace of the graph
+  std::deque<Workspace*> idle;    // those not being enqueued, in release order
   // device copies of the process-wide tree, one per version seen (old ones may
   // still be read by runs in flight, so they live until destroy)
   std::vector<TreeNode*> trees;
@@ -390,18 +392,31 @@ int create_workspace(bfs_graph* g, Workspace** out) {
   return BFS_OK;
 }
 
-// A workspace free for `stream`: idle on the device, or last used on the same
-// stream (then stream order protects it). At the pool limit the least recently
-// queued workspace is reused after `stream` waits for its last run.
+// A workspace free for `stream`: last used on the same stream (stream order
+// then protects it), or idle on the device. Released workspaces are kept in
+// release order and only the kIdleProbe oldest, the likeliest to have
+// finished, are queried, so a busy pool costs a few event queries per acquire,
+// not one per workspace. At the pool limit the oldest is reused after
+// `stream` waits for its last run.
+constexpr int kIdleProbe = 8;
 int acquire(bfs_graph* g, cudaStream_t stream, Workspace** out) {
   std::lock_guard<std::mutex> lk(g->mu);
   Workspace* pick = nullptr;
-  for (Workspace* ws : g->pool) {
-    if (ws->in_use) continue;
-    if (ws->last_stream == stream || cudaEventQuery(ws->done) == cudaSuccess) {
-      pick = ws;
+  auto& idle = g->idle;
+  for (auto it = idle.begin(); it != idle.end(); ++it)
+    if ((*it)->last_stream == stream) {
+      pick = *it;
+      idle.erase(it);
       break;
     }
+  if (!pick) {
+    int probed = 0;
+    for (auto it = idle.begin(); it != idle.end() && probed < kIdleProbe; ++it, ++probed)
+      if (cudaEventQuery((*it)->done) == cudaSuccess) {
+        pick = *it;
+        idle.erase(it);
+        break;
+      }
   }
   if (!pick && (int)g->pool.size() < kMaxWorkspaces) {
     Workspace* ws = nullptr;
@@ -410,12 +425,9 @@ int acquire(bfs_graph* g, cudaStream_t stream, Workspace** out) {
     pick = ws;
   }
   if (!pick) {
-    for (Workspace* ws : g->pool)
-      if (!ws->in_use) {
-        pick = ws;
-        break;
-      }
-    if (!pick) return fail(BFS_ERR_BUSY, "all %d workspaces are being enqueued", kMaxWorkspaces);
+    if (idle.empty()) return fail(BFS_ERR_BUSY, "all %d workspaces are being enqueued", kMaxWorkspaces);
+    pick = idle.front();
+    idle.pop_front();
     CU(cudaStreamWaitEvent(stream, pick->done, 0));
   }
   cudaGetLastError();  // clear a not-ready status from cudaEventQuery
@@ -429,6 +441,7 @@ int release(bfs_graph* g, Workspace* ws, cudaStream_t stream) {
   std::lock_guard<std::mutex> lk(g->mu);
   ws->last_stream = stream;
   ws->in_use = false;
+  g->idle.push_back(ws);
   if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
   return BFS_OK;
 }
