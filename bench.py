@@ -425,59 +425,54 @@ def bench_serve(bfs, torch, args):
         progress(f"serve graph {name} resident")
     rng = np.random.default_rng(5000)
     out = {"graphs": [n for n, _ in specs], "loads": [],
-           "warmup": "1000 queries submitted at once on a throwaway server before the measured loads (grows each "
-                     "graph's workspace pool; not reported)"}
+           "warmup": "one server for every load: graphs registered (probed) once, then 1000 queries submitted at "
+                     "once before the measured loads (fills the workspace and depth-buffer pools; not reported); "
+                     "each load starts a new statistics window and ends by cancelling what is still queued after "
+                     "the drain"}
+    s = bfs.bfs_serve_create(max_inflight=256, num_streams=256, queue_capacity=1 << 17, merge_batch=64)
     try:
-        # warm-up: workspaces are created on first need and then pooled with the graph
-        s = bfs.bfs_serve_create(max_inflight=256, num_streams=256, queue_capacity=1 << 17, merge_batch=64)
-        try:
-            ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
-            gsel = rng.integers(0, len(Gs), 1000)
-            tickets = [bfs.bfs_serve_submit(s, ids[k], int(cand[k][rng.integers(0, len(cand[k]))])) for k in gsel]
-            deadline = time.perf_counter() + 20.0
+        ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
+        out["shapes"] = {name: bfs.bfs_serve_graph_shape(s, i) for (name, _), i in zip(specs, ids)}
+
+        def drain(tickets, seconds):
+            deadline = time.perf_counter() + seconds
             for t in tickets:
                 left_us = int((deadline - time.perf_counter()) * 1e6)
                 if left_us <= 0 or bfs.bfs_serve_wait(s, t, left_us) == bfs.BFS_ERR_TIMEOUT:
-                    break
-        finally:
-            bfs.bfs_serve_destroy(s)
+                    return False
+            return True
+
+        gsel = rng.integers(0, len(Gs), 1000)
+        warm = [bfs.bfs_serve_submit(s, ids[k], int(cand[k][rng.integers(0, len(cand[k]))])) for k in gsel]
+        drain(warm, 30.0)
         progress("serve warm-up done")
         for rate in [float(x) for x in args.serve_rates.split(",")]:
             nq = int(rate * args.serve_seconds)
             arrivals = np.cumsum(rng.exponential(1.0 / rate, nq))
             gsel = rng.integers(0, len(Gs), nq)
             roots = [int(cand[k][rng.integers(0, len(cand[k]))]) for k in gsel]
-            s = bfs.bfs_serve_create(max_inflight=256, num_streams=256, queue_capacity=1 << 17, merge_batch=64)
-            try:
-                ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
-                out["shapes"] = {name: bfs.bfs_serve_graph_shape(s, i) for (name, _), i in zip(specs, ids)}
-                tickets = []
-                rejected = 0
-                t0 = time.perf_counter()
-                for q in range(nq):
-                    while time.perf_counter() - t0 < arrivals[q]:
-                        pass
-                    try:
-                        tickets.append(bfs.bfs_serve_submit(s, ids[gsel[q]], roots[q]))
-                    except bfs.BFSError:
-                        rejected += 1
-                # drain for at most 10 s; what is still queued then is cancelled at shutdown
-                deadline = time.perf_counter() + 10.0
-                for t in tickets:
-                    left_us = int((deadline - time.perf_counter()) * 1e6)
-                    if left_us <= 0 or bfs.bfs_serve_wait(s, t, left_us) == bfs.BFS_ERR_TIMEOUT:
-                        break
-                st = bfs.bfs_serve_stats(s)
-                out["loads"].append({"offered_qps": rate, "achieved_qps": st["qps"], "p50_ms": st["p50_ms"],
-                                     "p99_ms": st["p99_ms"], "wait_p50_ms": st["wait_p50_ms"],
-                                     "wait_p99_ms": st["wait_p99_ms"], "gteps": st["gteps"], "submitted": st["submitted"],
-                                     "completed": st["completed"], "not_finished": st["submitted"] - st["completed"],
-                                     "rejected": st["rejected"], "failed": st["failed"],
-                                     "merged_waves": st["merged_waves"],
-                                     "peak_bytes_inflight": st["peak_bytes_inflight"]})
-            finally:
-                bfs.bfs_serve_destroy(s)
+            bfs.bfs_serve_reset_stats(s)
+            tickets = []
+            t0 = time.perf_counter()
+            for q in range(nq):
+                while time.perf_counter() - t0 < arrivals[q]:
+                    pass
+                try:
+                    tickets.append(bfs.bfs_serve_submit(s, ids[gsel[q]], roots[q]))
+                except bfs.BFSError:
+                    pass  # counted by the server as rejected
+            drain(tickets, 10.0)  # what is still queued after 10 s is not finished
+            st = bfs.bfs_serve_stats(s)
+            out["loads"].append({"offered_qps": rate, "achieved_qps": st["qps"], "p50_ms": st["p50_ms"],
+                                 "p99_ms": st["p99_ms"], "wait_p50_ms": st["wait_p50_ms"],
+                                 "wait_p99_ms": st["wait_p99_ms"], "gteps": st["gteps"], "submitted": st["submitted"],
+                                 "completed": st["completed"], "not_finished": st["submitted"] - st["completed"],
+                                 "rejected": st["rejected"], "failed": st["failed"],
+                                 "merged_waves": st["merged_waves"], "peak_bytes_inflight": st["peak_bytes_inflight"]})
+            bfs.bfs_serve_cancel_queued(s)
+            drain(tickets, 60.0)  # the admitted ones finish before the next load
     finally:
+        bfs.bfs_serve_destroy(s)
         for G in Gs:
             G.close()
     return out

@@ -329,8 +329,17 @@ int bfs_serve_poll(bfs_server_t s, uint64_t ticket, int* state);
 /* Block until the query is done (timeout_us < 0: no limit). BFS_ERR_TIMEOUT if
  * it is still pending after timeout_us; otherwise the query's status. */
 int bfs_serve_wait(bfs_server_t s, uint64_t ticket, int64_t timeout_us);
-/* Counters and latency percentiles since creation (host struct). */
+/* Counters and latency percentiles since creation or the last
+ * bfs_serve_reset_stats (host struct). */
 int bfs_serve_stats(bfs_server_t s, bfs_serve_stats_t* out);
+/* Start a new statistics window: counters, latency records and the wall-time
+ * origin are cleared (queries in flight are counted in the new window when they
+ * complete). */
+int bfs_serve_reset_stats(bfs_server_t s);
+/* Load shedding: every query still queued (not yet admitted) finishes with
+ * BFS_ERR_CANCELLED; running ones are not touched. *cancelled (optional)
+ * receives how many were cancelled. */
+int bfs_serve_cancel_queued(bfs_server_t s, int64_t* cancelled);
 /* Let running queries finish, cancel queued ones (BFS_ERR_CANCELLED), stop the
  * dispatcher and free the server. A query larger than the whole budget is
  * admitted when nothing else is in flight, so every query eventually runs. */

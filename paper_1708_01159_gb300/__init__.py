@@ -149,6 +149,8 @@ def lib():
             "bfs_serve_create": (ctypes.c_int, [ctypes.POINTER(_ServeConfig), ctypes.POINTER(vp)]),
             "bfs_serve_add_graph": (ctypes.c_int, [vp, vp, ctypes.POINTER(c_i32)]),
             "bfs_serve_graph_shape": (ctypes.c_int, [vp, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+            "bfs_serve_reset_stats": (ctypes.c_int, [vp]),
+            "bfs_serve_cancel_queued": (ctypes.c_int, [vp, ctypes.POINTER(c_i64)]),
             "bfs_serve_submit": (ctypes.c_int, [vp, c_i32, c_i32, vp, ctypes.POINTER(ctypes.c_uint64)]),
             "bfs_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
             "bfs_serve_wait": (ctypes.c_int, [vp, ctypes.c_uint64, c_i64]),
@@ -396,6 +398,18 @@ def bfs_serve_stats(s: int) -> dict:
     st = _ServeStats()
     _check(lib().bfs_serve_stats(s, ctypes.byref(st)), "bfs_serve_stats")
     return {f: getattr(st, f) for f, _ in _ServeStats._fields_}
+
+
+def bfs_serve_reset_stats(s: int) -> None:
+    """Start a new statistics window."""
+    _check(lib().bfs_serve_reset_stats(s), "bfs_serve_reset_stats")
+
+
+def bfs_serve_cancel_queued(s: int) -> int:
+    """Cancel every query not yet admitted; returns how many."""
+    k = ctypes.c_int64(0)
+    _check(lib().bfs_serve_cancel_queued(s, ctypes.byref(k)), "bfs_serve_cancel_queued")
+    return k.value
 
 
 def bfs_serve_destroy(s: int) -> None:

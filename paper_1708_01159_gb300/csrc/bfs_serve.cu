@@ -595,6 +595,29 @@ int bfs_serve_stats(bfs_server_t s, bfs_serve_stats_t* out) {
   return BFS_OK;
 }
 
+int bfs_serve_reset_stats(bfs_server_t s) {
+  if (!s) return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->submitted = s->admitted = s->completed = s->rejected = s->failed = s->waves = 0;
+  s->latency_ms.clear();
+  s->wait_ms.clear();
+  s->edges_half = 0;
+  s->any_submit = false;
+  s->peak_bytes = s->bytes_inflight;
+  return BFS_OK;
+}
+
+int bfs_serve_cancel_queued(bfs_server_t s, int64_t* cancelled) {
+  if (!s) return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  const int64_t k = (int64_t)s->queue.size();
+  for (const Request& r : s->queue) finish_ticket(s, r.ticket, BFS_ERR_CANCELLED);
+  s->queue.clear();
+  if (cancelled) *cancelled = k;
+  s->done_cv.notify_all();
+  return BFS_OK;
+}
+
 int bfs_serve_destroy(bfs_server_t s) {
   if (!s) return BFS_OK;
   {

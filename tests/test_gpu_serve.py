@@ -134,3 +134,32 @@ def test_wait_timeout():
                 assert bfs.bfs_serve_wait(s, t) == bfs.BFS_OK
         finally:
             bfs.bfs_serve_destroy(s)
+
+
+def test_cancel_queued_and_stats_window():
+    """Load shedding cancels exactly the queries not yet admitted; running ones
+    finish; a statistics reset starts a new window."""
+    bfs.build()
+    g = gg.grid(400, 400, 0.1, seed=9)  # hundreds of levels: a query takes a while
+    with bfs.Graph(g.off, g.idx) as G:
+        s = bfs.bfs_serve_create(max_inflight=1, num_streams=1)
+        try:
+            gid = bfs.bfs_serve_add_graph(s, G.handle)
+            r = int(gg.sample_roots(g, 1, seed=1, giant=True)[0])
+            ts = [bfs.bfs_serve_submit(s, gid, r) for _ in range(10)]
+            k = bfs.bfs_serve_cancel_queued(s)
+            assert 1 <= k <= 9  # at least one was admitted, the tail of the queue was not
+            statuses = [bfs.bfs_serve_wait(s, t) for t in ts]
+            assert statuses.count(bfs.BFS_ERR_CANCELLED) == k
+            assert statuses.count(bfs.BFS_OK) == 10 - k
+            st = bfs.bfs_serve_stats(s)
+            assert st["completed"] == 10 - k and st["submitted"] == 10
+            bfs.bfs_serve_reset_stats(s)
+            st = bfs.bfs_serve_stats(s)
+            assert st["submitted"] == 0 and st["completed"] == 0 and st["p50_ms"] == 0
+            t = bfs.bfs_serve_submit(s, gid, r)
+            assert bfs.bfs_serve_wait(s, t) == bfs.BFS_OK
+            st = bfs.bfs_serve_stats(s)
+            assert st["submitted"] == 1 and st["completed"] == 1 and st["p50_ms"] > 0
+        finally:
+            bfs.bfs_serve_destroy(s)
