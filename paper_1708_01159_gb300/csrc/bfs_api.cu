@@ -11,6 +11,7 @@
 #include <deque>
 #include <fstream>
 #include <functional>
+#include <limits>
 #include <memory>
 #include <mutex>
 #include <sstream>
@@ -446,11 +447,24 @@ int release(bfs_graph* g, Workspace* ws, cudaStream_t stream) {
   return BFS_OK;
 }
 
-// Bit-parallel form of a tree (QsTree): leaves numbered by a left-first
-// depth-first walk from node 0, each internal node's mask clearing its left
-// subtree's leaves. False when the tree is too large for it or node 0 does not
-// root a tree (a node reached twice).
-bool build_qs(const std::vector<TreeNode>& t, QsTree* q) {
+// A test on a ppm share, floor(1e6 c / n) <= t, as the same test on the count
+// c itself: it holds exactly when 1e6 c < (t + 1) n, i.e. when c <= ceil((t +
+// 1) n / 1e6) - 1 (never for t < 0, always for t >= 1e6 since c <= n).
+long long ppm_to_count_threshold(long long t, long long n) {
+  if (t < 0) return -1;
+  if (t >= 1000000) return std::numeric_limits<long long>::max();
+  const long long a = (t + 1) * n;  // < 2^51 for n < 2^31
+  return (a + 999999) / 1000000 - 1;
+}
+
+// Bit-parallel form of a tree (QsTree) for one graph: leaves numbered by a
+// left-first depth-first walk from node 0, each internal node's mask clearing
+// its left subtree's leaves. A test on a graph feature (gfeat: n, m, degree
+// summary) is decided here: when it fails its mask goes into base, and either
+// way it leaves no node for the device. A test on a ppm share becomes the same
+// test on the count. False when the tree is too large for it or node 0 does
+// not root a tree (a node reached twice).
+bool build_qs(const std::vector<TreeNode>& t, const long long* gfeat, QsTree* q) {
   if (t.empty() || t.size() > 1024) return false;
   std::memset(q, 0, sizeof *q);
   std::vector<int> lo(t.size(), 0), hi(t.size(), 0);
@@ -476,19 +490,29 @@ bool build_qs(const std::vector<TreeNode>& t, QsTree* q) {
     }
     dfs(nd.l);
     dfs(nd.r);
-    if (!ok || nint >= kQsMax) {
+    if (!ok) return;
+    lo[i] = lo[nd.l];
+    hi[i] = hi[nd.r];
+    unsigned long long m = ~0ull;
+    for (int b = lo[nd.l]; b < hi[nd.l]; ++b) m &= ~(1ull << b);
+    if (nd.f < F_FRONTIER) {
+      if (!(gfeat[nd.f] <= nd.t)) q->base &= m;
+      return;
+    }
+    if (nint >= kQsMax) {
       ok = false;
       return;
     }
-    lo[i] = lo[nd.l];
-    hi[i] = hi[nd.r];
     QsNode& qn = q->node[nint++];
     qn.t = nd.t;
     qn.f = nd.f;
-    unsigned long long m = ~0ull;
-    for (int b = lo[nd.l]; b < hi[nd.l]; ++b) m &= ~(1ull << b);
+    if (nd.f == F_FRONTIER_PPM || nd.f == F_DISCOVERED_PPM) {
+      qn.f = nd.f == F_FRONTIER_PPM ? F_FRONTIER : F_DISCOVERED;
+      qn.t = ppm_to_count_threshold(nd.t, gfeat[F_N]);
+    }
     qn.mask = m;
   };
+  q->base = ~0ull;
   dfs(0);
   if (!ok) return false;
   q->n_int = nint;
@@ -505,7 +529,7 @@ int sync_tree(bfs_graph* g) {
   const size_t tree_bytes = ts.nodes.size() * sizeof(TreeNode);
   const size_t qs_off = (tree_bytes + 15) & ~size_t(15);
   QsTree qs;
-  const bool has_qs = build_qs(ts.nodes, &qs);
+  const bool has_qs = build_qs(ts.nodes, g->dg.gfeat, &qs);
   std::vector<char> host(qs_off + sizeof(QsTree), 0);
   std::memcpy(host.data(), ts.nodes.data(), tree_bytes);
   if (has_qs) std::memcpy(host.data() + qs_off, &qs, sizeof qs);

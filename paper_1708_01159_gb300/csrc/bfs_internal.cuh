@@ -72,20 +72,24 @@ static_assert(sizeof(TreeNode) == 24, "TreeNode layout");
 // al., SIGIR 2015): the leaves are numbered left to right; internal node k,
 // when its test x[f] <= t fails, clears the bits of the leaves of its left
 // subtree; after every failed test has cleared its bits, the lowest bit left
-// is the leaf the walk from the root reaches. All tests are independent, so a
-// block evaluates one per thread and ANDs the masks, instead of a chain of
-// dependent steps. Built on the host for trees of at most kQsMax internal
-// nodes and kQsMax leaves.
+// is the leaf the walk from the root reaches. All tests are independent, so
+// the lanes of a warp evaluate one each and AND the masks, instead of a chain
+// of dependent steps. Built on the host for one graph, for trees of at most
+// kQsMax internal nodes and kQsMax leaves: the tests on the graph's own
+// features (n, m, degree summary) have the same outcome at every level, so the
+// host folds them into `base` and only the tests on level features
+// (frontier, discovered, frontier edges, level) remain in node[].
 constexpr int kQsMax = 64;
 struct QsNode {
   long long t;
   unsigned long long mask;  // all ones except the bits of the left subtree's leaves
-  int32_t f;
+  int32_t f;                // a level feature: F_FRONTIER, F_DISCOVERED, F_FRONTIER_EDGES or F_LEVEL
   int32_t pad;
 };
 struct QsTree {
-  int32_t n_int;   // internal nodes
-  int32_t n_leaf;  // leaves
+  int32_t n_int;             // remaining (level-feature) internal nodes
+  int32_t n_leaf;            // leaves
+  unsigned long long base;   // AND of the masks of the graph-feature tests that fail on this graph
   QsNode node[kQsMax];
   int32_t leaf[kQsMax];  // class of each leaf, left to right (-1: unknown)
 };

@@ -264,25 +264,33 @@ __device__ __forceinline__ int32_t walk_tree(const DevGraph& g, const TreeNode* 
   return -1;
 }
 
-// The tree's prediction by the bit-parallel form: thread k tests internal
-// node k, the warps AND their masks, the lowest surviving bit names the leaf.
-// Every thread of the block calls it (it synchronises); s_and: one word per
-// warp of shared memory.
-__device__ __forceinline__ int32_t qs_eval(const DevGraph& g, const QsTree& q, int32_t L, long long f, long long e,
-                                           long long discovered, unsigned long long* s_and) {
-  unsigned long long m = ~0ull;
-  if ((int)threadIdx.x < q.n_int) {
-    const QsNode nd = q.node[threadIdx.x];
-    if (!feature_le(g, nd.f, nd.t, L, f, e, discovered)) m = nd.mask;
+// The test x_fi <= t of a level feature without branches, so that the lanes
+// of a warp, each on a different feature, do not diverge. The ppm shares do not
+// occur here: the host rewrote each as the equivalent test on the count
+// (floor(1e6 c / n) <= t is c <= ceil((t + 1) n / 1e6) - 1).
+__device__ __forceinline__ bool level_feature_le(int32_t fi, long long t, int32_t L, long long f, long long e,
+                                                 long long discovered) {
+  long long x = L;
+  x = (fi == F_FRONTIER) ? f : x;
+  x = (fi == F_DISCOVERED) ? discovered : x;
+  x = (fi == F_FRONTIER_EDGES) ? e : x;
+  return x <= t;
+}
+
+// The tree's prediction by the bit-parallel form, within one warp: lane k
+// tests the level-feature nodes k, k + 32; the graph-feature tests are already
+// folded into q.base. Every lane of the warp calls it and gets the same
+// result; no block-wide synchronisation.
+__device__ __forceinline__ int32_t qs_eval_warp(const QsTree& q, int32_t L, long long f, long long e,
+                                                long long discovered) {
+  unsigned long long m = q.base;
+  for (int k = lane_id(); k < q.n_int; k += 32) {
+    const QsNode nd = q.node[k];
+    if (!level_feature_le(nd.f, nd.t, L, f, e, discovered)) m &= nd.mask;
   }
   const uint32_t lo = __reduce_and_sync(kFull, (uint32_t)m);
   const uint32_t hi = __reduce_and_sync(kFull, (uint32_t)(m >> 32));
-  const int nw = (q.n_int + 31) >> 5;
-  if (lane_id() == 0 && (int)(threadIdx.x >> 5) < nw) s_and[threadIdx.x >> 5] = ((unsigned long long)hi << 32) | lo;
-  __syncthreads();
-  unsigned long long all = ~0ull;
-  for (int k = 0; k < nw; ++k) all &= s_and[k];
-  const int leaf = __ffsll((long long)all) - 1;
+  const int leaf = __ffsll((long long)(((unsigned long long)hi << 32) | lo)) - 1;
   return (leaf >= 0 && leaf < q.n_leaf) ? q.leaf[leaf] : -1;
 }
 
@@ -873,15 +881,14 @@ __global__ void k_loop_start(DevGraph g, Buffers b, RunState* st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) cudaGraphSetConditional((cudaGraphConditionalHandle)st->h_while, 1u);
 }
 
-// Level end + tree evaluation, between levels on the device (one thread).
-// Launched with kDecideThreads threads (one block): thread 0 closes the level
-// and keeps the state; all of them evaluate a tree that has a bit-parallel form
-// (one thread per internal node), else thread 0 walks it.
+// Level end + tree evaluation, between levels on the device. Launched with
+// kDecideThreads threads (one warp): lane 0 closes the level and keeps the
+// state; the warp evaluates a tree that has a bit-parallel form, else lane 0
+// walks it.
 __global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b, RunState* st) {
   (void)b;
   __shared__ long long s_in[3];  // f, e, discovered
   __shared__ int32_t s_go;       // 1: evaluate the tree this level
-  __shared__ unsigned long long s_and[kDecideThreads / 32];
   RunState& s = *st;
   int32_t L = 0;
   if (threadIdx.x == 0) {
@@ -921,7 +928,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b
   L = st->level;
   int32_t v = s.forced;
   const QsTree* qs = s.tree_qs;
-  if (v < 0 && qs != nullptr) v = qs_eval(g, *qs, L, f, e, discovered, s_and);  // all threads
+  if (v < 0 && qs != nullptr) v = qs_eval_warp(*qs, L, f, e, discovered);  // the whole warp
   if (threadIdx.x != 0) return;
   if (v < 0 && qs == nullptr && s.tree != nullptr && s.tree_nodes > 0)
     v = walk_tree(g, s.tree, s.tree_nodes, L, f, e, discovered);
@@ -1101,11 +1108,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   __shared__ alignas(128) int32_t ubuf[2 * kPeSlot];
   __shared__ alignas(8) uint64_t bar[2];
   __shared__ int s_split[2];
-  // the tree is evaluated by every block every level: its bit-parallel form
+  // the tree is evaluated by every warp every level: its bit-parallel form
   // (trees of up to 64 leaves) is kept in shared memory; larger trees are
   // walked in global memory
   __shared__ QsTree s_qs;
-  __shared__ unsigned long long s_and[kThreads / 32];
   const bool use_qs = qs != nullptr;
   if (use_qs) {
     static_assert(sizeof(QsTree) % 4 == 0, "QsTree copy");
@@ -1154,7 +1160,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     int32_t vw = 32;
     int32_t v = forced;
     if (v < 0 && use_qs)
-      v = qs_eval(g, s_qs, L, f, (long long)e, discovered, s_and);
+      v = qs_eval_warp(s_qs, L, f, (long long)e, discovered);
     else if (v < 0 && tree != nullptr && tree_nodes > 0)
       v = walk_tree(g, tree, tree_nodes, L, f, (long long)e, discovered);
     v = finish_variant(v, L, prev, f, (long long)e, &vw, forced >= 0);

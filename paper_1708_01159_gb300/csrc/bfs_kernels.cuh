@@ -6,7 +6,7 @@
 namespace bfs {
 
 constexpr int kThreads = 256;     // block size of the level kernels
-constexpr int kDecideThreads = 64;  // block size of k_decide: one thread per node of a bit-parallel tree (kQsMax)
+constexpr int kDecideThreads = 32;  // block size of k_decide: one warp evaluates the bit-parallel tree
 constexpr int kCtaChunk = 2048;   // int32 per shared-memory stage of the CTA variant (8 KB)
 constexpr int kCtaDirect = 512;   // adjacency shorter than this is read directly, not staged
 constexpr int kPeItems = 8;       // items per thread in the edge-centric scan / expand

@@ -360,6 +360,58 @@ def test_random_trees_schedule_matches_oracle_walk(tmp_path, depth):
             bfs.bfs_load_tree(None)
 
 
+def _write_tree(path, nodes):
+    path.write_text(f"bfs-tree 1 {len(nodes)}\n" + "".join(
+        f"{n['f']} {n['t']} {n['l']} {n['r']} {n['v']}\n" for n in nodes))
+
+
+def _stump(f, t, left, right):
+    return [{"f": f, "t": t, "l": 1, "r": 2, "v": -1}, {"f": -1, "t": 0, "l": -1, "r": -1, "v": left},
+            {"f": -1, "t": 0, "l": -1, "r": -1, "v": right}]
+
+
+def test_tree_threshold_edges(tmp_path):
+    """Split thresholds at the edges of each feature's range: ppm thresholds
+    below 0 and at 1e6, thresholds equal to an observed value and one below it
+    (the <= boundary, ppm compared without dividing), and trees whose only tests
+    are on graph features (decided once per graph, no level test left). Every
+    driver's schedule equals the oracle's walk."""
+    g = gg.rmat(13, 16, seed=46)
+    roots = [int(r) for r in gg.sample_roots(g, 2, seed=9)]
+    refs = [(r, oracle.bfs(g.off, g.idx, r)) for r in roots]
+    feats = oracle.level_features(g.off, refs[0][1])
+    mid = feats[len(feats) // 2]
+    trees = [_stump(9, -1, 1, 4), _stump(11, -1, 1, 4), _stump(9, 1000000, 1, 4), _stump(11, 999999, 1, 4)]
+    for fi in (8, 9, 10, 11, 12, 13):
+        trees += [_stump(fi, mid[fi], 0, 4), _stump(fi, mid[fi] - 1, 2, 3)]
+    for fi in range(8):  # graph features only
+        trees += [_stump(fi, feats[0][fi], 1, 4), _stump(fi, feats[0][fi] - 1, 1, 4)]
+    # a graph-feature test above a level-feature test, and below one
+    trees.append([{"f": 6, "t": feats[0][6], "l": 1, "r": 2, "v": -1},
+                  {"f": 11, "t": mid[11], "l": 3, "r": 4, "v": -1},
+                  {"f": -1, "t": 0, "l": -1, "r": -1, "v": 2},
+                  {"f": -1, "t": 0, "l": -1, "r": -1, "v": 3},
+                  {"f": -1, "t": 0, "l": -1, "r": -1, "v": 4}])
+    trees.append([{"f": 8, "t": mid[8], "l": 1, "r": 2, "v": -1},
+                  {"f": 0, "t": feats[0][0] - 1, "l": 3, "r": 4, "v": -1},
+                  {"f": -1, "t": 0, "l": -1, "r": -1, "v": 1},
+                  {"f": -1, "t": 0, "l": -1, "r": -1, "v": 0},
+                  {"f": -1, "t": 0, "l": -1, "r": -1, "v": 4}])
+    with make(g) as G:
+        for k, nodes in enumerate(trees):
+            p = tmp_path / f"e{k}.tree"
+            _write_tree(p, nodes)
+            bfs.bfs_load_tree(str(p))
+            try:
+                for r, ref in refs:
+                    want = oracle.predict_schedule({"nodes": nodes}, oracle.level_features(g.off, ref))
+                    for mode in (bfs.MODE_PERSISTENT, bfs.MODE_GRAPH, bfs.MODE_HOST_LOOP):
+                        _, st = assert_parity(g, G, r, mode=mode)
+                        assert st["variant"][:len(want)].tolist() == want, (k, nodes[0], mode)
+            finally:
+                bfs.bfs_load_tree(None)
+
+
 def test_profile_levels_features_match_oracle():
     g = gg.rmat(13, 16, seed=51)
     r = int(gg.sample_roots(g, 1, seed=8)[0])
