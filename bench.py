@@ -138,6 +138,19 @@ def workload_name(args, g):
             f"deduplicated): {g.n:,} vertices, {g.m:,} directed edges; {args.roots} roots in the giant component")
 
 
+def aggregate_ranks(total_s, edges_local, device):
+    """Whole-job GTEPS of independent replicas (one per rank, no data-path
+    collective): the edges all ranks traversed (edges_reached / 2, summed) over
+    the slowest rank's timed seconds. Returns (GTEPS, max seconds)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(edges_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(e.item()) / float(t.item()) / 1e9, float(t.item())
+
+
 def harmonic_gteps(times_s, edges):
     """k / sum(1 / GTEPS_i), GTEPS_i = (edges_i / 2) / t_i / 1e9."""
     inv = [t / (e / 2.0 / 1e9) for t, e in zip(times_s, edges)]
@@ -548,13 +561,7 @@ def run_ours(args):
     value_local = harmonic_gteps(times, np.tile(edges, args.steps))
     total_edges_local = float(edges.sum()) * args.steps / 2.0
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([total_edges_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        value = float(e.item()) / float(t.item()) / 1e9
-        total_s = float(t.item())
+        value, total_s = aggregate_ranks(total_s, total_edges_local, dev)
     else:
         value = value_local
 
