@@ -1,0 +1,94 @@
+"""The tree-training pipeline on CPU: the integer export reproduces the fitted
+classifier, a tied leaf becomes the unknown prediction of Section 4.1, the
+library parses what the exporter writes, and the Table-2-shaped evaluation
+and the paper's level split run on a small synthetic level table."""
+import contextlib
+import io
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_1708_01159_gb300 import FEATURES, NUM_VARIANTS, train
+
+pytest.importorskip("sklearn.tree")
+
+
+def _levels(seed=0, n=600):
+    """A synthetic level table: integer features, per-variant times whose
+    fastest variant depends on the frontier size (feature 8) and the level."""
+    rng = np.random.default_rng(seed)
+    X = rng.integers(0, 10_000, size=(n, len(FEATURES))).astype(np.int64)
+    X[:, 13] = np.arange(n) % 12
+    T = rng.uniform(1.0, 2.0, size=(n, NUM_VARIANTS))
+    best = np.where(X[:, 8] < 3000, 1, np.where(X[:, 8] < 7000, 3, 4))
+    T[np.arange(n), best] = 0.5
+    graph = np.array([f"g{i // 120}" for i in range(n)])
+    root = np.array([(i // 12) % 10 for i in range(n)])
+    return graph, root, X[:, 13].copy(), X, T
+
+
+def test_export_walk_equals_predict(tmp_path):
+    graph, root, level, X, T = _levels()
+    fidx = np.array(train.FEATURE_SETS["ext"])
+    clf = train.fit(X, T, fidx, max_depth=6, min_samples_leaf=4, weighting="uniform")
+    path = tmp_path / "t.tree"
+    train.export(clf, fidx, str(path), meta="unit test")
+    nodes = train.read_tree(str(path))
+    Xt = np.random.default_rng(1).integers(0, 10_000, size=(2000, len(FEATURES)))
+    pred = clf.predict(Xt[:, fidx])
+    walk = np.array([train.walk(nodes, x) for x in Xt])
+    known = walk >= 0
+    assert known.mean() > 0.9
+    assert np.array_equal(walk[known], pred[known])
+
+
+def test_tied_leaf_is_exported_unknown(tmp_path):
+    # every sample identical, two classes with equal weight: one leaf, a tie
+    X = np.zeros((4, len(FEATURES)), dtype=np.int64)
+    T = np.array([[0.5, 1, 1, 1, 1], [1, 0.5, 1, 1, 1]] * 2, dtype=float)
+    clf = train.fit(X, T, np.array(train.FEATURE_SETS["paper"]), max_depth=3, min_samples_leaf=1,
+                    weighting="uniform")
+    path = tmp_path / "tie.tree"
+    train.export(clf, np.array(train.FEATURE_SETS["paper"]), str(path))
+    nodes = train.read_tree(str(path))
+    assert len(nodes) == 1 and nodes[0]["v"] == -1
+    # the unknown rule: level 0 falls back to the edge-centric push, later levels repeat
+    lv = np.array([0, 1, 2])
+    assert train.schedule_time(nodes, X[:3], T[:3], lv).tolist() == [train.LEVEL0_DEFAULT] * 3
+
+
+def test_library_parses_exported_tree(tmp_path):
+    import paper_1708_01159_gb300 as bfs
+    try:
+        bfs.lib()
+    except RuntimeError:
+        pytest.skip("libbfs.so not built")
+    graph, root, level, X, T = _levels(2)
+    fidx = np.array(train.FEATURE_SETS["paper"])
+    clf = train.fit(X, T, fidx, max_depth=8, min_samples_leaf=2, weighting="regret")
+    path = tmp_path / "x.tree"
+    train.export(clf, fidx, str(path))
+    bfs.bfs_load_tree(str(path))
+    bfs.bfs_load_tree(None)
+
+
+def test_evaluate_and_level_split():
+    graph, root, level, X, T = _levels(3)
+    fidx = np.array(train.FEATURE_SETS["ext"])
+    clf = train.fit(X, T, fidx, max_depth=8, min_samples_leaf=1, weighting="uniform")
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "e.tree")
+        train.export(clf, fidx, p)
+        s = train.evaluate(graph, root, level, X, T, train.read_tree(p))
+    # the fit separates the synthetic rule exactly, so the schedule is the optimum
+    assert s["level_accuracy"] == pytest.approx(1.0)
+    assert s["predicted"]["average"] == pytest.approx(1.0)
+    assert s["best_fixed"]["average"] > 1.0
+    out = io.StringIO()
+    with contextlib.redirect_stdout(out):
+        train.level_split(graph, root, level, X, T, depths=(6,))
+    lines = out.getvalue().strip().splitlines()
+    assert len(lines) == len(train.FEATURE_SETS) * 2
+    assert all("held-out level accuracy" in ln for ln in lines)
