@@ -1,0 +1,74 @@
+"""Host-side arithmetic of bench.py, on CPU: the per-level algorithmic bytes
+behind the reported roofline (checked against a plain vertex-by-vertex count),
+the harmonic-mean GTEPS and the traffic lookup's staleness rule."""
+import hashlib
+import json
+
+import numpy as np
+import pytest
+
+import bench
+import graphgen as gg
+import oracle
+
+
+def _pull_bytes_plain(g, depth, L, nxt):
+    """Pull at level L, counted vertex by vertex: every bitmap word read and
+    written (8 B), the row extents of each vertex not visited by level L that
+    has in-edges (4 B), the adjacency entries it scans in order up to and
+    including its first in-neighbour at depth L, or all of them (4 B each),
+    and the depth and queue writes plus degree read of each new vertex (8 B)."""
+    words = (g.n + 31) // 32
+    U = S = 0
+    for v in range(g.n):
+        lo, hi = int(g.off[v]), int(g.off[v + 1])
+        if hi == lo or 0 <= depth[v] <= L:
+            continue
+        U += 1
+        k = 0
+        for e in range(lo, hi):
+            k += 1
+            if depth[g.idx[e]] == L:
+                break
+        S += k
+    return 8 * words + 4 * U + 4 * S + 8 * nxt
+
+
+@pytest.mark.parametrize("make", [lambda: gg.rmat(10, 8, seed=71), lambda: gg.grid(30, 20, 0.2, seed=72),
+                                  lambda: gg.erdos_renyi(3000, 3.0, seed=73)])
+def test_algorithmic_bytes_matches_plain_count(make):
+    g = make()
+    for r in gg.sample_roots(g, 2, seed=74):
+        res = oracle.bfs(g.off, g.idx, int(r))
+        feats = oracle.level_features(g.off, res)
+        for L in range(res.num_levels):
+            f = int(res.level_count[L])
+            e = int(res.level_edges[L])
+            nxt = int(res.level_count[L + 1]) if L + 1 < res.num_levels else 0
+            for v in range(4):  # every push variant moves the same bytes
+                assert bench.algorithmic_bytes(g, res.depth, feats, L, v) == 12 * f + 4 * e + 16 * nxt
+            assert bench.algorithmic_bytes(g, res.depth, feats, L, 4) == _pull_bytes_plain(g, res.depth, L, nxt)
+
+
+def test_harmonic_gteps():
+    # GTEPS_i = (e_i / 2) / t_i / 1e9; harmonic mean k / sum(1 / GTEPS_i)
+    times = [1.0, 2.0, 4.0]
+    edges = [2e9, 2e9, 2e9]  # 1, 0.5, 0.25 GTEPS
+    assert bench.harmonic_gteps(times, edges) == pytest.approx(3 / (1 + 2 + 4))
+    assert bench.harmonic_gteps([0.5], [4e9]) == pytest.approx(4.0)
+
+
+def test_traffic_lookup_requires_current_kernel_source(tmp_path, monkeypatch):
+    root = tmp_path
+    src_dir = root / "paper_1708_01159_gb300" / "csrc"
+    src_dir.mkdir(parents=True)
+    (src_dir / "bfs_kernels.cu").write_text("// kernels v1\n")
+    (root / "profiles").mkdir()
+    sha = hashlib.sha256(b"// kernels v1\n").hexdigest()[:16]
+    (root / "profiles" / "traffic.json").write_text(json.dumps(
+        {"kernels_sha": sha, "per_launch_bytes": {"pull": 123}}))
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.traffic_for("pull") == 123
+    assert bench.traffic_for("absent") is None
+    (src_dir / "bfs_kernels.cu").write_text("// kernels v2\n")  # the kernel changed: the capture is stale
+    assert bench.traffic_for("pull") is None
