@@ -61,6 +61,8 @@ NUM_FEATURES = len(FEATURES)
 
 
 class BFSError(RuntimeError):
+    """A non-zero status from the library; .code is the bfs_status value."""
+
     def __init__(self, code: int, where: str, detail: str):
         super().__init__(f"{where}: {status_string(code)} ({code}): {detail}")
         self.code = code
@@ -166,6 +168,7 @@ def lib():
 
 
 def status_string(code: int) -> str:
+    """The library's text for a status code (the number itself if the library is not built)."""
     try:
         return lib().bfs_status_string(code).decode()
     except Exception:  # library unavailable
@@ -225,10 +228,12 @@ def bfs_graph_create(row_offsets, col_indices, flags: int = BFS_SYMMETRIC) -> in
 
 
 def bfs_graph_destroy(g: int) -> None:
+    """Free a graph and its workspaces once its runs have finished."""
     _check(lib().bfs_graph_destroy(g), "bfs_graph_destroy")
 
 
 def bfs_graph_info(g: int) -> dict:
+    """Sizes, out-degree 5-number summary and floor(256 sd), resident bytes, symmetry, workspace count."""
     info = _GraphInfo()
     _check(lib().bfs_graph_info(g, ctypes.byref(info)), "bfs_graph_info")
     return {"n": info.n, "m": info.m, "deg_summary": list(info.deg_summary), "deg_sd256": info.deg_sd256,
@@ -301,6 +306,9 @@ def bfs_run_batch(g: int, roots, depth_out, stream=None, edges: bool = False):
 
 
 def bfs_batch_set_config(g: int, push_mode: int, alpha: int, grid_blocks: int = 0) -> None:
+    """Fix the multi-source launch shape of a graph: push_mode 0 (thread per vertex,
+    block for hubs) or 1 (warp per vertex), pull when frontier edges x alpha > m,
+    grid_blocks (0: a full occupancy wave)."""
     c = _BatchConfig(push_mode=push_mode, alpha=alpha, grid_blocks=grid_blocks)
     _check(lib().bfs_batch_set_config(g, ctypes.byref(c)), "bfs_batch_set_config")
 
@@ -348,6 +356,10 @@ def bfs_run_static(row_offsets, col_indices, root: int, depth_out, stream=None) 
 
 def bfs_serve_create(mem_budget_bytes: int = 0, max_inflight: int = 16, num_streams: int = 8,
                      queue_capacity: int = 1 << 16, merge_batch: int = 0, merge_policy: int = 0) -> int:
+    """Start a query server (its dispatcher thread owns the device side); returns its handle.
+    mem_budget_bytes: admission budget (0: none); max_inflight: units on the device at once;
+    merge_batch: most roots per merged multi-source wave (0 or 1: no merging); merge_policy:
+    0 merges where the registration probe found waves cheaper, 1 merges always."""
     c = _ServeConfig(mem_budget_bytes=mem_budget_bytes, max_inflight=max_inflight, num_streams=num_streams,
                      queue_capacity=queue_capacity, merge_batch=merge_batch, merge_policy=merge_policy)
     out = ctypes.c_void_p()
@@ -356,6 +368,7 @@ def bfs_serve_create(mem_budget_bytes: int = 0, max_inflight: int = 16, num_stre
 
 
 def bfs_serve_add_graph(s: int, g: int) -> int:
+    """Register a resident graph with the server (probes its query shape); returns its graph id."""
     gid = ctypes.c_int32()
     _check(lib().bfs_serve_add_graph(s, g, ctypes.byref(gid)), "bfs_serve_add_graph")
     return gid.value
@@ -395,6 +408,7 @@ def bfs_serve_wait(s: int, ticket: int, timeout_us: int = -1) -> int:
 
 
 def bfs_serve_stats(s: int) -> dict:
+    """Counters, queries/s, GTEPS, latency and queue-wait percentiles since creation or the last reset."""
     st = _ServeStats()
     _check(lib().bfs_serve_stats(s, ctypes.byref(st)), "bfs_serve_stats")
     return {f: getattr(st, f) for f, _ in _ServeStats._fields_}
@@ -413,6 +427,7 @@ def bfs_serve_cancel_queued(s: int) -> int:
 
 
 def bfs_serve_destroy(s: int) -> None:
+    """Stop the server: queued queries are cancelled, running ones finish."""
     _check(lib().bfs_serve_destroy(s), "bfs_serve_destroy")
 
 
