@@ -142,6 +142,10 @@ int parse_tree(const std::string& text, std::vector<TreeNode>* out) {
     TreeNode nd{};
     long long f, l, r, v;
     if (!(ls >> f >> nd.t >> l >> r >> v)) return fail(BFS_ERR_INVALID_ARG, "bad tree node line: %s", line.c_str());
+    // narrowed to int32 below: out-of-range values must not wrap into valid ones
+    const auto fits = [](long long x) { return x >= -1 && x <= std::numeric_limits<int32_t>::max(); };
+    if (!fits(f) || !fits(l) || !fits(r) || !fits(v))
+      return fail(BFS_ERR_INVALID_ARG, "tree node field out of range: %s", line.c_str());
     nd.f = (int32_t)f;
     nd.l = (int32_t)l;
     nd.r = (int32_t)r;

@@ -79,3 +79,25 @@ def test_tree_files(lib, tmp_path):
     bad.write_text("bfs-tree 1 3\n99 5 1 2 -1\n-1 0 -1 -1 3\n-1 0 -1 -1 4\n")  # feature out of range
     with pytest.raises(bfs.BFSError):
         bfs.bfs_load_tree(str(bad))
+    good_leaves = "-1 0 -1 -1 3\n-1 0 -1 -1 4\n"
+    for text in (
+        "bfs-tree 1 3\n4294967304 5 1 2 -1\n" + good_leaves,  # feature 2^32 + 8 must not wrap to 8
+        "bfs-tree 1 3\n8 5 4294967297 2 -1\n" + good_leaves,  # child 2^32 + 1 must not wrap to 1
+        "bfs-tree 1 1\n-1 0 -1 -1 4294967297\n",              # class 2^32 + 1 must not wrap to 1
+        "bfs-tree 1 3\n8 5 1 3 -1\n" + good_leaves,            # child past the last node
+        "bfs-tree 2 3\n8 5 1 2 -1\n" + good_leaves,            # unknown format version
+        "bfs-tree 1 0\n",                                       # no nodes
+        "bfs-tree 1 4\n8 5 1 2 -1\n" + good_leaves,            # fewer nodes than declared
+        "bfs-tree 1 3\n8 five 1 2 -1\n" + good_leaves,         # not a number
+        "8 5 1 2 -1\n" + good_leaves,                            # no header
+    ):
+        bad.write_text(text)
+        with pytest.raises(bfs.BFSError) as e:
+            bfs.bfs_load_tree(str(bad))
+        assert e.value.code == bfs.BFS_ERR_INVALID_ARG, text
+    # a subtree shared by two parents is a valid tree file (every walk ends);
+    # it is walked node by node instead of bit-parallel
+    ok = tmp_path / "dag.tree"
+    ok.write_text("bfs-tree 1 4\n8 5 1 2 -1\n10 7 3 3 -1\n12 9 3 3 -1\n-1 0 -1 -1 1\n")
+    bfs.bfs_load_tree(str(ok))
+    bfs.bfs_load_tree(None)
