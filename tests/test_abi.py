@@ -101,3 +101,34 @@ def test_tree_files(lib, tmp_path):
     ok.write_text("bfs-tree 1 4\n8 5 1 2 -1\n10 7 3 3 -1\n12 9 3 3 -1\n-1 0 -1 -1 1\n")
     bfs.bfs_load_tree(str(ok))
     bfs.bfs_load_tree(None)
+
+
+def test_serve_and_batch_argument_checks(lib):
+    """Server configurations out of range and null handles are rejected before
+    any CUDA call (these run on a machine without a GPU)."""
+    good = dict(mem_budget_bytes=0, max_inflight=16, num_streams=8, queue_capacity=1024, merge_batch=0,
+                merge_policy=0, reserved=0)
+    out = ctypes.c_void_p()
+    for field, value in (("max_inflight", 0), ("max_inflight", 1025), ("num_streams", 0), ("num_streams", 1025),
+                         ("queue_capacity", 0), ("merge_batch", -1), ("merge_batch", 65),
+                         ("mem_budget_bytes", -1), ("merge_policy", 2), ("reserved", 1)):
+        cfg = bfs._ServeConfig(**dict(good, **{field: value}))
+        assert lib.bfs_serve_create(ctypes.byref(cfg), ctypes.byref(out)) == bfs.BFS_ERR_INVALID_ARG, field
+    cfg = bfs._ServeConfig(**good)
+    assert lib.bfs_serve_create(None, ctypes.byref(out)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_create(ctypes.byref(cfg), None) == bfs.BFS_ERR_INVALID_ARG
+    i32, u64, i64 = ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_int64()
+    st = ctypes.c_int()
+    stats = bfs._ServeStats()
+    assert lib.bfs_serve_add_graph(None, None, ctypes.byref(i32)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_graph_shape(None, 0, ctypes.byref(i32), ctypes.byref(i32)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_submit(None, 0, 0, None, ctypes.byref(u64)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_poll(None, 1, ctypes.byref(st)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_wait(None, 1, 0) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_stats(None, ctypes.byref(stats)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_reset_stats(None) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_cancel_queued(None, ctypes.byref(i64)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_serve_destroy(None) == bfs.BFS_OK
+    bc = bfs._BatchConfig(push_mode=2, alpha=8, grid_blocks=0)
+    assert lib.bfs_batch_set_config(None, ctypes.byref(bc)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_run_batch(None, None, 1, None, None, None) == bfs.BFS_ERR_INVALID_ARG
