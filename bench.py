@@ -151,6 +151,18 @@ def aggregate_ranks(total_s, edges_local, device):
     return float(e.item()) / float(t.item()) / 1e9, float(t.item())
 
 
+def per_root_summary(times_s, edges, steps):
+    """Per-root view of the timed steps (times step-major, one per root per
+    step): the harmonic-mean GTEPS of each root's median and of its mean time,
+    and the spread of the per-root GTEPS over the roots."""
+    t = np.asarray(times_s, dtype=np.float64).reshape(steps, len(edges))
+    med, mean = np.median(t, axis=0), t.mean(axis=0)
+    g = np.asarray(edges, dtype=np.float64) / 2.0 / med / 1e9
+    return {"harmonic_gteps_of_medians": harmonic_gteps(med, edges),
+            "harmonic_gteps_of_means": harmonic_gteps(mean, edges),
+            "min_gteps": float(g.min()), "max_gteps": float(g.max()), "runs_per_root": int(steps)}
+
+
 def harmonic_gteps(times_s, edges):
     """k / sum(1 / GTEPS_i), GTEPS_i = (edges_i / 2) / t_i / 1e9."""
     inv = [t / (e / 2.0 / 1e9) for t, e in zip(times_s, edges)]
@@ -579,6 +591,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
+        "per_root": per_root_summary(times, edges, args.steps),
     }
 
     # every fixed variant on the same roots (the "best fixed kernel" comparison)

@@ -72,3 +72,15 @@ def test_traffic_lookup_requires_current_kernel_source(tmp_path, monkeypatch):
     assert bench.traffic_for("absent") is None
     (src_dir / "bfs_kernels.cu").write_text("// kernels v2\n")  # the kernel changed: the capture is stale
     assert bench.traffic_for("pull") is None
+
+
+def test_per_root_summary():
+    # two roots, three steps: root 0 takes 1, 1, 4 s; root 1 takes 2, 2, 2 s
+    times = [1.0, 2.0, 1.0, 2.0, 4.0, 2.0]
+    edges = [2e9, 4e9]  # 1e9 and 2e9 traversed edges
+    s = bench.per_root_summary(times, edges, 3)
+    # medians 1 s and 2 s: 1 GTEPS each; means 2 s and 2 s: 0.5 and 1 GTEPS
+    assert s["harmonic_gteps_of_medians"] == pytest.approx(1.0)
+    assert s["harmonic_gteps_of_means"] == pytest.approx(2 / (1 / 0.5 + 1 / 1.0))
+    assert s["min_gteps"] == pytest.approx(1.0) and s["max_gteps"] == pytest.approx(1.0)
+    assert s["runs_per_root"] == 3
