@@ -1,8 +1,12 @@
 """Host-side arithmetic of bench.py, on CPU: the per-level algorithmic bytes
 behind the reported roofline (checked against a plain vertex-by-vertex count),
-the harmonic-mean GTEPS and the traffic lookup's staleness rule."""
+the harmonic-mean GTEPS, the per-root summary, the traffic lookup's staleness
+rule, and the reference arm end to end at a small scale."""
 import hashlib
 import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -84,3 +88,19 @@ def test_per_root_summary():
     assert s["harmonic_gteps_of_means"] == pytest.approx(2 / (1 / 0.5 + 1 / 1.0))
     assert s["min_gteps"] == pytest.approx(1.0) and s["max_gteps"] == pytest.approx(1.0)
     assert s["runs_per_root"] == 3
+
+
+def test_reference_arm_runs_and_prints_one_line():
+    """`bench.py --impl reference` (the oracle timed on the host) at a small
+    scale: one JSON line with the contract's keys."""
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--scale", "10", "--edge-factor", "8", "--roots", "4"],
+                       capture_output=True, text=True, timeout=300, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "GTEPS"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
