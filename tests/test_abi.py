@@ -132,3 +132,19 @@ def test_serve_and_batch_argument_checks(lib):
     bc = bfs._BatchConfig(push_mode=2, alpha=8, grid_blocks=0)
     assert lib.bfs_batch_set_config(None, ctypes.byref(bc)) == bfs.BFS_ERR_INVALID_ARG
     assert lib.bfs_run_batch(None, None, 1, None, None, None) == bfs.BFS_ERR_INVALID_ARG
+
+
+def test_no_cpu_fallback_without_the_library(tmp_path, monkeypatch):
+    """Without libbfs.so the binding raises on first use: nothing on the path
+    falls back to a CPU implementation."""
+    import numpy as np
+    monkeypatch.setattr(bfs, "LIB_PATH", str(tmp_path / "absent" / "libbfs.so"))
+    monkeypatch.setattr(bfs, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        bfs.lib()
+    off = np.array([0, 1, 2], np.int32)
+    idx = np.array([1, 0], np.int32)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        bfs.bfs_graph_create(off, idx)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        bfs.bfs_run_ex(1, 0, np.zeros(2, np.int32), depth_on_host=True)
