@@ -332,18 +332,17 @@ def bench_batch_graphs(bfs, torch):
     factor 8-32, seeded): each graph's 64 roots in one launch, the 32 launches
     spread over 8 streams; against the same 2048 roots as single-source runs."""
     import graphgen as gg
-    rng = np.random.default_rng(6000)
-    specs = [(int(rng.integers(12, 21)), int(rng.choice([8, 16, 32]))) for _ in range(32)]
+    specs = gg.rmat_batch_specs()
     streams = [torch.cuda.Stream() for _ in range(8)]
     main = torch.cuda.current_stream()
     Gs, roots, outs, tuned = [], [], [], 0
     edges_total = 0
     try:
-        for i, (sc, ef) in enumerate(specs):
-            g = gg.rmat(sc, ef, seed=6000 + i)
+        for sc, ef, gseed, rseed in specs:
+            g = gg.rmat(sc, ef, seed=gseed)
             G = bfs.Graph(g.off, g.idx)
             Gs.append(G)
-            r = gg.sample_roots(g, 64, seed=6100 + i, giant=True)
+            r = gg.sample_roots(g, 64, seed=rseed, giant=True)
             roots.append(r)
             out = torch.empty(64 * g.n, dtype=torch.int32, device="cuda")
             outs.append(out)
@@ -383,7 +382,7 @@ def bench_batch_graphs(bfs, torch):
             G.close()
     return {"workload": "32 R-MAT graphs (a/b/c/d .57/.19/.19/.05), scale 12-20 and edge factor 8-32 drawn with "
                         "seed 6000, 64 giant-component roots each; one multi-source launch per graph, 8 streams",
-            "scales": [sc for sc, _ in specs], "edge_factors": [ef for _, ef in specs],
+            "scales": [sp[0] for sp in specs], "edge_factors": [sp[1] for sp in specs],
             "gteps": edges_total / 2 / t / 1e9, "ms_per_batch": t * 1e3,
             "single_source_gteps": edges_total / 2 / ts / 1e9, "speedup_vs_single": ts / t,
             "tuned_graphs": tuned}
@@ -436,11 +435,7 @@ def bench_serve(bfs, torch, args):
     """Serving: 8 resident graphs, Poisson arrivals of single-root queries (graph
     uniform, root uniform over vertices of nonzero degree), continuous batching."""
     import graphgen as gg
-    specs = [("rmat16", lambda: gg.rmat(16, 16, seed=5016)), ("rmat18", lambda: gg.rmat(18, 16, seed=5018)),
-             ("rmat20", lambda: gg.rmat(20, 16, seed=5020)), ("rmat22", lambda: gg.rmat(22, 16, seed=5022)),
-             ("rmat24", lambda: gg.rmat(24, 16, seed=5024)), ("grid2048", lambda: gg.grid(2048, 2048, 0.1, seed=5025)),
-             ("grid4096", lambda: gg.grid(4096, 4096, 0.1, seed=5026)),
-             ("er21", lambda: gg.erdos_renyi(1 << 21, 16.0, seed=5027))]
+    specs = gg.serve_graph_specs()
     Gs, cand = [], []
     for name, mk in specs:
         g = mk()

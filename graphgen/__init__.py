@@ -193,3 +193,24 @@ def grid_4096_permuted(seed: int = SEED_GRAPH + 2) -> Graph:
 def er_2p22_d8(seed: int = SEED_GRAPH + 3) -> Graph:
     """Erdos-Renyi with 2^22 vertices and average degree 8."""
     return erdos_renyi(1 << 22, 8.0, seed=seed)
+
+
+def rmat_batch_specs(count: int = 32, seed: int = 6000):
+    """The batch of uneven R-MAT graphs: `count` (scale, edge factor, graph
+    seed, root seed) tuples, scale drawn from 12-20 and edge factor from
+    {8, 16, 32} with a seeded generator; graph i is rmat(scale, ef,
+    seed=seed + i) with 64 giant-component roots drawn with seed + 100 + i."""
+    rng = np.random.default_rng(seed)
+    specs = [(int(rng.integers(12, 21)), int(rng.choice([8, 16, 32]))) for _ in range(count)]
+    return [(sc, ef, seed + i, seed + 100 + i) for i, (sc, ef) in enumerate(specs)]
+
+
+def serve_graph_specs():
+    """The eight graphs the query server holds resident: (name, maker) pairs.
+    R-MAT scale 16/18/20/22/24 at edge factor 16, 2048^2 and 4096^2 permuted
+    grids with 10% of edges dropped, Erdos-Renyi 2^21 with average degree 16."""
+    return [("rmat16", lambda: rmat(16, 16, seed=5016)), ("rmat18", lambda: rmat(18, 16, seed=5018)),
+            ("rmat20", lambda: rmat(20, 16, seed=5020)), ("rmat22", lambda: rmat(22, 16, seed=5022)),
+            ("rmat24", lambda: rmat(24, 16, seed=5024)), ("grid2048", lambda: grid(2048, 2048, 0.1, seed=5025)),
+            ("grid4096", lambda: grid(4096, 4096, 0.1, seed=5026)),
+            ("er21", lambda: erdos_renyi(1 << 21, 16.0, seed=5027))]

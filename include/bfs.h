@@ -251,9 +251,14 @@ int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* dept
  * Limit: n <= 1,048,576 vertices; larger n returns BFS_ERR_INVALID_ARG. The
  * traversal's scratch (two frontier queues, the visited bitmap, counters) is a
  * fixed device array of about 8.1 MB inside the library, held by every GPU that
- * loads the library until the process exits. The first call on each device
- * looks up that array's device address (cudaGetSymbolAddress) with the device
- * current; make that first call before any stream capture. All calls share
+ * loads the library until the process exits. Every call looks up that array's
+ * device address in the current device's context (cudaGetSymbolAddress, which
+ * allocates nothing), so a device reset between calls leaves no stale address;
+ * the first call on a device also loads the library's kernels there, so make
+ * that first call before any stream capture. `stream` must belong to the
+ * current device (BFS_ERR_INVALID_ARG otherwise); NULL is the legacy default
+ * stream. A launch that fails returns BFS_ERR_CUDA with the CUDA error text in
+ * bfs_last_error_detail(). All calls share
  * the one array, which keeps the previous call's contents (each call clears
  * what it reads first): calls whose work overlaps on the GPU, from any stream
  * or thread, race and corrupt each other, so serialise them. The CSR is
@@ -317,6 +322,11 @@ int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id);
  * one query's persistent grid, and *merges, 1 when its queued queries may be
  * merged into waves under merge_policy 0. BFS_ERR_NOT_FOUND for an unknown id. */
 int bfs_serve_graph_shape(bfs_server_t s, int32_t graph_id, int32_t* query_blocks, int32_t* merges);
+/* Device bytes a single query of the graph is charged against mem_budget_bytes
+ * when it is admitted (its traversal workspace, plus an n-entry depth buffer
+ * when with_output is 0, i.e. when the caller passes no depth_out).
+ * BFS_ERR_NOT_FOUND for an unknown id. */
+int bfs_serve_query_bytes(bfs_server_t s, int32_t graph_id, int32_t with_output, int64_t* bytes);
 /* Queue a query; non-blocking. depth_out: device, n int32, or NULL (the server
  * supplies a buffer and the depths are not returned). The server's streams do
  * not wait on the caller's streams: depth_out must be ready to be written when
@@ -374,6 +384,23 @@ int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advanc
  * paths without exhausting a shared GPU.
  */
 int bfs_debug_fail_alloc_after(int n);
+
+/*
+ * Test hook: make one bounded device-side wait of the next persistent
+ * traversal (bfs_run / bfs_run_ex in the persistent driver) or multi-source
+ * wave (bfs_run_batch) launched by this process run out, so that tests can
+ * check the timeout path without hanging or faulting a GPU. mode 1: the
+ * launch's first grid barrier expects one arrival more than the grid has;
+ * mode 2: the first level-ending barrier of a traversal, likewise; mode 3: the
+ * first adjacency copy staged by the CTA push expects 16 bytes more than it
+ * copies (a level the CTA push expands with a list of 512 entries or more).
+ * Every wait of the library is bounded (about 2 s), so the kernel gives up,
+ * records BFS_ERR_TIMEOUT in its status word (bfs_run_ex with stats, or
+ * bfs_run_batch with edges_out, returns it) and exits; the next launch on the
+ * same graph resets that state and runs normally. The hook is taken by the
+ * first launch that reads it; mode 0 clears it. Errors: BFS_ERR_INVALID_ARG.
+ */
+int bfs_debug_stall_next_launch(int mode);
 
 #ifdef __cplusplus
 }

@@ -145,12 +145,14 @@ def lib():
             "bfs_profile_levels": (ctypes.c_int, [vp, c_i32, c_i32, c_i32, vp, ctypes.POINTER(_LevelProfile), c_i32,
                                                   ctypes.POINTER(c_i32)]),
             "bfs_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int]),
+            "bfs_debug_stall_next_launch": (ctypes.c_int, [ctypes.c_int]),
             "bfs_run_static": (ctypes.c_int, [vp, vp, c_i64, c_i64, c_i32, vp, vp]),
             "bfs_batch_set_config": (ctypes.c_int, [vp, ctypes.POINTER(_BatchConfig)]),
             "bfs_batch_tune": (ctypes.c_int, [vp, vp, c_i32, vp, vp, ctypes.POINTER(_BatchConfig)]),
             "bfs_serve_create": (ctypes.c_int, [ctypes.POINTER(_ServeConfig), ctypes.POINTER(vp)]),
             "bfs_serve_add_graph": (ctypes.c_int, [vp, vp, ctypes.POINTER(c_i32)]),
             "bfs_serve_graph_shape": (ctypes.c_int, [vp, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
+            "bfs_serve_query_bytes": (ctypes.c_int, [vp, c_i32, c_i32, ctypes.POINTER(c_i64)]),
             "bfs_serve_reset_stats": (ctypes.c_int, [vp]),
             "bfs_serve_cancel_queued": (ctypes.c_int, [vp, ctypes.POINTER(c_i64)]),
             "bfs_serve_submit": (ctypes.c_int, [vp, c_i32, c_i32, vp, ctypes.POINTER(ctypes.c_uint64)]),
@@ -339,6 +341,14 @@ def bfs_profile_levels(g: int, root: int, reps: int = 5, advance_variant: int = 
     return feats, ms, tv
 
 
+def bfs_debug_stall_next_launch(mode: int) -> None:
+    """Test hook: the next persistent traversal or multi-source wave lets one
+    bounded device wait run out (1 first grid barrier, 2 first level barrier,
+    3 first staged copy of the CTA push; 0 clears), so the run reports
+    BFS_ERR_TIMEOUT after about 2 s instead of finishing."""
+    _check(lib().bfs_debug_stall_next_launch(int(mode)), "bfs_debug_stall_next_launch")
+
+
 def bfs_run_static(row_offsets, col_indices, root: int, depth_out, stream=None) -> None:
     """BFS that allocates nothing, for callers that cannot allocate device memory
     while they run. All three arrays are CUDA int32 tensors the caller owns; the
@@ -379,6 +389,14 @@ def bfs_serve_graph_shape(s: int, graph_id: int) -> dict:
     b, m = ctypes.c_int32(0), ctypes.c_int32(0)
     _check(lib().bfs_serve_graph_shape(s, int(graph_id), ctypes.byref(b), ctypes.byref(m)), "bfs_serve_graph_shape")
     return {"query_blocks": b.value, "merges": bool(m.value)}
+
+
+def bfs_serve_query_bytes(s: int, graph_id: int, with_output: bool = False) -> int:
+    """Device bytes one query of the graph is charged against the memory budget."""
+    b = ctypes.c_int64()
+    _check(lib().bfs_serve_query_bytes(s, int(graph_id), int(bool(with_output)), ctypes.byref(b)),
+           "bfs_serve_query_bytes")
+    return int(b.value)
 
 
 def bfs_serve_submit(s: int, graph_id: int, root: int, depth_out=None) -> int:

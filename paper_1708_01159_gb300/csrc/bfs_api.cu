@@ -57,6 +57,11 @@ int fail(int code, const char* fmt, ...) {
 // exercise the out-of-memory paths without exhausting a shared GPU.
 std::atomic<int> g_fail_alloc_countdown{0};
 
+// Test hook: the bounded wait (enum Stall) the next persistent traversal or
+// multi-source wave makes run out; taken by the first launch that reads it.
+std::atomic<int> g_stall_next{0};
+int take_stall() { return g_stall_next.exchange(0); }
+
 int dmalloc(void** p, size_t bytes) {
   int c = g_fail_alloc_countdown.load();
   if (c > 0 && g_fail_alloc_countdown.fetch_sub(1) == 1) {
@@ -608,7 +613,8 @@ int launch_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth,
   int32_t nodes = g->tree_nodes;
   const QsTree* qs = g->tree_qs;
   uint32_t epoch = ++ws->epoch;  // runs on one workspace are ordered, so consecutive launches differ
-  void* args[] = {&dg, &b, &st, &depth, &root, &forced, &tree, &nodes, &qs, &epoch};
+  int32_t stall = take_stall();
+  void* args[] = {&dg, &b, &st, &depth, &root, &forced, &tree, &nodes, &qs, &epoch, &stall};
   const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->shapes.persist) : g->shapes.persist;
   CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_bfs_persistent), dim3(grid), dim3(kThreads), args, 0,
                                  stream));
@@ -741,7 +747,8 @@ int ms_launch_wave(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth
   DevGraph dg = g->dg;
   MsBuffers mb = g->ms;
   MsState* st = g->ms_state;
-  void* args[] = {&dg, &mb, &st, &k, &depth_out, &cfg};
+  int32_t stall = take_stall();
+  void* args[] = {&dg, &mb, &st, &k, &depth_out, &cfg, &stall};
   const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->ms_grid) : g->ms_grid;
   CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_msbfs), dim3(grid), dim3(kMsThreads), args, 0, s));
   return BFS_OK;
@@ -828,6 +835,12 @@ int bfs_version(void) { return 100; }
 // allocation from now fail with BFS_ERR_OOM; 0 disables.
 int bfs_debug_fail_alloc_after(int n) {
   g_fail_alloc_countdown.store(n < 0 ? 0 : n);
+  return BFS_OK;
+}
+
+int bfs_debug_stall_next_launch(int mode) {
+  if (mode < STALL_NONE || mode > STALL_BULK_COPY) return fail(BFS_ERR_INVALID_ARG, "stall mode %d", mode);
+  g_stall_next.store(mode);
   return BFS_OK;
 }
 

@@ -54,6 +54,15 @@ enum Feature : int32_t {
 
 enum Status : int32_t { ST_OK = 0, ST_TIMEOUT = 5 };
 
+// Test hook (bfs_debug_stall_next_launch): which bounded wait of the next
+// persistent traversal or multi-source wave is made to run out.
+enum Stall : int32_t {
+  STALL_NONE = 0,
+  STALL_GRID_BARRIER = 1,   // the first grid barrier expects one arrival more than the grid has
+  STALL_LEVEL_BARRIER = 2,  // the first level-ending barrier of a traversal, likewise
+  STALL_BULK_COPY = 3,      // the first staged adjacency copy of the CTA push expects 16 bytes more than it copies
+};
+
 // Section 4.1: an unknown prediction at the first level falls back to the
 // edge list implementation (the edge-centric push here).
 constexpr int32_t kLevel0Default = V_PUSH_EDGE;
@@ -335,13 +344,18 @@ __device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, un
   return old;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen_word, int32_t* status) {
+// `extra` (0 in normal operation) makes the barrier wait for that many
+// arrivals more than the grid has: the test hook that lets a test run a
+// bounded wait out (the last arrival never comes, every block's wait ends at
+// the limit and the status word reports it).
+__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen_word, int32_t* status,
+                                             unsigned int extra = 0u) {
   __syncthreads();
   bool ok = true;
   if (threadIdx.x == 0) {
     const unsigned int gen = ld_acquire_u32(gen_word);
     const unsigned int arrived = atom_add_acq_rel_u32(count, 1u);
-    if (arrived == gridDim.x - 1) {
+    if (arrived == gridDim.x - 1 + extra) {
       *count = 0;
       st_release_u32(gen_word, gen + 1u);
     } else {
@@ -379,7 +393,8 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 // (both below 2^31: f <= n and e <= m). Bounded like grid_barrier.
 __device__ __forceinline__ bool level_barrier(unsigned int* count, unsigned long long* word, int32_t* status,
                                               const unsigned int* next_f, const unsigned long long* next_e,
-                                              unsigned int* f_out, unsigned long long* e_out) {
+                                              unsigned int* f_out, unsigned long long* e_out,
+                                              unsigned int extra = 0u) {
   __shared__ unsigned long long s_word;
   constexpr unsigned long long kMask31 = (1ull << 31) - 1ull;
   __syncthreads();
@@ -389,7 +404,7 @@ __device__ __forceinline__ bool level_barrier(unsigned int* count, unsigned long
     const unsigned long long phase = w0 >> 63;
     const unsigned int arrived = atom_add_acq_rel_u32(count, 1u);
     unsigned long long w = w0;
-    if (arrived == gridDim.x - 1) {
+    if (arrived == gridDim.x - 1 + extra) {
       *count = 0;
       const unsigned long long f = *reinterpret_cast<const volatile unsigned int*>(next_f);
       const unsigned long long e = *reinterpret_cast<const volatile unsigned long long*>(next_e);

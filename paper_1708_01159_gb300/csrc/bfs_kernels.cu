@@ -402,6 +402,7 @@ struct CtaPipe {
   int32_t* chunk;  // 2 x kCtaChunk entries of shared memory
   uint64_t* bar;   // 2 mbarriers, initialised once per block
   uint32_t parity0, parity1;
+  uint32_t extra_tx;  // test hook: bytes the next copy's barrier expects beyond the copy (0 normally)
 };
 
 __device__ __forceinline__ void cta_pipe_init(uint64_t* bar) {
@@ -446,7 +447,8 @@ __device__ bool body_push_cta(const DevGraph& g, const Level& lv, const Stage& s
       const int32_t cb = abeg + c * kCtaChunk;
       const uint32_t bytes = (uint32_t)min(kCtaChunk, aend - cb) * 4u;
       uint64_t* br = &pp.bar[c & 1];
-      mbar_expect_tx(br, bytes);
+      mbar_expect_tx(br, bytes + pp.extra_tx);
+      pp.extra_tx = 0;
       bulk_g2s(pp.chunk + (c & 1) * kCtaChunk, g.idx + cb, bytes, br);
     };
     if (tid == 0) {
@@ -986,7 +988,7 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
   BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(b, st);
   cta_pipe_init(bar);
-  CtaPipe pp{chunk, bar, 0u, 0u};
+  CtaPipe pp{chunk, bar, 0u, 0u, 0u};
   unsigned long long edges = 0;
   body_push_cta(g, lv, stage, pp, &st->status, edges);
   stage_flush(stage, lv, 1);
@@ -1094,9 +1096,11 @@ __global__ void k_undo_level(Buffers b, RunState* st) {
 // (which a failed run may leave set) and then publishes epoch; every other
 // block waits for it before its first barrier, so no separate reset launch is
 // needed.
+// stall: STALL_NONE, or the test hook's choice of one bounded wait to run out.
 __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth,
                                                              int32_t root, int32_t forced, const TreeNode* tree,
-                                                             int32_t tree_nodes, const QsTree* qs, uint32_t epoch) {
+                                                             int32_t tree_nodes, const QsTree* qs, uint32_t epoch,
+                                                             int32_t stall) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->bar_count = 0;
     st->status = ST_OK;
@@ -1134,7 +1138,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     b.q[0][0] = root;
   }
   cta_pipe_init(bar);
-  CtaPipe pp{ubuf, bar, 0u, 0u};
+  CtaPipe pp{ubuf, bar, 0u, 0u, stall == STALL_BULK_COPY ? 16u : 0u};
   // the previous run's barrier state is cleared before any block arrives
   if (blockIdx.x != 0 && threadIdx.x == 0) {
     const unsigned long long t0 = global_ns();
@@ -1148,7 +1152,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   // level 0's frontier is the root; later levels' f and e arrive with the barrier
   unsigned int f = 1;
   unsigned long long e = (unsigned long long)(g.off[root + 1] - g.off[root]);
-  bool ok = grid_sync(st);
+  bool ok = grid_barrier(&st->bar_count, &st->bar_gen, &st->status, stall == STALL_GRID_BARRIER ? 1u : 0u);
   for (; ok; ++L) {
     discovered += f;
     reached += (long long)e;
@@ -1211,7 +1215,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     if (v == V_PULL) vsel ^= 1u;
     prev = v;
     ok = level_barrier(&st->bar_count, &st->lvl_word, &st->status, &st->cnt3[(L + 1) % 3], &st->edg3[(L + 1) % 3],
-                       &f, &e);
+                       &f, &e, (stall == STALL_LEVEL_BARRIER && L == 0) ? 1u : 0u);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->levels = L;

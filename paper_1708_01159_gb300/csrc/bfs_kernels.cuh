@@ -32,7 +32,8 @@ __global__ void k_rev_edge_list(DevGraph g, Buffers b, RunState* st);
 __global__ void k_build_origin(const int32_t* off, int32_t n, int32_t* origin);
 __global__ void k_undo_level(Buffers b, RunState* st);
 __global__ void k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root, int32_t forced,
-                                 const TreeNode* tree, int32_t tree_nodes, const QsTree* qs, uint32_t epoch);
+                                 const TreeNode* tree, int32_t tree_nodes, const QsTree* qs, uint32_t epoch,
+                                 int32_t stall);
 
 // graph creation
 __global__ void k_validate(const int32_t* off, const int32_t* idx, int32_t n, int32_t m, int32_t* bad);

@@ -49,7 +49,7 @@ __device__ __forceinline__ void ms_depth_rows(int32_t* depth, int64_t n, int64_t
 }  // namespace
 
 __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, MsState* st, int32_t k,
-                                                       int32_t* depth, MsConfig cfg) {
+                                                       int32_t* depth, MsConfig cfg, int32_t stall) {
   __shared__ unsigned long long s_edges[64];
   __shared__ int32_t s_big[kMsThreads];
   __shared__ int s_nbig;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
   } else {
     for (int64_t i = tid; i < total; i += stride) depth[i] = -1;
   }
-  if (!grid_barrier(&st->bar_count, &st->bar_gen, &st->status)) return;
+  if (!grid_barrier(&st->bar_count, &st->bar_gen, &st->status, stall == STALL_GRID_BARRIER ? 1u : 0u)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // roots: the level 0 frontier; a vertex repeated as several roots carries several bits
     unsigned int fc = 0;

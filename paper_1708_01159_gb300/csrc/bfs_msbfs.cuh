@@ -32,7 +32,10 @@ struct MsConfig {
   int32_t alpha;      // a level pulls when its frontier edges x alpha exceed m
 };
 
-__global__ void k_msbfs(DevGraph g, MsBuffers mb, MsState* st, int32_t k, int32_t* depth, MsConfig cfg);
+// stall: STALL_GRID_BARRIER makes the first grid barrier wait for an arrival
+// that never comes (test hook); STALL_NONE otherwise.
+__global__ void k_msbfs(DevGraph g, MsBuffers mb, MsState* st, int32_t k, int32_t* depth, MsConfig cfg,
+                        int32_t stall);
 __global__ void k_ms_reset(MsState* st);
 
 }  // namespace bfs

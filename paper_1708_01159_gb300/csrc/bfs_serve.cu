@@ -510,6 +510,17 @@ int bfs_serve_graph_shape(bfs_server_t s, int32_t graph_id, int32_t* query_block
   return BFS_OK;
 }
 
+int bfs_serve_query_bytes(bfs_server_t s, int32_t graph_id, int32_t with_output, int64_t* bytes) {
+  if (!s || !bytes) return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size())
+    return bfs::set_error_detail(BFS_ERR_NOT_FOUND, "unknown graph id");
+  static int32_t dummy;
+  const Request r{0, graph_id, 0, with_output ? &dummy : nullptr, Clock::now()};
+  *bytes = unit_bytes(s, r, 1);
+  return BFS_OK;
+}
+
 int bfs_serve_submit(bfs_server_t s, int32_t graph_id, int32_t root, int32_t* depth_out, uint64_t* ticket) {
   if (!s || !ticket) return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "null argument");
   std::lock_guard<std::mutex> lk(s->mu);

@@ -13,7 +13,7 @@
 // library, reading its queues and counters from that array. The level loop is
 // driven from the host, one small device-to-host read of the next frontier
 // size per level.
-#include <mutex>
+#include <cstdio>
 
 #include "bfs.h"
 #include "bfs_internal.cuh"
@@ -90,12 +90,25 @@ __global__ void __launch_bounds__(kStaticThreads)
   }
 }
 
-std::mutex g_static_mu;
-StaticScratch* g_static_ptr[64] = {};  // device address of the array, per device ordinal
-
 int static_fail(int code, const char* msg) { return bfs::set_error_detail(code, msg); }
 
+// A launch that could not start (a stream of another device, say) reports its
+// CUDA error string instead of surfacing later as a failed copy.
+int launch_status(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return BFS_OK;
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s launch: %s", what, cudaGetErrorString(e));
+  return static_fail(BFS_ERR_CUDA, buf);
+}
+
 }  // namespace
+
+#define TRY_LAUNCH(what)                     \
+  do {                                       \
+    const int r_ = launch_status(what);      \
+    if (r_ != BFS_OK) return r_;             \
+  } while (0)
 
 extern "C" {
 
@@ -109,34 +122,43 @@ int bfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int64
   if (root < 0 || root >= n) return static_fail(BFS_ERR_INVALID_ARG, "root not in [0, n)");
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-    return static_fail(BFS_ERR_CUDA, "cudaGetDevice failed");
-  StaticScratch* s = nullptr;
-  {
-    // set-up, once per device, with that device current: the array's device address
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-      if (e != cudaSuccess || !p) return static_fail(BFS_ERR_CUDA, "cudaGetSymbolAddress failed");
-      g_static_ptr[dev] = static_cast<StaticScratch*>(p);
+  if (cudaGetDevice(&dev) != cudaSuccess) return static_fail(BFS_ERR_CUDA, "cudaGetDevice failed");
+  if (stream) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(stream, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return static_fail(BFS_ERR_INVALID_ARG, "stream is not a valid CUDA stream");
     }
-    s = g_static_ptr[dev];
+    if (sdev != dev) return static_fail(BFS_ERR_INVALID_ARG, "stream belongs to another device than the current one");
   }
+  // The array's device address in the current device's context, looked up on
+  // every call (the lookup allocates nothing), so a device reset between calls
+  // never leaves a stale address behind; in host code the array's name is only
+  // a host-side stand-in and must not be passed to a kernel.
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+    cudaGetLastError();
+    return static_fail(BFS_ERR_CUDA, "cudaGetSymbolAddress failed");
+  }
+  StaticScratch* s = static_cast<StaticScratch*>(p);
   const int32_t nn = (int32_t)n, mm = (int32_t)m;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
   const int grid = sms * 4;
   k_static_clear_flag<<<1, 1, 0, stream>>>(s);
+  TRY_LAUNCH("clear");
   k_static_validate<<<grid, kStaticThreads, 0, stream>>>(s, row_offsets, col_indices, nn, mm);
+  TRY_LAUNCH("validate");
   int32_t bad = 0;
   if (cudaMemcpyAsync(&bad, &s->bad, sizeof bad, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
       cudaStreamSynchronize(stream) != cudaSuccess)
     return static_fail(BFS_ERR_CUDA, "validation failed to run");
   if (bad) return static_fail(BFS_ERR_BAD_GRAPH, "CSR failed validation");
   k_static_init<<<grid, kStaticThreads, 0, stream>>>(s, nn, root, depth_out);
+  TRY_LAUNCH("init");
   for (int32_t L = 0; L <= nn; ++L) {
     k_static_level<<<grid, kStaticThreads, 0, stream>>>(s, row_offsets, col_indices, depth_out, L);
+    TRY_LAUNCH("level");
     unsigned int next = 0;
     if (cudaMemcpyAsync(&next, &s->count[(L + 1) % 3], sizeof next, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
         cudaStreamSynchronize(stream) != cudaSuccess)

@@ -148,3 +148,9 @@ def test_no_cpu_fallback_without_the_library(tmp_path, monkeypatch):
         bfs.bfs_graph_create(off, idx)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         bfs.bfs_run_ex(1, 0, np.zeros(2, np.int32), depth_on_host=True)
+
+
+def test_stall_hook_modes_checked_on_the_host(lib):
+    assert lib.bfs_debug_stall_next_launch(4) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_debug_stall_next_launch(-1) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_debug_stall_next_launch(0) == bfs.BFS_OK

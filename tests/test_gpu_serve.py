@@ -76,11 +76,21 @@ def test_mixed_results_equal_alone(graphs, merge, policy):
 
 
 def test_memory_budget_admission(graphs):
+    """Admission by memory: with a budget that fits two of the largest queries at
+    once, the memory held by admitted queries never exceeds it, although the
+    slot limit alone would admit eight."""
     gs, Gs = graphs
-    # a budget that fits one query of the largest graph at a time
-    s = bfs.bfs_serve_create(mem_budget_bytes=40 * gs[0].n, max_inflight=8, num_streams=4)
+    probe = bfs.bfs_serve_create(max_inflight=1, num_streams=1)
+    try:
+        need = [bfs.bfs_serve_query_bytes(probe, bfs.bfs_serve_add_graph(probe, G.handle)) for G in Gs]
+    finally:
+        bfs.bfs_serve_destroy(probe)
+    budget = 2 * max(need) + 1
+    s = bfs.bfs_serve_create(mem_budget_bytes=budget, max_inflight=8, num_streams=4)
     try:
         ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
+        assert [bfs.bfs_serve_query_bytes(s, i) for i in ids] == need
+        assert all(bfs.bfs_serve_query_bytes(s, i, with_output=True) < need[k] for k, i in enumerate(ids))
         tickets = []
         for q in range(40):
             gi = q % len(gs)
@@ -89,7 +99,10 @@ def test_memory_budget_admission(graphs):
             assert bfs.bfs_serve_wait(s, t) == bfs.BFS_OK
         st = bfs.bfs_serve_stats(s)
         assert st["completed"] == 40
-        assert 0 < st["peak_bytes_inflight"] <= 40 * gs[0].n or st["peak_bytes_inflight"] > 0
+        assert min(need) <= st["peak_bytes_inflight"] <= budget
+        with pytest.raises(bfs.BFSError) as e:
+            bfs.bfs_serve_query_bytes(s, len(ids))
+        assert e.value.code == bfs.BFS_ERR_NOT_FOUND
     finally:
         bfs.bfs_serve_destroy(s)
 

@@ -50,3 +50,62 @@ def test_run_static_rejects_sizes_beyond_its_limit():
     rc = L.bfs_run_static(off.data_ptr(), idx.data_ptr(), n, 0, 0, out.data_ptr(), None)
     assert rc == bfs.BFS_ERR_INVALID_ARG
     assert "1048576" in L.bfs_last_error_detail().decode()
+
+
+def _static(g, root):
+    off = torch.from_numpy(g.off).cuda()
+    idx = torch.from_numpy(g.idx if g.m else np.zeros(1, np.int32)).cuda()
+    out = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+    rc = bfs.lib().bfs_run_static(off.data_ptr(), idx.data_ptr(), g.n, g.m, int(root), out.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return rc, out.cpu().numpy()
+
+
+def test_run_static_against_the_oracle_at_the_size_limit_and_after_it():
+    """n = 1,048,576 exactly (a permuted 1024 x 1024 grid: the fixed queues at
+    capacity, hundreds of levels), then a scale-10 R-MAT graph: the second call
+    reuses the array the first one filled, and both equal the oracle."""
+    import oracle
+    bfs.build()
+    big = gg.grid(1024, 1024, 0.1, seed=77)
+    assert big.n == 1 << 20
+    small = gg.rmat(10, 16, seed=78)
+    for g, r in ((big, int(gg.sample_roots(big, 1, seed=79, giant=True)[0])),
+                 (small, int(gg.sample_roots(small, 1, seed=80)[0]))):
+        rc, got = _static(g, r)
+        assert rc == bfs.BFS_OK, bfs.lib().bfs_last_error_detail().decode()
+        assert np.array_equal(got, oracle.bfs(g.off, g.idx, r).depth)
+
+
+def test_run_static_directed_graph_and_isolated_root():
+    import oracle
+    bfs.build()
+    rng = np.random.default_rng(81)
+    n = 3000
+    g = gg.from_edges(n, rng.integers(0, n - 10, 9000), rng.integers(0, n - 10, 9000), symmetrize=False)
+    iso = n - 1  # no edges reach or leave the last vertices
+    for r in (int(gg.sample_roots(g, 1, seed=82)[0]), iso):
+        rc, got = _static(g, r)
+        assert rc == bfs.BFS_OK, bfs.lib().bfs_last_error_detail().decode()
+        assert np.array_equal(got, oracle.bfs(g.off, g.idx, r).depth)
+    rc, got = _static(g, iso)
+    assert got[iso] == 0 and (np.delete(got, iso) == -1).all()
+
+
+def test_run_static_rejects_a_malformed_csr_and_the_next_call_works():
+    import oracle
+    bfs.build()
+    g = gg.rmat(11, 8, seed=83)
+    bad_idx = g.idx.copy()
+    bad_idx[len(bad_idx) // 2] = g.n  # one index out of range
+    rc, _ = _static(gg.Graph(g.off, bad_idx), 0)
+    assert rc == bfs.BFS_ERR_BAD_GRAPH
+    bad_off = g.off.copy()
+    bad_off[5], bad_off[6] = bad_off[6], bad_off[5] - 1  # offsets decreasing
+    rc, _ = _static(gg.Graph(bad_off, g.idx), 0)
+    assert rc == bfs.BFS_ERR_BAD_GRAPH
+    r = int(gg.sample_roots(g, 1, seed=84)[0])
+    rc, got = _static(g, r)
+    assert rc == bfs.BFS_OK
+    assert np.array_equal(got, oracle.bfs(g.off, g.idx, r).depth)
