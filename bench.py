@@ -289,6 +289,42 @@ def bench_count_modes(bfs, torch, G, g, roots, edges, stream):
     return out
 
 
+def bench_c1(bfs, torch, stream, reps=5):
+    """R-MAT scale 14, edge factor 16, 16 seeded roots of nonzero degree, every
+    level run by the fixed one-thread-per-vertex push (the paper's vertex push):
+    the persistent driver (one launch per traversal) and the graph driver, CUDA
+    events per traversal, harmonic-mean GTEPS over the roots (median of `reps`
+    runs per root). The graph is about 2 MB, L2-resident: latency bound."""
+    import graphgen as gg
+    g = gg.rmat_s14_ef16()
+    roots = gg.sample_roots(g, 16, seed=gg.SEED_ROOTS)
+    out = {"workload": f"R-MAT scale 14 edge factor 16 ({g.n:,} vertices, {g.m:,} directed edges), 16 roots, "
+                       "push_thread forced"}
+    with bfs.Graph(g.off, g.idx) as G:
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        sts = [bfs.bfs_run_ex(G.handle, int(r), d, stream, forced_variant=0, stats=True, log_capacity=256)
+               for r in roots]
+        edges = [st["edges_reached"] for st in sts]
+        for name, mode in (("persistent", bfs.MODE_PERSISTENT), ("graph", bfs.MODE_GRAPH)):
+            bfs.bfs_run_ex(G.handle, int(roots[0]), d, stream, forced_variant=0, mode=mode)
+            torch.cuda.synchronize()
+            med = []
+            for r in roots:
+                ts = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    bfs.bfs_run_ex(G.handle, int(r), d, stream, forced_variant=0, mode=mode)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1) / 1e3)
+                med.append(float(np.median(ts)))
+            out[name] = {"gteps": harmonic_gteps(med, edges), "us_per_traversal": 1e6 * float(np.mean(med))}
+        out["levels"] = [st["levels"] for st in sts]
+        out["device_us"] = float(np.mean([st.get("device_ns", 0) for st in sts]) / 1e3)
+    return out
+
+
 def bench_batch(bfs, torch, stream):
     """Multi-source BFS: ER 2^22, average degree 8, 64 roots in one launch (tuned), against
     the same 64 roots as single-source switched traversals."""
@@ -449,7 +485,10 @@ def bench_serve(bfs, torch, args):
                      "once before the measured loads (fills the workspace and depth-buffer pools; not reported); "
                      "each load starts a new statistics window and ends by cancelling what is still queued after "
                      "the drain"}
-    s = bfs.bfs_serve_create(max_inflight=256, num_streams=256, queue_capacity=1 << 17, merge_batch=64)
+    budget = 40 << 30
+    out["mem_budget_bytes"] = budget
+    s = bfs.bfs_serve_create(mem_budget_bytes=budget, max_inflight=256, num_streams=256, queue_capacity=1 << 17,
+                             merge_batch=64)
     try:
         ids = [bfs.bfs_serve_add_graph(s, G.handle) for G in Gs]
         out["shapes"] = {name: bfs.bfs_serve_graph_shape(s, i) for (name, _), i in zip(specs, ids)}
@@ -705,6 +744,8 @@ def run_ours(args):
     G.close()
     del depth
     progress("switched, fixed, e2e and roofline done")
+    line["c1"] = bench_c1(bfs, torch, stream)
+    progress("C1 done")
     if not args.no_batch:
         line["batch"] = bench_batch(bfs, torch, stream)
         progress("batch (ER) done")

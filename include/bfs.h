@@ -138,6 +138,8 @@ typedef struct bfs_run_stats {
   int64_t* log_frontier_edges; /* host, sum of out-degrees over that frontier */
   int64_t* log_time_ns;      /* host, log_capacity + 1 entries: device %globaltimer (ns) at the start
                                 of level L, and entry [levels] at the end (graph and persistent drivers) */
+  int64_t start_ns;          /* device %globaltimer (ns) when the run's first kernel started, before the
+                                depth initialisation (same clock as log_time_ns) */
 } bfs_run_stats;
 
 /* Text of a status code (static storage). */
@@ -207,8 +209,10 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
  * host, k int32 (repeats allowed). depth_out: device, k * n int32, row-major
  * (row i for roots[i]), caller-owned. Roots are processed in waves of up to 64
  * by one persistent kernel per wave, one bit per root in 64-bit visited /
- * frontier masks per vertex (8 n bytes each, allocated on the first call and
- * kept with the graph); each level pushes or pulls for all roots at once.
+ * frontier masks per vertex, each level pushing or pulling for all roots at
+ * once; depths up to 13 are kept as 4-bit codes per vertex and root until the
+ * wave ends, when each output row is written once (76 n bytes of buffers in
+ * all, allocated on the first call and kept with the graph).
  * Batches on one graph are ordered after each other on the device.
  * edges_out: optional host array of k int64 reached-edge counts; when given,
  * the call synchronises `stream`. Errors as bfs_run.
@@ -273,12 +277,16 @@ int bfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int64
  * Serving: a request loop over graphs resident in HBM (the paper has no
  * serving layer; this wraps the Section 3.1 traversal for many concurrent
  * queries). A dispatcher thread admits submitted single-root queries whenever
- * an in-flight slot and the memory the query needs (its traversal workspace,
- * plus an n-entry depth buffer when the caller passes none) fit the budget,
- * first fit over the head of the queue; admitted queries run on a pool of
- * streams and overlap on the device; queued queries to the same graph are
- * merged into one multi-source wave (continuous batching). Results are the
- * same as alone: depths are exact.
+ * an in-flight slot and the memory the unit needs fit the budget, first fit
+ * over the head of the queue. A unit is one query's traversal (charged its
+ * workspace, plus an n-entry depth buffer when the caller passes none) or a
+ * multi-source wave merging up to merge_batch queued queries of one graph
+ * (charged one wave buffer set, 76 n bytes, plus a depth buffer per query
+ * without one): continuous batching. Units run on a pool of streams and overlap
+ * on the device; each wave root's depths go straight to its query's buffer.
+ * Results are the same as alone: depths are exact. Workspaces, depth buffers
+ * and wave sets are allocated when a graph is registered; the dispatcher
+ * allocates no device memory (a unit whose pool is empty waits).
  */
 typedef struct bfs_server* bfs_server_t;
 
@@ -309,14 +317,20 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out);
 /* Register a graph (same device; up to 256; the caller keeps it alive until
  * bfs_serve_destroy). Synchronous: probe runs on a private stream size the
  * graph's queries. Traversals from vertices 0, n/3, 2n/3 and n-1 pick the one
- * reaching the most edges; it is timed on 8, 16, 32, 64 blocks, one per SM and
- * a full occupancy wave, and queries get the count with the least blocks x time
- * among those at most 4x slower than the fastest. One 64-root multi-source wave
- * (roots the probe reached, on the wave grid of at most two blocks per SM that
- * merged queries run on; needs 256 n bytes of scratch, skipped if that does not
- * fit) decides whether queued queries are merged (merge_policy 0): when its
- * blocks x time per root is below a single query's. Takes a few traversals'
- * time, up to about a second on a high-diameter graph of 16M vertices. */
+ * reaching the most edges; it is timed on 8, 16, 32, 64 blocks, one and two
+ * per SM and a full occupancy wave, and queries get the count with the least
+ * blocks x time among those at most 4x slower than the fastest. One 64-root
+ * multi-source wave (roots the probe reached, on the wave grid of at most two
+ * blocks per SM that merged queries run on; needs 332 n bytes of temporary
+ * memory, skipped if that does not fit) decides whether queued queries are
+ * merged (merge_policy 0): when its blocks x time per root is below a single
+ * query's. Then the graph's pools are allocated: min(max_inflight, 16)
+ * traversal workspaces, and when its queries may merge (merge_batch > 1 and
+ * the probe or merge_policy 1 allows it) two wave buffer sets (76 n bytes
+ * each, so two waves of the graph can run at once), plus n-entry depth buffers
+ * for queries submitted without one (one per workspace and merge_batch per
+ * set). Takes a few traversals' time, up to a few seconds on a high-diameter
+ * graph of 16M vertices. BFS_ERR_OOM if the pools do not fit. */
 int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id);
 /* The launch shape registration chose for a graph: *query_blocks, the blocks of
  * one query's persistent grid, and *merges, 1 when its queued queries may be

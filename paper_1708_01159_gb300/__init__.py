@@ -83,7 +83,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("edges_reached", ctypes.c_int64), ("vertices_reached", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("status", ctypes.c_int32), ("log_capacity", ctypes.c_int32),
                 ("log_variant", ctypes.POINTER(ctypes.c_int32)), ("log_frontier", ctypes.POINTER(ctypes.c_int64)),
-                ("log_frontier_edges", ctypes.POINTER(ctypes.c_int64)), ("log_time_ns", ctypes.POINTER(ctypes.c_int64))]
+                ("log_frontier_edges", ctypes.POINTER(ctypes.c_int64)), ("log_time_ns", ctypes.POINTER(ctypes.c_int64)),
+                ("start_ns", ctypes.c_int64)]
 
 
 class _ServeConfig(ctypes.Structure):
@@ -292,6 +293,9 @@ def bfs_run_ex(g: int, root: int, depth_out, stream=None, forced_variant: int = 
         # per-level device time (ns) from the start stamps (graph and persistent drivers)
         if st.levels < log_capacity + 1 and mode != MODE_HOST_LOOP:
             out["level_ns"] = np.diff(logs[3][: st.levels + 1])
+            # from the first kernel's start to level 0 (depth init, first barrier), and to the end
+            out["init_ns"] = int(logs[3][0] - st.start_ns)
+            out["device_ns"] = int(logs[3][st.levels] - st.start_ns)
     return out
 
 

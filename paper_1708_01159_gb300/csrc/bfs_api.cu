@@ -196,6 +196,17 @@ struct Shapes {
 
 }  // namespace
 
+// One multi-source wave's buffers (bfs::MsSet, declared in bfs_internal.cuh):
+// the graph's own set serves bfs_run_batch; the query server holds more so that
+// several waves on one graph can run at once.
+struct bfs::MsSet {
+  MsBuffers mb{};
+  MsState* st = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after each wave run on the set
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+};
+
 struct bfs_graph {
   int device = 0;
   int sms = 0;
@@ -218,12 +229,9 @@ struct bfs_graph {
   bool has_origin = false;
   int32_t tree_nodes = 0;
   uint64_t tree_version = 0;
-  // multi-source buffers (allocated on the first batch; batches on one graph
-  // are ordered through ms_done)
-  MsBuffers ms{};
-  MsState* ms_state = nullptr;
-  int32_t* ms_roots = nullptr;
-  cudaEvent_t ms_done = nullptr;
+  // the graph's own multi-source buffer set (allocated on the first batch;
+  // bfs_run_batch and bfs_batch_tune waves on it are ordered through its event)
+  bfs::MsSet* ms_set = nullptr;
   std::mutex ms_mu;
   MsConfig ms_cfg{0, 16};
   int ms_grid = 0;       // one full occupancy wave of the multi-source kernel
@@ -295,7 +303,23 @@ int add_kernel(cudaGraph_t graph, cudaGraphNode_t* node, const cudaGraphNode_t* 
   return BFS_OK;
 }
 
-// Build the level loop of one workspace as a CUDA graph with conditional nodes.
+// The workspace's device state before its first run: the log buffers and, once
+// the level-loop graph exists, its conditional handles.
+int init_run_state(Workspace* ws, unsigned long long h_while, unsigned long long h_switch) {
+  RunState init{};
+  init.h_while = h_while;
+  init.h_switch = h_switch;
+  init.use_handles = h_while != 0;
+  init.log_cap = ws->log_cap;
+  init.log_variant = ws->log_variant;
+  init.log_frontier = ws->log_frontier;
+  init.log_edges = ws->log_edges;
+  init.log_time = ws->log_time;
+  return upload_now(ws->st, &init, sizeof init);
+}
+
+// Build the level loop of one workspace as a CUDA graph with conditional nodes
+// (on the workspace's first run in the graph driver).
 // The graph holds the level loop only: k_loop_start opens the WHILE loop on the
 // device, and per-run values (root, output, forced variant, tree) reach it
 // through RunState, written by a k_init launched on the same stream just
@@ -348,18 +372,8 @@ int build_graph(bfs_graph* g, Workspace* ws) {
   TRY(add_kernel(vb[V_REV_EDGE_LIST], &n0, nullptr, reinterpret_cast<const void*>(&k_rev_edge_list), s.edge_list,
                  kThreads, ka));
   CU(cudaGraphInstantiate(&ws->exec, ws->graph, 0));
-
   // the handles live in the device state, where decide sets them each level
-  RunState init{};
-  init.h_while = hw;
-  init.h_switch = hs;
-  init.use_handles = 1;
-  init.log_cap = ws->log_cap;
-  init.log_variant = ws->log_variant;
-  init.log_frontier = ws->log_frontier;
-  init.log_edges = ws->log_edges;
-  init.log_time = ws->log_time;
-  return upload_now(ws->st, &init, sizeof init);
+  return init_run_state(ws, hw, hs);
 }
 
 int create_workspace(bfs_graph* g, Workspace** out) {
@@ -388,12 +402,11 @@ int create_workspace(bfs_graph* g, Workspace** out) {
   ws->log_frontier = static_cast<long long*>(A(ws->log_cap * 8));
   ws->log_edges = static_cast<long long*>(A(ws->log_cap * 8));
   ws->log_time = static_cast<long long*>(A(ws->log_cap * 8));
-  ws->host_depth_stage = static_cast<int32_t*>(A(n * 4));
   if (r == BFS_OK) {
     cudaError_t e = cudaEventCreateWithFlags(&ws->done, cudaEventDisableTiming);
     if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
   }
-  if (r == BFS_OK) r = build_graph(g, ws);
+  if (r == BFS_OK) r = init_run_state(ws, 0, 0);
   if (r != BFS_OK) {
     free_workspace(ws);
     return r;
@@ -594,6 +607,12 @@ int ensure_origin(bfs_graph* g) {
 int launch_variant(bfs_graph* g, Workspace* ws, int v, cudaStream_t s, int32_t count_mode = CM_BLOCK);
 
 int launch_graph(bfs_graph* g, Workspace* ws, int32_t root, int32_t* depth, int32_t forced, cudaStream_t stream) {
+  if (!ws->exec) {
+    // first graph-driver run on this workspace: its previous runs (other
+    // drivers) finish before the state they use is rewritten
+    CU(cudaEventSynchronize(ws->done));
+    TRY(build_graph(g, ws));
+  }
   k_init<<<g->shapes.init, kThreads, 0, stream>>>(g->dg, ws->b, ws->st, depth, root, forced, g->tree, g->tree_nodes,
                                                   g->tree_qs, 1);
   CU(cudaGetLastError());
@@ -688,70 +707,52 @@ int check_graph(bfs_graph_t g) {
   return BFS_OK;
 }
 
-// Multi-source buffers: four masks of n x 8 bytes, the wave's roots and state.
-// Called with g->ms_mu held.
-int ms_prepare(bfs_graph* g) {
-  if (g->ms_state) return BFS_OK;
-  const size_t n = (size_t)g->dg.n;
-  constexpr int kBufs = 9;
-  void* p[kBufs] = {};
-  int r = BFS_OK;
-  // visit, front x 2, next, roots, state, frontier lists x 2, touched list
-  const size_t sizes[kBufs] = {n * 8, n * 8, n * 8, n * 8, 64 * 4, sizeof(MsState), n * 4, n * 4, n * 4};
-  for (int i = 0; i < kBufs && r == BFS_OK; ++i) r = dmalloc(&p[i], sizes[i]);
-  if (r == BFS_OK && cudaEventCreateWithFlags(&g->ms_done, cudaEventDisableTiming) != cudaSuccess)
-    r = fail(BFS_ERR_CUDA, "cudaEventCreate");
-  if (r == BFS_OK) {
-    MsState init{};
-    r = upload_now(p[5], &init, sizeof init);
+// Blocks of one full occupancy wave of the multi-source kernel (cooperative
+// launch required). Called with g->ms_mu held.
+int ms_grid_init(bfs_graph* g) {
+  if (g->ms_grid > 0) return BFS_OK;
+  int coop = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
+  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(&k_msbfs),
+                                                             kMsThreads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return fail(BFS_ERR_CUDA, "multi-source BFS needs cooperative launch");
   }
-  int per_sm = 0;
-  if (r == BFS_OK) {
-    int coop = 0;
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, g->device);
-    if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(&k_msbfs),
-                                                               kMsThreads, 0) != cudaSuccess || per_sm < 1)
-      r = fail(BFS_ERR_CUDA, "multi-source BFS needs cooperative launch");
-  }
-  if (r != BFS_OK) {
-    for (void* q : p)
-      if (q) cudaFree(q);
-    if (g->ms_done) cudaEventDestroy(g->ms_done);
-    g->ms_done = nullptr;
-    return r;
-  }
-  for (int i = 0; i < kBufs; ++i) {
-    g->allocs.push_back(p[i]);
-    g->bytes += sizes[i];
-  }
-  g->ms.visit = static_cast<unsigned long long*>(p[0]);
-  g->ms.front[0] = static_cast<unsigned long long*>(p[1]);
-  g->ms.front[1] = static_cast<unsigned long long*>(p[2]);
-  g->ms.next = static_cast<unsigned long long*>(p[3]);
-  g->ms.flist[0] = static_cast<int32_t*>(p[6]);
-  g->ms.flist[1] = static_cast<int32_t*>(p[7]);
-  g->ms.tlist = static_cast<int32_t*>(p[8]);
-  g->ms_roots = static_cast<int32_t*>(p[4]);
-  g->ms.roots = g->ms_roots;
-  g->ms_state = static_cast<MsState*>(p[5]);
   g->ms_grid = g->sms * std::min(per_sm, 8);
   return BFS_OK;
 }
 
-// One wave of up to 64 roots (host array) into k rows of depth_out.
-int ms_launch_wave(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t s, MsConfig cfg,
-                   int32_t grid_blocks = 0) {
-  CU(cudaMemcpyAsync(g->ms_roots, roots, (size_t)k * 4, cudaMemcpyHostToDevice, s));
-  k_ms_reset<<<1, 1, 0, s>>>(g->ms_state);
+// The graph's own set. Called with g->ms_mu held.
+int ms_prepare(bfs_graph* g) {
+  if (g->ms_set) return BFS_OK;
+  TRY(ms_grid_init(g));
+  return bfs::ms_set_create(g, &g->ms_set);
+}
+
+// One wave of up to 64 roots (host array) into the k output rows (host array
+// of device pointers) on the given set.
+int ms_launch_wave(bfs_graph* g, MsSet* set, const int32_t* roots, int32_t k, int32_t* const* rows_out,
+                   cudaStream_t s, MsConfig cfg, int32_t grid_blocks = 0) {
+  MsRows rows{};
+  for (int32_t i = 0; i < k; ++i) {
+    rows.row[i] = rows_out[i];
+    rows.root[i] = roots[i];
+  }
+  k_ms_reset<<<1, 1, 0, s>>>(set->st);
   CU(cudaGetLastError());
   DevGraph dg = g->dg;
-  MsBuffers mb = g->ms;
-  MsState* st = g->ms_state;
+  MsBuffers mb = set->mb;
+  MsState* st = set->st;
   int32_t stall = take_stall();
-  void* args[] = {&dg, &mb, &st, &k, &depth_out, &cfg, &stall};
+  void* args[] = {&dg, &mb, &st, &k, &rows, &cfg, &stall};
   const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->ms_grid) : g->ms_grid;
   CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_msbfs), dim3(grid), dim3(kMsThreads), args, 0, s));
   return BFS_OK;
+}
+
+// Row pointers of a k x n row-major block.
+void block_rows(int32_t* base, int64_t n, int32_t k, int32_t** rows) {
+  for (int32_t i = 0; i < k; ++i) rows[i] = base + (size_t)i * (size_t)n;
 }
 
 }  // namespace
@@ -760,8 +761,9 @@ int bfs::set_error_detail(int code, const char* msg) { return fail(code, "%s", m
 
 long long bfs::workspace_bytes(const bfs_graph* g) {
   const long long n = g->dg.n, words = g->dg.words;
-  // two queues, two bitmaps, edge-centric scan scratch, host-output stage, logs
-  return 4 * n * 2 + 4 * words * 2 + 4 * (n + 1) + 4 * n + 8 * ((n + kPeTile - 1) / kPeTile + 2) + 4 * n +
+  // two queues, two bitmaps, edge-centric scan scratch, logs (a host-output
+  // stage of 4 n bytes is added on a workspace's first host-output run)
+  return 4 * n * 2 + 4 * words * 2 + 4 * (n + 1) + 4 * n + 8 * ((n + kPeTile - 1) / kPeTile + 2) +
          20 * std::min<long long>(n + 1, 1 << 16) + (long long)sizeof(RunState);
 }
 
@@ -773,12 +775,24 @@ int32_t bfs::persistent_grid(const bfs_graph* g) { return g->shapes.persist; }
 
 int32_t bfs::wave_grid(bfs_graph* g) {
   std::lock_guard<std::mutex> lk(g->ms_mu);
-  if (ms_prepare(g) != BFS_OK) return 0;
+  if (ms_grid_init(g) != BFS_OK) return 0;
   return g->ms_grid;
 }
 
+int bfs::reserve_workspaces(bfs_graph* g, int32_t count) {
+  DeviceGuard dgd(g->device);
+  std::lock_guard<std::mutex> lk(g->mu);
+  while ((int32_t)g->pool.size() < std::min<int32_t>(count, kMaxWorkspaces)) {
+    Workspace* ws = nullptr;
+    TRY(create_workspace(g, &ws));
+    g->pool.push_back(ws);
+    g->idle.push_back(ws);
+  }
+  return BFS_OK;
+}
+
 int bfs::run_async(bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t stream, int32_t mode,
-                   long long* edges_dst, int32_t grid_blocks) {
+                   long long* edges_dst, int32_t grid_blocks, int32_t* status_dst) {
   if (root < 0 || root >= g->dg.n || !depth_out) return fail(BFS_ERR_INVALID_ARG, "run_async arguments");
   DeviceGuard dgd(g->device);
   TRY(sync_tree(g));
@@ -790,20 +804,83 @@ int bfs::run_async(bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t 
                                     stream);
     if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "edges copy: %s", cudaGetErrorString(e));
   }
+  if (r == BFS_OK && status_dst) {
+    cudaError_t e = cudaMemcpyAsync(status_dst, &ws->st->status, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+    if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "status copy: %s", cudaGetErrorString(e));
+  }
   int rr = release(g, ws, stream);
   return r != BFS_OK ? r : rr;
 }
 
-int bfs::batch_async(bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t stream,
-                     unsigned long long* edges_dst, int32_t grid_blocks) {
-  if (k < 1 || k > 64 || !roots || !depth_out) return fail(BFS_ERR_INVALID_ARG, "batch_async arguments");
+long long bfs::ms_set_bytes(const bfs_graph* g) {
+  return ms_set_bytes_per_vertex() * (long long)g->dg.n + (long long)sizeof(MsState);
+}
+
+int bfs::ms_set_create(bfs_graph* g, MsSet** out) {
   DeviceGuard dgd(g->device);
-  std::lock_guard<std::mutex> lk(g->ms_mu);
-  TRY(ms_prepare(g));
-  CU(cudaStreamWaitEvent(stream, g->ms_done, 0));
-  TRY(ms_launch_wave(g, roots, k, depth_out, stream, g->ms_cfg, grid_blocks));
-  if (edges_dst) CU(cudaMemcpyAsync(edges_dst, g->ms_state->edges, 64 * 8, cudaMemcpyDeviceToHost, stream));
-  CU(cudaEventRecord(g->ms_done, stream));
+  auto* set = new MsSet;
+  const size_t n = (size_t)g->dg.n;
+  int r = BFS_OK;
+  auto A = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    if (r == BFS_OK) r = dmalloc(&p, bytes);
+    if (r == BFS_OK) {
+      set->allocs.push_back(p);
+      set->bytes += bytes;
+    }
+    return p;
+  };
+  set->mb.visit = static_cast<unsigned long long*>(A(n * 8));
+  set->mb.front[0] = static_cast<unsigned long long*>(A(n * 8));
+  set->mb.front[1] = static_cast<unsigned long long*>(A(n * 8));
+  set->mb.next = static_cast<unsigned long long*>(A(n * 8));
+  set->mb.codes = static_cast<unsigned long long*>(A(n * 32));
+  set->mb.flist[0] = static_cast<int32_t*>(A(n * 4));
+  set->mb.flist[1] = static_cast<int32_t*>(A(n * 4));
+  set->mb.tlist = static_cast<int32_t*>(A(n * 4));
+  set->st = static_cast<MsState*>(A(sizeof(MsState)));
+  if (r == BFS_OK && cudaEventCreateWithFlags(&set->done, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    r = fail(BFS_ERR_CUDA, "cudaEventCreate");
+  }
+  if (r == BFS_OK) {
+    MsState init{};
+    r = upload_now(set->st, &init, sizeof init);
+  }
+  if (r != BFS_OK) {
+    ms_set_free(set);
+    return r;
+  }
+  *out = set;
+  return BFS_OK;
+}
+
+void bfs::ms_set_free(MsSet* set) {
+  if (!set) return;
+  if (set->done) {
+    cudaEventSynchronize(set->done);
+    cudaEventDestroy(set->done);
+  }
+  for (void* p : set->allocs) cudaFree(p);
+  delete set;
+}
+
+int bfs::batch_async(bfs_graph* g, MsSet* set, const int32_t* roots, int32_t k, int32_t* const* rows,
+                     cudaStream_t stream, unsigned long long* edges_dst, int32_t grid_blocks, int32_t* status_dst) {
+  if (!set || k < 1 || k > kMsMaxRoots || !roots || !rows) return fail(BFS_ERR_INVALID_ARG, "batch_async arguments");
+  for (int32_t i = 0; i < k; ++i)
+    if (!rows[i] || roots[i] < 0 || roots[i] >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "batch_async row or root");
+  DeviceGuard dgd(g->device);
+  MsConfig cfg;
+  {
+    std::lock_guard<std::mutex> lk(g->ms_mu);
+    TRY(ms_grid_init(g));
+    cfg = g->ms_cfg;
+  }
+  TRY(ms_launch_wave(g, set, roots, k, rows, stream, cfg, grid_blocks));
+  if (edges_dst) CU(cudaMemcpyAsync(edges_dst, set->st->edges, kMsMaxRoots * 8, cudaMemcpyDeviceToHost, stream));
+  if (status_dst) CU(cudaMemcpyAsync(status_dst, &set->st->status, 4, cudaMemcpyDeviceToHost, stream));
+  CU(cudaEventRecord(set->done, stream));
   return BFS_OK;
 }
 
@@ -972,11 +1049,20 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
     cleanup();
     return r;
   }
-  k_vis_init<<<blocks, kThreads>>>(off, in_off, (int32_t)n, (int32_t)words, vis_init);
-  e = cudaDeviceSynchronize();
+  unsigned int* iso = nullptr;
+  unsigned int iso_h = 0;
+  e = cudaMalloc(&iso, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(iso, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) {
+    k_vis_init<<<blocks, kThreads>>>(off, in_off, (int32_t)n, (int32_t)words, vis_init, iso);
+    e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&iso_h, iso, sizeof iso_h, cudaMemcpyDeviceToHost);
+  if (iso) cudaFree(iso);
   if (e != cudaSuccess) {
     cleanup();
-    return fail(BFS_ERR_CUDA, "graph create: %s", cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA, "graph create: %s",
+                cudaGetErrorString(e));
   }
   DevGraph& dg = g->dg;
   dg.off = off;
@@ -989,6 +1075,7 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
   dg.m = (int32_t)m;
   dg.words = (int32_t)((n + 31) / 32);
   dg.symmetric = g->symmetric ? 1 : 0;
+  dg.n_active = (int32_t)(n - (int64_t)iso_h);
   dg.gfeat[F_N] = n;
   dg.gfeat[F_M] = m;
   for (int k = 0; k < 6; ++k) dg.gfeat[F_DEG_MIN + k] = g->stats6[k];
@@ -1019,7 +1106,7 @@ int bfs_graph_destroy(bfs_graph_t g) {
   cudaError_t e = cudaDeviceSynchronize();
   for (Workspace* ws : g->pool) free_workspace(ws);
   for (TreeNode* t : g->trees) cudaFree(t);
-  if (g->ms_done) cudaEventDestroy(g->ms_done);
+  bfs::ms_set_free(g->ms_set);
   for (void* p : g->allocs) cudaFree(p);
   delete g;
   if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "destroy: %s", cudaGetErrorString(e));
@@ -1093,8 +1180,14 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   if (forced == V_EDGE_LIST || forced == V_REV_EDGE_LIST) TRY(ensure_origin(g));
   Workspace* ws = nullptr;
   TRY(acquire(g, stream, &ws));
+  int r = BFS_OK;
+  if (host_out && !ws->host_depth_stage) {  // allocated on a workspace's first host-output run
+    void* p = nullptr;
+    r = ws_alloc(ws, &p, (size_t)g->dg.n * 4);
+    ws->host_depth_stage = static_cast<int32_t*>(p);
+  }
   int32_t* dst = host_out ? ws->host_depth_stage : depth_out;
-  int r = launch_run(g, ws, root, dst, forced, mode, stream, grid_blocks, count_mode);
+  if (r == BFS_OK) r = launch_run(g, ws, root, dst, forced, mode, stream, grid_blocks, count_mode);
   RunState hs{};
   if (r == BFS_OK && host_out) {
     cudaError_t e = cudaMemcpyAsync(depth_out, dst, (size_t)g->dg.n * 4, cudaMemcpyDeviceToHost, stream);
@@ -1131,6 +1224,7 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
     stats->vertices_reached = hs.discovered;
     stats->levels = hs.levels;
     stats->status = hs.status;
+    stats->start_ns = hs.t_entry;
     if (hs.status != ST_OK) return fail(BFS_ERR_TIMEOUT, "a bounded device-side wait gave up");
   }
   return BFS_OK;
@@ -1152,23 +1246,26 @@ int bfs_run_batch(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth
   DeviceGuard dgd(g->device);
   std::lock_guard<std::mutex> lk(g->ms_mu);
   TRY(ms_prepare(g));
+  MsSet* set = g->ms_set;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  CU(cudaStreamWaitEvent(s, g->ms_done, 0));
+  CU(cudaStreamWaitEvent(s, set->done, 0));
   const int64_t n = g->dg.n;
-  for (int32_t w0 = 0; w0 < k; w0 += 64) {
-    const int32_t kw = std::min<int32_t>(64, k - w0);
-    TRY(ms_launch_wave(g, roots + w0, kw, depth_out + (size_t)w0 * n, s, g->ms_cfg, g->ms_grid_user));
+  for (int32_t w0 = 0; w0 < k; w0 += kMsMaxRoots) {
+    const int32_t kw = std::min<int32_t>(kMsMaxRoots, k - w0);
+    int32_t* rows[kMsMaxRoots];
+    block_rows(depth_out + (size_t)w0 * n, n, kw, rows);
+    TRY(ms_launch_wave(g, set, roots + w0, kw, rows, s, g->ms_cfg, g->ms_grid_user));
     if (edges_out) {
-      unsigned long long e[64];
-      CU(cudaMemcpyAsync(e, g->ms_state->edges, sizeof e, cudaMemcpyDeviceToHost, s));
+      unsigned long long e[kMsMaxRoots];
+      CU(cudaMemcpyAsync(e, set->st->edges, sizeof e, cudaMemcpyDeviceToHost, s));
       int32_t status = 0;
-      CU(cudaMemcpyAsync(&status, &g->ms_state->status, 4, cudaMemcpyDeviceToHost, s));
+      CU(cudaMemcpyAsync(&status, &set->st->status, 4, cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
       if (status != ST_OK) return fail(BFS_ERR_TIMEOUT, "a bounded device-side wait gave up");
       for (int32_t i = 0; i < kw; ++i) edges_out[w0 + i] = (int64_t)e[i];
     }
   }
-  CU(cudaEventRecord(g->ms_done, s));
+  CU(cudaEventRecord(set->done, s));
   return BFS_OK;
 }
 
@@ -1192,8 +1289,11 @@ int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* dept
   DeviceGuard dgd(g->device);
   std::lock_guard<std::mutex> lk(g->ms_mu);
   TRY(ms_prepare(g));
+  MsSet* set = g->ms_set;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  CU(cudaStreamWaitEvent(s, g->ms_done, 0));
+  CU(cudaStreamWaitEvent(s, set->done, 0));
+  int32_t* rows[kMsMaxRoots];
+  block_rows(depth_scratch, g->dg.n, k, rows);
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
@@ -1208,11 +1308,11 @@ int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* dept
     for (int pm = 0; pm < 2 && r == BFS_OK; ++pm)
       for (int a : alphas) {
         const MsConfig c{pm, a};
-        r = ms_launch_wave(g, roots, k, depth_scratch, s, c, grid);  // warm-up
+        r = ms_launch_wave(g, set, roots, k, rows, s, c, grid);  // warm-up
         if (r != BFS_OK) break;
         float ms = 0;
         if (cudaEventRecord(e0, s) != cudaSuccess ||
-            (r = ms_launch_wave(g, roots, k, depth_scratch, s, c, grid)) != BFS_OK ||
+            (r = ms_launch_wave(g, set, roots, k, rows, s, c, grid)) != BFS_OK ||
             cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
           if (r == BFS_OK) r = fail(BFS_ERR_CUDA, "tuning run failed");
@@ -1234,7 +1334,7 @@ int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* dept
   best->alpha = best_cfg.alpha;
   best->ms = best_ms;
   best->grid_blocks = best_grid;
-  CU(cudaEventRecord(g->ms_done, s));
+  CU(cudaEventRecord(set->done, s));
   return BFS_OK;
 }
 

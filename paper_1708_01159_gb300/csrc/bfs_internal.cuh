@@ -127,6 +127,8 @@ struct DevGraph {
   int32_t m;
   int32_t words;  // ceil(n / 32)
   int32_t symmetric;
+  int32_t n_active;  // vertices with at least one in- or out-edge (the others start visited)
+  int32_t pad_;
   long long gfeat[8];  // F_N .. F_DEG_SD256
 };
 
@@ -146,8 +148,8 @@ struct RunState {
   int32_t status;            // ST_OK / ST_TIMEOUT
   int32_t vw;                // virtual warp width of the push_warp variant at this level
   int32_t levels;            // levels completed (set when the run ends)
-  unsigned int next_count;   // f_{L+1}: output queue tail
-  unsigned int done_blocks;  // scratch counter
+  int32_t pad0_;
+  unsigned long long next_count;  // f_{L+1}: output queue tail
   unsigned long long next_edges;  // e_{L+1}
   long long frontier_edges;  // e_L
   long long discovered;      // sum of f_j, j <= L
@@ -155,18 +157,20 @@ struct RunState {
   unsigned long long h_while;   // cudaGraphConditionalHandle of the level loop
   unsigned long long h_switch;  // cudaGraphConditionalHandle of the variant switch
   long long feat[F_NUM];     // feature vector of the current level (written by decide)
-  // persistent driver: level counters indexed by level % 3 (level L reads slot
-  // L % 3, appends to (L + 1) % 3 and clears (L + 2) % 3) and the grid barrier
-  unsigned int cnt3[3];
-  unsigned int bar_count;
+  // persistent driver: level words indexed by level % 3 (level L reads slot
+  // L % 3, appends to (L + 1) % 3 and clears (L + 2) % 3). tail3: the output
+  // queue tail in the low 32 bits (the next frontier size), the blocks that
+  // reached the level-ending barrier in the high 32; edg3: the out-degree sum
+  // of the appended vertices in the low 40 bits (e_L <= m < 2^31), arrivals in
+  // the high 24. bar64: monotonic arrival count of the other grid barriers.
+  unsigned long long tail3[3];
   unsigned long long edg3[3];
-  unsigned int bar_gen;
-  int32_t pad2_;
-  unsigned long long lvl_word;  // persistent driver: level barrier word (phase, next f and e)
+  unsigned long long bar64;
   unsigned int run_epoch;       // persistent driver: epoch of the launch whose block 0 reset the barrier state
   int32_t pad3_;
   int32_t log_cap;
   int32_t pad_;
+  long long t_entry;  // %globaltimer (ns) when the run's first kernel started (before the depth init)
   int32_t* log_variant;
   long long* log_frontier;
   long long* log_edges;
@@ -189,14 +193,24 @@ int set_error_detail(int code, const char* msg);
 // Library-internal entry points used by the serving loop (not part of the C ABI).
 // run_async: enqueue one traversal on `stream` in the given bfs_mode and, when
 // edges_dst (pinned host memory) is not null, an asynchronous copy of its
-// reached-edge count there. batch_async: one multi-source wave (k <= 64) into k
-// rows of depth_out, per-root reached-edge counts copied to edges_dst (pinned,
-// 64 entries). grid_blocks > 0 limits a persistent run (or a wave) to that many
+// reached-edge count there. batch_async: one multi-source wave (k <= 64) on a
+// buffer set, root i's depths into rows[i] (device, n int32 each), per-root
+// reached-edge counts copied to edges_dst (pinned, 64 entries). grid_blocks > 0 limits a persistent run (or a wave) to that many
 // blocks so several can be resident at once. Both return a bfs_status code.
+// status_dst (pinned, optional) receives the run's device status word.
 int run_async(struct ::bfs_graph* g, int32_t root, int32_t* depth_out, cudaStream_t stream, int32_t mode,
-              long long* edges_dst, int32_t grid_blocks);
-int batch_async(struct ::bfs_graph* g, const int32_t* roots, int32_t k, int32_t* depth_out, cudaStream_t stream,
-                unsigned long long* edges_dst, int32_t grid_blocks);
+              long long* edges_dst, int32_t grid_blocks, int32_t* status_dst);
+int batch_async(struct ::bfs_graph* g, struct MsSet* set, const int32_t* roots, int32_t k, int32_t* const* rows,
+                cudaStream_t stream, unsigned long long* edges_dst, int32_t grid_blocks, int32_t* status_dst);
+// Create workspaces until the graph holds `count` of them (at most the pool
+// limit), so that up to that many concurrent runs allocate nothing.
+int reserve_workspaces(struct ::bfs_graph* g, int32_t count);
+// Multi-source buffer sets: one wave runs on a set at a time (the caller orders
+// waves on one set); a set holds ms_set_bytes(g) device bytes.
+struct MsSet;
+int ms_set_create(struct ::bfs_graph* g, MsSet** out);
+void ms_set_free(MsSet* set);
+long long ms_set_bytes(const struct ::bfs_graph* g);
 // Device bytes one traversal of the graph holds (workspace), for admission control.
 long long workspace_bytes(const struct ::bfs_graph* g);
 int32_t graph_vertices(const struct ::bfs_graph* g);
@@ -253,12 +267,15 @@ __device__ __forceinline__ void block_add_u64(unsigned long long x, unsigned lon
 }
 
 // Append v to the output queue with one atomic per group of converged lanes
-// (warp-aggregated atomic). The queue tail doubles as the next frontier size.
-__device__ __forceinline__ void queue_append(int32_t* qout, unsigned int* tail, int32_t v) {
+// (warp-aggregated atomic). The queue tail doubles as the next frontier size;
+// a 64-bit tail keeps it in its low 32 bits (the persistent kernel counts
+// barrier arrivals in the high half of the same word).
+template <typename TailT>
+__device__ __forceinline__ void queue_append(int32_t* qout, TailT* tail, int32_t v) {
   const uint32_t mask = __activemask();
   const int leader = __ffs(mask) - 1;
   unsigned int base = 0;
-  if ((int)lane_id() == leader) base = atomicAdd(tail, (unsigned)__popc(mask));
+  if ((int)lane_id() == leader) base = (unsigned int)atomicAdd(tail, (TailT)__popc(mask));
   base = __shfl_sync(mask, base, leader);
   qout[base + __popc(mask & lanemask_lt())] = v;
 }
@@ -284,7 +301,8 @@ struct Stage {
   __syncthreads();                                \
   const Stage name { name##_buf, &name##_cnt, &name##_base }
 
-__device__ __forceinline__ void stage_put(const Stage& s, int32_t* out, unsigned int* tail, int32_t v) {
+template <typename TailT>
+__device__ __forceinline__ void stage_put(const Stage& s, int32_t* out, TailT* tail, int32_t v) {
   const uint32_t mask = __activemask();
   const int leader = __ffs(mask) - 1;
   unsigned int pos = 0;
@@ -298,11 +316,12 @@ __device__ __forceinline__ void stage_put(const Stage& s, int32_t* out, unsigned
 
 // Copies the staged entries out once at least `threshold` are waiting. Every
 // thread of the block must call it (it synchronises).
-__device__ __forceinline__ void stage_drain(const Stage& s, int32_t* out, unsigned int* tail, unsigned int threshold) {
+template <typename TailT>
+__device__ __forceinline__ void stage_drain(const Stage& s, int32_t* out, TailT* tail, unsigned int threshold) {
   __syncthreads();
   const unsigned int c = min(*s.cnt, (unsigned)kStageCap);
   if (c == 0 || c < threshold) return;  // uniform: every thread read the same count
-  if (threadIdx.x == 0) *s.base = atomicAdd(tail, c);
+  if (threadIdx.x == 0) *s.base = (unsigned int)atomicAdd(tail, (TailT)c);
   __syncthreads();
   const unsigned int b = *s.base;
   for (unsigned int i = threadIdx.x; i < c; i += blockDim.x) out[b + i] = s.buf[i];
@@ -329,50 +348,6 @@ __device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) 
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier for persistent kernels (cooperative launch, so every block
-// is resident): arrival counter plus generation word. Thread 0 of each block
-// arrives with an acq_rel atomic (releasing its block's writes, which the
-// preceding __syncthreads ordered before it); the last arrival clears the
-// counter and publishes the next generation with a release store; the others
-// poll the generation with acquire loads, and the closing __syncthreads passes
-// what thread 0 acquired on to its block. Waiting is bounded by kWaitLimitNs
-// and abandoned early once *status is not ST_OK; on either the status word is
-// set and false returned, so a kernel never spins forever.
-__device__ __forceinline__ unsigned int atom_add_acq_rel_u32(unsigned int* p, unsigned int v) {
-  unsigned int old;
-  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-
-// `extra` (0 in normal operation) makes the barrier wait for that many
-// arrivals more than the grid has: the test hook that lets a test run a
-// bounded wait out (the last arrival never comes, every block's wait ends at
-// the limit and the status word reports it).
-__device__ __forceinline__ bool grid_barrier(unsigned int* count, unsigned int* gen_word, int32_t* status,
-                                             unsigned int extra = 0u) {
-  __syncthreads();
-  bool ok = true;
-  if (threadIdx.x == 0) {
-    const unsigned int gen = ld_acquire_u32(gen_word);
-    const unsigned int arrived = atom_add_acq_rel_u32(count, 1u);
-    if (arrived == gridDim.x - 1 + extra) {
-      *count = 0;
-      st_release_u32(gen_word, gen + 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (ld_acquire_u32(gen_word) == gen) {
-        if (*reinterpret_cast<volatile int32_t*>(status) != ST_OK || global_ns() - t0 > kWaitLimitNs) {
-          *status = ST_TIMEOUT;
-          ok = false;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-  }
-  return __syncthreads_and(ok) != 0;
-}
-
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -383,50 +358,107 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// The grid barrier that ends a level of the persistent kernel, carrying the
-// next level's frontier size f and frontier edge count e to every block: the
-// last arrival reads the two counters (every other block's appends were
-// released by its arrival and acquired by the last one's) and publishes them
-// with a flipped phase bit in one 64-bit release store, so the waiting blocks
-// get them with the poll that ends their wait instead of one more round trip
-// to the counters. Layout of *word: bit 63 phase, bits 31-61 e, bits 0-30 f
-// (both below 2^31: f <= n and e <= m). Bounded like grid_barrier.
-__device__ __forceinline__ bool level_barrier(unsigned int* count, unsigned long long* word, int32_t* status,
-                                              const unsigned int* next_f, const unsigned long long* next_e,
-                                              unsigned int* f_out, unsigned long long* e_out,
-                                              unsigned int extra = 0u) {
-  __shared__ unsigned long long s_word;
-  constexpr unsigned long long kMask31 = (1ull << 31) - 1ull;
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Sum of x over the block, returned to every thread. Every thread of the block
+// must call it (it synchronises).
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x) {
+  __shared__ unsigned long long part[33];
+  x = warp_sum(x);
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 0) part[w] = x;
   __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    unsigned long long y = lane_id() < (uint32_t)nw ? part[lane_id()] : 0ull;
+    y = warp_sum(y);
+    if (lane_id() == 0) part[32] = y;
+  }
+  __syncthreads();
+  const unsigned long long total = part[32];
+  __syncthreads();
+  return total;
+}
+
+// Grid-wide barrier on a monotonic 64-bit arrival count (cooperative launch:
+// every block resident). Thread 0 of each block adds 1 with a release
+// reduction (no value comes back, so nothing waits for it) and polls the count
+// with acquire loads until every block of this barrier has arrived: `target`,
+// a copy each block keeps, advances by the grid size per barrier, so the count
+// is never reset within a launch and the last arrival publishes nothing. The
+// preceding __syncthreads orders the block's writes before thread 0's release;
+// the closing one passes what thread 0 acquired on to the block. `extra`
+// (0 normally) makes the barrier wait for that many arrivals more than the
+// grid has: the test hook that runs a bounded wait out. The wait ends after
+// kWaitLimitNs, or early once *status is not ST_OK; then the status word is
+// set and false returned.
+__device__ __forceinline__ bool grid_arrive_wait(unsigned long long* count, unsigned long long& target,
+                                                 int32_t* status, unsigned int extra = 0u) {
+  __syncthreads();
+  target += gridDim.x;
   bool ok = true;
   if (threadIdx.x == 0) {
-    const unsigned long long w0 = ld_acquire_u64(word);
-    const unsigned long long phase = w0 >> 63;
-    const unsigned int arrived = atom_add_acq_rel_u32(count, 1u);
-    unsigned long long w = w0;
-    if (arrived == gridDim.x - 1 + extra) {
-      *count = 0;
-      const unsigned long long f = *reinterpret_cast<const volatile unsigned int*>(next_f);
-      const unsigned long long e = *reinterpret_cast<const volatile unsigned long long*>(next_e);
-      w = ((phase ^ 1ull) << 63) | (min(e, kMask31) << 31) | min(f, kMask31);
-      st_release_u64(word, w);
-    } else {
+    red_release_add_u64(count, 1ull);
+    const unsigned long long want = target + extra;
+    if (ld_acquire_u64(count) < want) {
       const unsigned long long t0 = global_ns();
-      while (((w = ld_acquire_u64(word)) >> 63) == phase) {
+      while (ld_acquire_u64(count) < want) {
         if (*reinterpret_cast<volatile int32_t*>(status) != ST_OK || global_ns() - t0 > kWaitLimitNs) {
           *status = ST_TIMEOUT;
           ok = false;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
-    s_word = w;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// The barrier that ends a level of the persistent kernel. Two words of the
+// next level's slot carry both the arrivals and the next level's inputs:
+// *tail holds the output queue tail (f, low 32 bits) and *edges the frontier
+// edge sum (e, low 40 bits). Thread 0 adds its block's edge sum e_block
+// together with one arrival (bit 40) to *edges, then one arrival (bit 32) to
+// *tail, both as release reductions after all of the block's appends; then it
+// polls both words until each shows every block's arrival, and reads f and e
+// from the same loads. No block waits for an atomic's return, no last block
+// publishes anything, and no block reads a counter after the barrier. Bounded
+// and hookable like grid_arrive_wait.
+__device__ __forceinline__ bool level_arrive_wait(unsigned long long* tail, unsigned long long* edges,
+                                                  unsigned long long e_block, int32_t* status, unsigned int* f_out,
+                                                  unsigned long long* e_out, unsigned int extra = 0u) {
+  __shared__ unsigned long long s_w[2];
+  constexpr unsigned long long kLow32 = 0xffffffffull, kLow40 = (1ull << 40) - 1ull;
+  __syncthreads();
+  bool ok = true;
+  if (threadIdx.x == 0) {
+    red_release_add_u64(edges, (1ull << 40) + e_block);
+    red_release_add_u64(tail, 1ull << 32);
+    const unsigned long long want = (unsigned long long)gridDim.x + extra;
+    unsigned long long a = ld_acquire_u64(tail), b = ld_acquire_u64(edges);
+    if ((a >> 32) < want || (b >> 40) < want) {
+      const unsigned long long t0 = global_ns();
+      for (;;) {
+        a = ld_acquire_u64(tail);
+        b = ld_acquire_u64(edges);
+        if ((a >> 32) >= want && (b >> 40) >= want) break;
+        if (*reinterpret_cast<volatile int32_t*>(status) != ST_OK || global_ns() - t0 > kWaitLimitNs) {
+          *status = ST_TIMEOUT;
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    s_w[0] = a;
+    s_w[1] = b;
   }
   ok = __syncthreads_and(ok) != 0;
-  const unsigned long long w = s_word;
-  *f_out = (unsigned int)(w & kMask31);
-  *e_out = (w >> 31) & kMask31;
+  *f_out = (unsigned int)(s_w[0] & kLow32);
+  *e_out = s_w[1] & kLow40;
   return ok;
 }
 

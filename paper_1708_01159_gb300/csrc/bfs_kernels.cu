@@ -74,7 +74,6 @@ __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
   return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
-__device__ __forceinline__ bool grid_sync(RunState* st) { return grid_barrier(&st->bar_count, &st->bar_gen, &st->status); }
 
 // ---- output staging and per-edge visit --------------------------------------
 
@@ -87,12 +86,22 @@ struct Level {
   uint32_t* vis;       // current visited bitmap (push updates it in place; pull reads it)
   uint32_t* vis_next;  // the other bitmap (pull writes it)
   int32_t* depth;
-  unsigned int* tail;
+  unsigned long long* tail;  // output queue tail (low 32 bits)
   int32_t next_depth;
   int32_t frontier;
+  int32_t latency_bound;  // the level's frontier has fewer than kLatencyEdges edges
+  int32_t pull_sparse;    // fewer than 1/16 of the vertices with edges are still unvisited
 };
 
-__device__ __forceinline__ Level load_level(const Buffers& b, RunState* st) {
+// Below this many frontier edges a level cannot fill the GPU: its time is the
+// latency of its chain of dependent memory accesses, not bandwidth. Such a
+// level claims targets without reading their bitmap word first (one round trip
+// less; the extra atomics cost nothing at this size) and prefetches the first
+// adjacency sector of every vertex it reaches into L2, so the next level's
+// list reads are L2 hits.
+constexpr long long kLatencyEdges = 1ll << 17;
+
+__device__ __forceinline__ Level load_level(const DevGraph& g, const Buffers& b, RunState* st) {
   Level lv;
   // select with ternaries: indexing the by-value parameter arrays would copy them to local memory
   const bool qs = st->qsel != 0u;
@@ -105,6 +114,8 @@ __device__ __forceinline__ Level load_level(const Buffers& b, RunState* st) {
   lv.tail = &st->next_count;
   lv.next_depth = st->level + 1;
   lv.frontier = st->frontier;
+  lv.latency_bound = st->frontier_edges < kLatencyEdges;
+  lv.pull_sparse = (long long)g.n_active - st->discovered < (long long)(g.n_active >> 4);
   return lv;
 }
 
@@ -118,27 +129,42 @@ __device__ __forceinline__ void stage_flush(const Stage& s, const Level& lv, uns
   stage_drain(s, lv.qout, lv.tail, threshold);
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Top-down visit of up to K edges u -> v[k] (Section 3.1.2 push). The bitmap
-// words of all K targets are read, then the claims (atomicOr) issued, then the
-// winners' degrees read, so the K edges' memory round trips overlap instead of
-// forming one dependent chain per edge. The one thread whose atomicOr flips a
-// vertex's bit writes its depth, counts its out-degree and stages it.
+// words of all K targets are read (except on latency-bound levels), then the
+// claims (atomicOr) issued, then the winners' row extents read, so the K
+// edges' memory round trips overlap instead of forming one dependent chain per
+// edge. The one thread whose atomicOr flips a vertex's bit writes its depth,
+// counts its out-degree and stages it.
+// valid: bit k set when v[k] is an edge to visit.
 template <int K, int kCount = CM_BLOCK>
-__device__ __forceinline__ void visit_k(const DevGraph& g, const Level& lv, const Stage& s, const int32_t (&v)[K],
-                                        int nv, unsigned long long& edges) {
+__device__ __forceinline__ void visit_km(const DevGraph& g, const Level& lv, const Stage& s, const int32_t (&v)[K],
+                                         uint32_t valid, unsigned long long& edges) {
+  const bool filter = !lv.latency_bound;
   uint32_t word[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) word[k] = k < nv ? ld_volatile_u32(lv.vis + (v[k] >> 5)) : 0xffffffffu;
+  for (int k = 0; k < K; ++k)
+    word[k] = (valid >> k) & 1u ? (filter ? ld_volatile_u32(lv.vis + (v[k] >> 5)) : 0u) : 0xffffffffu;
   bool won[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const uint32_t bit = 1u << (v[k] & 31);
     won[k] = false;
-    if (k < nv && !(word[k] & bit)) won[k] = (atomicOr(lv.vis + (v[k] >> 5), bit) & bit) == 0u;
+    if (((valid >> k) & 1u) && !(word[k] & bit)) won[k] = (atomicOr(lv.vis + (v[k] >> 5), bit) & bit) == 0u;
   }
   int32_t d[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) d[k] = won[k] ? g.off[v[k] + 1] - g.off[v[k]] : 0;
+  for (int k = 0; k < K; ++k) {
+    d[k] = 0;
+    if (won[k]) {
+      const int32_t b0 = g.off[v[k]];
+      d[k] = g.off[v[k] + 1] - b0;
+      if (!filter && d[k] > 0) prefetch_l2(g.idx + b0);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < K; ++k)
     if (won[k]) {
@@ -149,8 +175,15 @@ __device__ __forceinline__ void visit_k(const DevGraph& g, const Level& lv, cons
       else if (kCount == CM_WARP)
         queue_append(lv.qout, lv.tail, v[k]);
       else
-        lv.qout[atomicAdd(lv.tail, 1u)] = v[k];
+        lv.qout[(unsigned int)atomicAdd(lv.tail, 1ull)] = v[k];
     }
+}
+
+// The first nv entries of v are edges to visit.
+template <int K, int kCount = CM_BLOCK>
+__device__ __forceinline__ void visit_k(const DevGraph& g, const Level& lv, const Stage& s, const int32_t (&v)[K],
+                                        int nv, unsigned long long& edges) {
+  visit_km<K, kCount>(g, lv, s, v, nv >= 32 ? 0xffffffffu : (1u << nv) - 1u, edges);
 }
 
 template <typename T>
@@ -343,6 +376,44 @@ __device__ __forceinline__ void push_vwarp(const DevGraph& g, const Level& lv, c
                                            unsigned long long& edges) {
   constexpr int G = kThreads / W;  // groups per block
   const int lane = threadIdx.x & (W - 1);
+  if (W < 32 && lv.frontier > (int)gridDim.x * G) {
+    // More frontier vertices than groups: a group takes kR consecutive
+    // frontier vertices per step, and each round every lane visits one edge of
+    // each of them (edge lane, lane + W, ...), so kR independent chains of
+    // loads are in flight per lane and the level needs a quarter of the steps
+    // (a high-diameter graph's levels on a narrow grid). A frontier that fits
+    // one step keeps one vertex per group, spread over every block.
+    constexpr int kR = 4;
+    const int grp = (int)threadIdx.x / W;
+    for (int base = blockIdx.x * G * kR; base < lv.frontier; base += gridDim.x * G * kR) {
+      int32_t e[kR], end[kR];
+#pragma unroll
+      for (int j = 0; j < kR; ++j) {
+        const int i = base + grp * kR + j;
+        e[j] = end[j] = 0;
+        if (i < lv.frontier) {
+          const int32_t u = lv.qin[i];
+          e[j] = g.off[u] + lane;
+          end[j] = g.off[u + 1];
+        }
+      }
+      uint32_t valid;
+      do {
+        int32_t v[kR];
+        valid = 0;
+#pragma unroll
+        for (int j = 0; j < kR; ++j) {
+          const bool ok = e[j] < end[j];
+          v[j] = ok ? g.idx[e[j]] : 0;
+          valid |= (uint32_t)ok << j;
+          e[j] += W;
+        }
+        if (valid) visit_km<kR>(g, lv, stage, v, valid, edges);
+      } while (valid);
+      stage_flush(stage, lv, kStageCap / 2);
+    }
+    return;
+  }
   for (int base = blockIdx.x * G; base < lv.frontier; base += gridDim.x * G) {
     const int i = base + (int)threadIdx.x / W;
     if (i < lv.frontier) {
@@ -625,10 +696,18 @@ __device__ void body_pe_expand(const DevGraph& g, const Level& lv, const Buffers
   const int32_t* scan = kSmall ? s_a_buf + 1 : b.pe_scan;
   const int32_t E = scan[f];
   const long long total = (long long)f + E;
-  const long long ntiles = (total + kPeTile - 1) / kPeTile;
+  // Tile length: a whole multiple of the block size, as short as spreads the
+  // items over every block (one per thread at least), at most kPeTile. A
+  // small level (a handful of frontier vertices with some thousands of edges)
+  // then runs on many blocks with an item or two per thread instead of a few
+  // full tiles, so its latency is one visit chain instead of eight.
+  const long long per_block = (total + gridDim.x - 1) / gridDim.x;
+  const int tile = (int)min((long long)kPeTile, max((long long)kThreads, (per_block + kThreads - 1) / kThreads * kThreads));
+  const int ipt = tile / kThreads;  // items per thread, 1..kPeItems
+  const long long ntiles = (total + tile - 1) / tile;
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const long long d0 = t * kPeTile;
-    const long long d1 = min(d0 + kPeTile, total);
+    const long long d0 = t * tile;
+    const long long d1 = min(d0 + tile, total);
     if (threadIdx.x < 2) s_split[threadIdx.x] = merge_split(scan, f, 0, E, threadIdx.x ? d1 : d0);
     __syncthreads();
     const int i0 = s_split[0], i1 = s_split[1];
@@ -650,8 +729,8 @@ __device__ void body_pe_expand(const DevGraph& g, const Level& lv, const Buffers
       }
       __syncthreads();
     }
-    const int td0 = min((int)threadIdx.x * kPeItems, tl);
-    const int td1 = min(td0 + kPeItems, tl);
+    const int td0 = min((int)threadIdx.x * ipt, tl);
+    const int td1 = min(td0 + ipt, tl);
     const int ti = merge_split(s_a + 1, na, j0, nb, td0);
     int cur = ti;          // s index of the current vertex
     int anext = ti + 1;    // s index of the next boundary
@@ -709,92 +788,157 @@ static_assert(kStageCap % (kThreads / 32) == 0, "stage slices");
 __device__ __forceinline__ void warp_stage_flush(int32_t* wbuf, unsigned int cnt, const Level& lv) {
   __syncwarp();
   unsigned int base = 0;
-  if (lane_id() == 0) base = atomicAdd(lv.tail, cnt);
+  if (lane_id() == 0) base = (unsigned int)atomicAdd(lv.tail, (unsigned long long)cnt);
   base = __shfl_sync(kFull, base, 0);
   for (unsigned int i = lane_id(); i < cnt; i += 32) lv.qout[base + i] = wbuf[i];
   __syncwarp();
 }
 
+// The scan of kWords bitmap words (w[j] < 0: none) with current words cw[j]:
+// each lane takes vertex w[j] * 32 + lane of every word, scans its
+// in-neighbours four per round, interleaving the kWords scans, and stops at
+// the first visited one; found vertices get their depth and a slot of the
+// warp's stage, and the next bitmap's words are written.
+template <bool kReadOnlyCache, int kWords>
+__device__ __forceinline__ void pull_words(const DevGraph& g, const Level& lv, const int32_t (&w)[kWords],
+                                           const uint32_t (&cw)[kWords], int32_t* wbuf, unsigned int& wcnt,
+                                           unsigned long long& edges) {
+  const uint32_t lane = lane_id();
+  int32_t v[kWords], pos[kWords], beg[kWords], end[kWords];
+  bool active[kWords], found[kWords];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < kWords; ++j) {
+    v[j] = w[j] * 32 + (int32_t)lane;
+    active[j] = w[j] >= 0 && cw[j] != kFull && v[j] < g.n && !((cw[j] >> lane) & 1u);
+    found[j] = false;
+    beg[j] = end[j] = 0;
+    if (active[j]) {
+      beg[j] = g.in_off[v[j]];
+      end[j] = g.in_off[v[j] + 1];
+    }
+    pos[j] = beg[j];
+    active[j] = active[j] && beg[j] < end[j];
+    any = any || active[j];
+  }
+  while (any) {
+    int32_t u[kWords][4];
+#pragma unroll
+    for (int j = 0; j < kWords; ++j) {
+      const int nv = active[j] ? min(4, end[j] - pos[j]) : 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) u[j][k] = nv ? g.in_idx[k < nv ? pos[j] + k : pos[j]] : 0;
+    }
+    any = false;
+#pragma unroll
+    for (int j = 0; j < kWords; ++j) {
+      if (!active[j]) continue;
+      uint32_t hit = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) hit |= vis_bit<kReadOnlyCache>(lv.vis, u[j][k]);
+      pos[j] += 4;
+      if (hit) {
+        found[j] = true;
+        active[j] = false;
+      } else if (pos[j] >= end[j]) {
+        active[j] = false;
+      }
+      any = any || active[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kWords; ++j) {
+    const uint32_t fm = __ballot_sync(kFull, found[j]);
+    if (found[j]) {
+      const int32_t deg = g.symmetric ? end[j] - beg[j] : g.off[v[j] + 1] - g.off[v[j]];
+      lv.depth[v[j]] = lv.next_depth;
+      edges += (unsigned long long)deg;
+      wbuf[wcnt + __popc(fm & lanemask_lt())] = v[j];
+    }
+    wcnt += (unsigned)__popc(fm);
+    if (lane == 0 && w[j] >= 0) lv.vis_next[w[j]] = cw[j] | fm;
+  }
+}
+
+// Two walks over the bitmap words share pull_words. This warp's k-th word is
+// (k / kWords) * stride + base0 + (k % kWords) * kWarps (consecutive warps take
+// consecutive words; increasing in k), and it takes kWords per step.
+//  - dense (most reachable vertices still unvisited): each step's words are
+//    loaded one step ahead, so that load's round trip overlaps the scans;
+//  - sparse (few left): a batch of 32 of the warp's words is loaded at once,
+//    one per lane; words with no unvisited vertex are settled right there
+//    (their next-bitmap word is all ones), the row extents of the others are
+//    prefetched into L2, and only those are scanned. A late level whose words
+//    are nearly all full then costs one round trip per 32 words instead of
+//    one per kWords.
+template <bool kReadOnlyCache>
+__device__ __forceinline__ uint32_t pull_load_word(const uint32_t* vis, int32_t w) {
+  return kReadOnlyCache ? ld_nc_u32(vis + w) : vis[w];
+}
+
 template <bool kReadOnlyCache, int kWords>
 __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
   static_assert(kWords * 32 <= kWarpStage, "a step must fit a stage slice");
-  const uint32_t* cur_vis = lv.vis;
-  uint32_t* nxt_vis = lv.vis_next;
+  static_assert(32 % kWords == 0, "a batch holds whole steps");
   const uint32_t lane = lane_id();
   constexpr int kWarps = kThreads / 32;
   const int wib = threadIdx.x >> 5;
   int32_t* wbuf = stage.buf + wib * kWarpStage;  // the block stage is empty on entry
   unsigned int wcnt = 0;
   const int stride = gridDim.x * kWarps * kWords;
-  uint32_t cw_next[kWords];
-#pragma unroll
-  for (int j = 0; j < kWords; ++j) {
-    const int wn = blockIdx.x * kWarps * kWords + j * kWarps + wib;
-    cw_next[j] = wn < g.words ? cur_vis[wn] : kFull;
-  }
-  for (int wbase = blockIdx.x * kWarps * kWords; wbase < g.words; wbase += stride) {
-    int32_t w[kWords], v[kWords], pos[kWords], beg[kWords], end[kWords];
-    uint32_t cw[kWords];
-    bool active[kWords], found[kWords];
-    bool any = false;
+  const int base0 = blockIdx.x * kWarps * kWords + wib;
+  if (!lv.pull_sparse) {
+    uint32_t cw_next[kWords];
 #pragma unroll
     for (int j = 0; j < kWords; ++j) {
-      w[j] = wbase + j * kWarps + wib;  // consecutive warps take consecutive words
-      cw[j] = cw_next[j];
-      const int wn = w[j] + stride;
-      cw_next[j] = wn < g.words ? cur_vis[wn] : kFull;
-      v[j] = w[j] * 32 + (int32_t)lane;
-      active[j] = cw[j] != kFull && v[j] < g.n && !((cw[j] >> lane) & 1u);
-      found[j] = false;
-      beg[j] = end[j] = 0;
-      if (active[j]) {
-        beg[j] = g.in_off[v[j]];
-        end[j] = g.in_off[v[j] + 1];
-      }
-      pos[j] = beg[j];
-      active[j] = active[j] && beg[j] < end[j];
-      any = any || active[j];
+      const int wn = base0 + j * kWarps;
+      cw_next[j] = wn < g.words ? pull_load_word<kReadOnlyCache>(lv.vis, wn) : kFull;
     }
-    while (any) {
-      int32_t u[kWords][4];
+    for (int wb = base0; wb < g.words; wb += stride) {
+      int32_t w[kWords];
+      uint32_t cw[kWords];
 #pragma unroll
       for (int j = 0; j < kWords; ++j) {
-        const int nv = active[j] ? min(4, end[j] - pos[j]) : 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) u[j][k] = nv ? g.in_idx[k < nv ? pos[j] + k : pos[j]] : 0;
+        w[j] = wb + j * kWarps;
+        w[j] = w[j] < g.words ? w[j] : -1;
+        cw[j] = cw_next[j];
+        const int wn = wb + j * kWarps + stride;
+        cw_next[j] = wn < g.words ? pull_load_word<kReadOnlyCache>(lv.vis, wn) : kFull;
       }
-      any = false;
+      pull_words<kReadOnlyCache, kWords>(g, lv, w, cw, wbuf, wcnt, edges);
+      if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
+        warp_stage_flush(wbuf, wcnt, lv);
+        wcnt = 0;
+      }
+    }
+  } else {
+    for (int k0 = 0;; k0 += 32) {
+      const int kk = k0 + (int)lane;
+      const int wl = (kk / kWords) * stride + base0 + (kk % kWords) * kWarps;
+      if (__shfl_sync(kFull, wl, 0) >= g.words) break;  // uniform: lane 0 holds the batch's smallest word
+      const bool inb = wl < g.words;
+      const uint32_t cwl = inb ? pull_load_word<kReadOnlyCache>(lv.vis, wl) : kFull;
+      const bool open = inb && cwl != kFull;
+      if (inb && !open) lv.vis_next[wl] = kFull;
+      if (open) prefetch_l2(g.in_off + (size_t)wl * 32);
+      uint32_t todo = __ballot_sync(kFull, open);
+      while (todo) {  // uniform
+        int32_t w[kWords];
+        uint32_t cw[kWords];
 #pragma unroll
-      for (int j = 0; j < kWords; ++j) {
-        if (!active[j]) continue;
-        uint32_t hit = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) hit |= vis_bit<kReadOnlyCache>(cur_vis, u[j][k]);
-        pos[j] += 4;
-        if (hit) {
-          found[j] = true;
-          active[j] = false;
-        } else if (pos[j] >= end[j]) {
-          active[j] = false;
+        for (int j = 0; j < kWords; ++j) {
+          const int src = todo ? __ffs(todo) - 1 : 0;
+          const bool have = todo != 0u;
+          todo &= todo - 1u;
+          w[j] = have ? __shfl_sync(kFull, wl, src) : -1;
+          cw[j] = have ? __shfl_sync(kFull, cwl, src) : kFull;
         }
-        any = any || active[j];
+        pull_words<kReadOnlyCache, kWords>(g, lv, w, cw, wbuf, wcnt, edges);
+        if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
+          warp_stage_flush(wbuf, wcnt, lv);
+          wcnt = 0;
+        }
       }
-    }
-#pragma unroll
-    for (int j = 0; j < kWords; ++j) {
-      const uint32_t fm = __ballot_sync(kFull, found[j]);
-      if (found[j]) {
-        const int32_t deg = g.symmetric ? end[j] - beg[j] : g.off[v[j] + 1] - g.off[v[j]];
-        lv.depth[v[j]] = lv.next_depth;
-        edges += (unsigned long long)deg;
-        wbuf[wcnt + __popc(fm & lanemask_lt())] = v[j];
-      }
-      wcnt += (unsigned)__popc(fm);
-      if (lane == 0 && w[j] < g.words) nxt_vis[w[j]] = cw[j] | fm;
-    }
-    if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
-      warp_stage_flush(wbuf, wcnt, lv);
-      wcnt = 0;
     }
   }
   if (wcnt) warp_stage_flush(wbuf, wcnt, lv);
@@ -845,6 +989,7 @@ __device__ void body_edge_list(const DevGraph& g, const Level& lv, const Stage& 
 __global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root,
                                                    int32_t forced, const TreeNode* tree, int32_t tree_nodes,
                                                    const QsTree* tree_qs, int32_t use_handles) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->t_entry = (long long)global_ns();
   init_fill(g, b.vis[0], depth, root);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->depth = depth;
@@ -862,7 +1007,6 @@ __global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunSta
     st->status = ST_OK;
     st->vw = 32;
     st->levels = 0;
-    st->done_blocks = 0;
     st->frontier_edges = 0;
     st->discovered = 0;
     st->edges_reached = 0;
@@ -895,7 +1039,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b
   int32_t L = 0;
   if (threadIdx.x == 0) {
     // close level L-1: its output queue becomes the frontier of level L
-    const unsigned int f = *reinterpret_cast<volatile unsigned int*>(&s.next_count);
+    const unsigned int f = (unsigned int)*reinterpret_cast<volatile unsigned long long*>(&s.next_count);
     const unsigned long long e = *reinterpret_cast<volatile unsigned long long*>(&s.next_edges);
     s.next_count = 0;
     s.next_edges = 0;
@@ -950,7 +1094,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b
 // Vertex push with the other frontier-count modes (Section 3.1.4 comparison).
 __global__ void __launch_bounds__(kThreads) k_push_thread_warp_count(DevGraph g, Buffers b, RunState* st) {
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
   body_push_thread<CM_WARP>(g, lv, stage, edges);
   block_add_u64(edges, &st->next_edges);
@@ -958,7 +1102,7 @@ __global__ void __launch_bounds__(kThreads) k_push_thread_warp_count(DevGraph g,
 
 __global__ void __launch_bounds__(kThreads) k_push_thread_atomic_count(DevGraph g, Buffers b, RunState* st) {
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
   body_push_thread<CM_ATOMIC>(g, lv, stage, edges);
   block_add_u64(edges, &st->next_edges);
@@ -966,7 +1110,7 @@ __global__ void __launch_bounds__(kThreads) k_push_thread_atomic_count(DevGraph 
 
 __global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b, RunState* st) {
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
   body_push_thread(g, lv, stage, edges);
   stage_flush(stage, lv, 1);
@@ -975,7 +1119,7 @@ __global__ void __launch_bounds__(kThreads) k_push_thread(DevGraph g, Buffers b,
 
 __global__ void __launch_bounds__(kThreads) k_push_warp(DevGraph g, Buffers b, RunState* st) {
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
   body_push_warp(g, lv, stage, st->vw, edges);
   stage_flush(stage, lv, 1);
@@ -986,7 +1130,7 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
   __shared__ alignas(128) int32_t chunk[2 * kCtaChunk];
   __shared__ alignas(8) uint64_t bar[2];
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   cta_pipe_init(bar);
   CtaPipe pp{chunk, bar, 0u, 0u, 0u};
   unsigned long long edges = 0;
@@ -998,7 +1142,7 @@ __global__ void __launch_bounds__(kThreads) k_push_cta(DevGraph g, Buffers b, Ru
 // (A frontier of at most kPeSmall vertices is scanned by k_pe_expand itself:
 // the three scan launches then return at once.)
 __global__ void __launch_bounds__(kThreads) k_pe_reduce(DevGraph g, Buffers b, RunState* st) {
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   if (lv.frontier <= kPeSmall) return;
   body_pe_reduce(g, lv, b);
 }
@@ -1022,7 +1166,7 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
   __shared__ int32_t s_beg[kPeTile + 1];
   __shared__ int s_split[2];
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
   if (lv.frontier <= kPeSmall) {
     pe_small_scan(g, lv, s_a, s_beg);
@@ -1035,7 +1179,7 @@ __global__ void __launch_bounds__(kThreads) k_pe_expand(DevGraph g, Buffers b, R
 
 __global__ void __launch_bounds__(kThreads) k_edge_list(DevGraph g, Buffers b, RunState* st) {
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
   body_edge_list<false>(g, lv, stage, edges);
   stage_flush(stage, lv, 1);
@@ -1044,7 +1188,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_list(DevGraph g, Buffers b, R
 
 __global__ void __launch_bounds__(kThreads) k_rev_edge_list(DevGraph g, Buffers b, RunState* st) {
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
   body_edge_list<true>(g, lv, stage, edges);
   stage_flush(stage, lv, 1);
@@ -1060,7 +1204,7 @@ __global__ void k_build_origin(const int32_t* off, int32_t n, int32_t* origin) {
 
 __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunState* st) {
   BFS_DECLARE_STAGE(stage);
-  const Level lv = load_level(b, st);
+  const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
   body_pull<true, kPullWordsLaunch>(g, lv, stage, edges);
   stage_flush(stage, lv, 1);
@@ -1078,7 +1222,7 @@ __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunSta
 // started from, in time proportional to the level's output (pull wrote only
 // the other bitmap, which is rewritten whole before it is read again).
 __global__ void k_undo_level(Buffers b, RunState* st) {
-  const unsigned int count = st->next_count;
+  const unsigned int count = (unsigned int)st->next_count;
   const int32_t* qout = st->qsel ? b.q[0] : b.q[1];
   uint32_t* vis = st->vsel ? b.vis[1] : b.vis[0];
   int32_t* depth = st->depth;
@@ -1102,8 +1246,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
                                                              int32_t tree_nodes, const QsTree* qs, uint32_t epoch,
                                                              int32_t stall) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->bar_count = 0;
+    st->t_entry = (long long)global_ns();
+    st->bar64 = 0;
     st->status = ST_OK;
+    for (int k = 0; k < 3; ++k) {
+      st->tail3[k] = 0;
+      st->edg3[k] = 0;
+    }
     st_release_u32(&st->run_epoch, epoch);
   }
   // one shared buffer serves the CTA variant's copy stage or the edge-centric tile
@@ -1129,12 +1278,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     st->depth = depth;
     st->root = root;
     st->forced = forced;
-    st->cnt3[0] = 1;
-    st->cnt3[1] = 0;
-    st->cnt3[2] = 0;
-    st->edg3[0] = (unsigned long long)(g.off[root + 1] - g.off[root]);
-    st->edg3[1] = 0;
-    st->edg3[2] = 0;
     b.q[0][0] = root;
   }
   cta_pipe_init(bar);
@@ -1152,7 +1295,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   // level 0's frontier is the root; later levels' f and e arrive with the barrier
   unsigned int f = 1;
   unsigned long long e = (unsigned long long)(g.off[root + 1] - g.off[root]);
-  bool ok = grid_barrier(&st->bar_count, &st->bar_gen, &st->status, stall == STALL_GRID_BARRIER ? 1u : 0u);
+  unsigned long long bar_target = 0;  // this block's copy of the grid barriers' arrival target
+  bool ok = grid_arrive_wait(&st->bar64, bar_target, &st->status, stall == STALL_GRID_BARRIER ? 1u : 0u);
   for (; ok; ++L) {
     discovered += f;
     reached += (long long)e;
@@ -1169,7 +1313,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
       v = walk_tree(g, tree, tree_nodes, L, f, (long long)e, discovered);
     v = finish_variant(v, L, prev, f, (long long)e, &vw, forced >= 0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st->cnt3[(L + 2) % 3] = 0;  // last read by level L - 1, which every block has finished
+      st->tail3[(L + 2) % 3] = 0;  // the slot of level L - 2's barrier, which every block has left
       st->edg3[(L + 2) % 3] = 0;
       if (L < st->log_cap) {
         st->log_variant[L] = v;
@@ -1184,9 +1328,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     lv.vis = vsel ? b.vis[1] : b.vis[0];
     lv.vis_next = vsel ? b.vis[0] : b.vis[1];
     lv.depth = depth;
-    lv.tail = &st->cnt3[(L + 1) % 3];
+    lv.tail = &st->tail3[(L + 1) % 3];
     lv.next_depth = L + 1;
     lv.frontier = (int32_t)f;
+    lv.latency_bound = (long long)e < kLatencyEdges;
+    lv.pull_sparse = (long long)g.n_active - discovered < (long long)(g.n_active >> 4);
     unsigned long long edges = 0;
     switch (v) {
       case V_PUSH_THREAD: body_push_thread(g, lv, stage, edges); break;
@@ -1199,11 +1345,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
           break;
         }
         body_pe_reduce(g, lv, b);
-        if (!grid_sync(st)) break;
+        if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
         if (blockIdx.x == 0) body_pe_top(b, (int)f);
-        if (!grid_sync(st)) break;
+        if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
         body_pe_scan(b, (int)f);
-        if (!grid_sync(st)) break;
+        if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
         body_pe_expand<false>(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
         break;
       case V_EDGE_LIST: body_edge_list<false>(g, lv, stage, edges); break;
@@ -1211,11 +1357,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
       default: body_pull<false, kPullWordsPersistent>(g, lv, stage, edges); break;
     }
     stage_flush(stage, lv, 1);
-    block_add_u64(edges, &st->edg3[(L + 1) % 3]);
+    const unsigned long long e_block = block_sum_u64(edges);
     if (v == V_PULL) vsel ^= 1u;
     prev = v;
-    ok = level_barrier(&st->bar_count, &st->lvl_word, &st->status, &st->cnt3[(L + 1) % 3], &st->edg3[(L + 1) % 3],
-                       &f, &e, (stall == STALL_LEVEL_BARRIER && L == 0) ? 1u : 0u);
+    ok = level_arrive_wait(&st->tail3[(L + 1) % 3], &st->edg3[(L + 1) % 3], e_block, &st->status, &f, &e,
+                           (stall == STALL_LEVEL_BARRIER && L == 0) ? 1u : 0u);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->levels = L;
@@ -1395,13 +1541,17 @@ __global__ void k_tr_scatter(const int32_t* off, const int32_t* idx, int32_t n, 
 // visited changes no depth; pull then skips it, and skips whole words of them.
 // (A vertex with out-edges only must stay clear: pull would take its set bit
 // for a frontier in-neighbour.) Bits past n stay clear.
-__global__ void k_vis_init(const int32_t* off, const int32_t* in_off, int32_t n, int32_t words, uint32_t* vis_init) {
+__global__ void k_vis_init(const int32_t* off, const int32_t* in_off, int32_t n, int32_t words, uint32_t* vis_init,
+                           unsigned int* isolated_count) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < (int64_t)words * 32; v += stride) {
     // 32 consecutive threads share one word; every lane of a warp runs the same trips
     const bool isolated = v < n && off[v + 1] == off[v] && in_off[v + 1] == in_off[v];
     const uint32_t word = __ballot_sync(kFull, isolated);
-    if ((v & 31) == 0) vis_init[v >> 5] = word;
+    if ((v & 31) == 0) {
+      vis_init[v >> 5] = word;
+      if (word) atomicAdd(isolated_count, (unsigned)__popc(word));
+    }
   }
 }
 

@@ -11,9 +11,19 @@
 //         frontier masks, stopping once every unvisited lane is found.
 // Push and commit touch only the frontier and its neighbours (so thousands of
 // small levels stay cheap); pull sweeps every vertex, a warp per 32
-// consecutive vertices, so each root's new depths are written as coalesced row
-// segments. The result equals k independent single-source traversals (each
-// lane is one level-synchronous BFS from its root, Section 3.1).
+// consecutive vertices. The result equals k independent single-source
+// traversals (each lane is one level-synchronous BFS from its root, Section
+// 3.1).
+//
+// Output. A depth found at a level is not written to the k x n output then:
+// each output sector holds 8 vertices of one root, which would be filled piece
+// by piece over several levels (and, being far larger than L2, read back and
+// merged each time). Instead each vertex keeps a 4-bit code per root in a
+// 32-byte block (0: not reached, d + 1: depth d <= 13, 15: deeper), updated
+// whole by the one lane that owns the vertex at that level (the pull lane, or
+// the commit lane of a touched vertex), and a final pass writes every output
+// sector once, -1 included. Depths beyond 13 (high-diameter graphs) are
+// written when found and their code 15 tells the final pass to leave them.
 //
 // Level L uses frontier slot L % 4 (ftail, fedges), appends to (L + 1) % 4 and
 // clears (L + 2) % 4, which every block finished reading two levels ago; the
@@ -34,22 +44,39 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
   return x;
 }
 
-// Depth rows of a warp's 32 consecutive vertices (u = w * 32 + lane) newly
-// reached in lanes nb: one coalesced masked store per root present.
-__device__ __forceinline__ void ms_depth_rows(int32_t* depth, int64_t n, int64_t u, bool valid, unsigned long long nb,
-                                              int32_t d) {
-  unsigned long long any = warp_or64(valid ? nb : 0ull);
-  while (any) {
-    const int i = __ffsll((long long)any) - 1;
-    any &= any - 1;
-    if (valid && ((nb >> i) & 1ull)) depth[(int64_t)i * n + u] = d;
-  }
+// Bit k of b (k < 16) moved to bit 4k: a nibble of 1 for every set bit.
+__device__ __forceinline__ unsigned long long nibble_spread16(unsigned long long b) {
+  b &= 0xffffull;
+  b = (b | (b << 24)) & 0x000000ff000000ffull;
+  b = (b | (b << 12)) & 0x000f000f000f000full;
+  b = (b | (b << 6)) & 0x0303030303030303ull;
+  b = (b | (b << 3)) & 0x1111111111111111ull;
+  return b;
+}
+
+// Record that vertex u was reached at depth d by the roots in nb: the lane
+// that owns u at this level reads its 32-byte code block, sets those roots'
+// nibbles and writes the whole block back (one full sector). Depths beyond
+// kMsCodeMaxDepth get code 15 and go to the output rows now.
+__device__ __forceinline__ void ms_record(const MsBuffers& mb, const MsRows& rows, int64_t u, unsigned long long nb,
+                                          int32_t d) {
+  const unsigned long long c = d <= kMsCodeMaxDepth ? (unsigned long long)(d + 1) : 15ull;
+  ulonglong2* p = reinterpret_cast<ulonglong2*>(mb.codes + 4 * u);
+  ulonglong2 lo = p[0], hi = p[1];
+  lo.x |= nibble_spread16(nb) * c;
+  lo.y |= nibble_spread16(nb >> 16) * c;
+  hi.x |= nibble_spread16(nb >> 32) * c;
+  hi.y |= nibble_spread16(nb >> 48) * c;
+  p[0] = lo;
+  p[1] = hi;
+  if (d > kMsCodeMaxDepth)
+    for (unsigned long long m = nb; m; m &= m - 1) rows.row[__ffsll((long long)m) - 1][u] = d;
 }
 
 }  // namespace
 
 __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, MsState* st, int32_t k,
-                                                       int32_t* depth, MsConfig cfg, int32_t stall) {
+                                                       MsRows rows, MsConfig cfg, int32_t stall) {
   __shared__ unsigned long long s_edges[64];
   __shared__ int32_t s_big[kMsThreads];
   __shared__ int s_nbig;
@@ -62,36 +89,31 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
   const int wib = threadIdx.x >> 5;
   constexpr int kWarps = kMsThreads / 32;
   for (int i = threadIdx.x; i < 64; i += blockDim.x) s_edges[i] = 0;
-  // init: masks cleared, depth rows -1 (16-byte stores when aligned)
+  // init: masks and codes cleared (the output rows are written once, at the end)
   for (int64_t v = tid; v < n; v += stride) {
     mb.visit[v] = 0;
     mb.front[0][v] = 0;
     mb.front[1][v] = 0;
     mb.next[v] = 0;
+    ulonglong2* c = reinterpret_cast<ulonglong2*>(mb.codes + 4 * v);
+    c[0] = make_ulonglong2(0ull, 0ull);
+    c[1] = make_ulonglong2(0ull, 0ull);
   }
-  const int64_t total = n * k;
-  if ((reinterpret_cast<uintptr_t>(depth) & 15u) == 0) {
-    int4* d4 = reinterpret_cast<int4*>(depth);
-    const int64_t t4 = total >> 2;
-    for (int64_t i = tid; i < t4; i += stride) d4[i] = make_int4(-1, -1, -1, -1);
-    for (int64_t i = (t4 << 2) + tid; i < total; i += stride) depth[i] = -1;
-  } else {
-    for (int64_t i = tid; i < total; i += stride) depth[i] = -1;
-  }
-  if (!grid_barrier(&st->bar_count, &st->bar_gen, &st->status, stall == STALL_GRID_BARRIER ? 1u : 0u)) return;
+  unsigned long long bar_target = 0;  // this block's copy of the barriers' arrival target
+  if (!grid_arrive_wait(&st->bar64, bar_target, &st->status, stall == STALL_GRID_BARRIER ? 1u : 0u)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     // roots: the level 0 frontier; a vertex repeated as several roots carries several bits
     unsigned int fc = 0;
     unsigned long long fe = 0;
     for (int i = 0; i < k; ++i) {
-      const int32_t r = mb.roots[i];
+      const int32_t r = rows.root[i];
       if (mb.visit[r] == 0) {
         mb.flist[0][fc++] = r;
         fe += (unsigned long long)(g.off[r + 1] - g.off[r]);
       }
       mb.visit[r] |= 1ull << i;
       mb.front[0][r] |= 1ull << i;
-      depth[(int64_t)i * n + r] = 0;
+      mb.codes[4 * (int64_t)r + (i >> 4)] |= 1ull << (4 * (i & 15));  // code 1: depth 0
     }
     for (int i = 0; i < 64; ++i) st->edges[i] = 0;
     for (int s = 0; s < 4; ++s) {
@@ -102,7 +124,7 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
     st->fedges[0] = fe;
     st->ttail[0] = st->ttail[1] = 0;
   }
-  bool ok = grid_barrier(&st->bar_count, &st->bar_gen, &st->status);
+  bool ok = grid_arrive_wait(&st->bar64, bar_target, &st->status);
   const int64_t words = (n + 31) / 32;
   int32_t L = 0;
   for (; ok; ++L) {
@@ -184,7 +206,7 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
         }
       }
       stage_drain(stage, mb.tlist, ttail, 1);
-      ok = grid_barrier(&st->bar_count, &st->bar_gen, &st->status);
+      ok = grid_arrive_wait(&st->bar64, bar_target, &st->status);
       if (!ok) break;
       // commit the touched vertices: next -> new frontier, depths, next frontier list
       const unsigned int t = *reinterpret_cast<volatile unsigned int*>(ttail);
@@ -199,7 +221,7 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
           if (nb) {
             my_fe += (unsigned long long)(g.off[u + 1] - g.off[u]);
             stage_put(stage, out_list, out_tail, u);
-            for (unsigned long long m = nb; m; m &= m - 1) depth[(int64_t)(__ffsll((long long)m) - 1) * n + u] = L + 1;
+            ms_record(mb, rows, u, nb, L + 1);
           }
         }
         stage_drain(stage, out_list, out_tail, kStageCap / 2);
@@ -229,25 +251,41 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
               mb.visit[u] = vis | nb;
               my_fe += (unsigned long long)(g.off[u + 1] - g.off[u]);
               stage_put(stage, out_list, out_tail, (int32_t)u);
+              ms_record(mb, rows, u, nb, L + 1);
             }
           }
           nxt[u] = nb;
         }
-        if (w < words) ms_depth_rows(depth, n, u, valid, nb, L + 1);
         stage_drain(stage, out_list, out_tail, kStageCap - kMsThreads);
       }
     }
     stage_drain(stage, out_list, out_tail, 1);
     block_add_u64(my_fe, &st->fedges[(L + 1) % 4]);
-    ok = grid_barrier(&st->bar_count, &st->bar_gen, &st->status);
+    ok = grid_arrive_wait(&st->bar64, bar_target, &st->status);
   }
-  // per-root reached-edge counts: for each root, the sum of out-degrees of the
-  // vertices whose visit mask carries its bit
+  // Final pass, a warp per 32 consecutive vertices: every output sector written
+  // once from the codes (coalesced 128-byte row segments, one per root), and
+  // the per-root reached-edge counts: for each root, the sum of out-degrees of
+  // the vertices whose visit mask carries its bit. (The loop ended right after
+  // a grid barrier, so every block's codes are visible.)
   for (int64_t wbase = (int64_t)blockIdx.x * kWarps; wbase < words; wbase += (int64_t)gridDim.x * kWarps) {
     const int64_t w = wbase + wib;
     if (w >= words) continue;  // whole warp
     const int64_t u = w * 32 + lane;
     const bool valid = u < n;
+    if (ok) {
+      ulonglong2 lo = make_ulonglong2(0ull, 0ull), hi = make_ulonglong2(0ull, 0ull);
+      if (valid) {
+        const ulonglong2* c = reinterpret_cast<const ulonglong2*>(mb.codes + 4 * u);
+        lo = c[0];
+        hi = c[1];
+      }
+      for (int i = 0; i < k; ++i) {
+        const unsigned long long word = i < 16 ? lo.x : i < 32 ? lo.y : i < 48 ? hi.x : hi.y;
+        const unsigned int code = (unsigned int)(word >> (4 * (i & 15))) & 15u;
+        if (valid && code != 15u) rows.row[i][u] = code == 0u ? -1 : (int32_t)code - 1;
+      }
+    }
     const unsigned long long vis = valid ? mb.visit[u] : 0ull;
     const unsigned deg = valid ? (unsigned)(g.off[u + 1] - g.off[u]) : 0u;
     unsigned long long any = warp_or64(vis);
@@ -266,7 +304,7 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
 
 __global__ void k_ms_reset(MsState* st) {
   st->status = ST_OK;
-  st->bar_count = 0;
+  st->bar64 = 0;
 }
 
 }  // namespace bfs

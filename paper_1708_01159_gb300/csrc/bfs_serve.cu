@@ -1,21 +1,24 @@
 // bfs_serve: a continuous-batching BFS server over graphs resident in HBM.
 //
 // A dispatcher thread owns the device side. Submissions enter a FIFO queue;
-// whenever an in-flight slot and the memory a query needs (its traversal
-// workspace, plus a depth buffer when the caller gives none) fit the budget,
-// the dispatcher admits it, first fit over the head of the queue, so a large
-// query waiting for memory does not block smaller ones behind it. Admitted
-// queries run on a pool of streams and overlap on the device; queued queries to
-// the same graph are merged into one multi-source wave (up to merge_batch
-// roots, one bit each in 64-bit masks). Completion is observed by polling a
-// CUDA event per admitted unit; latency runs from submission to that
-// observation. Queries run as persistent cooperative kernels whose block count
-// is chosen per graph from probe runs at registration (probe_shape), as is
-// whether its queued queries are merged into waves: a high-diameter graph (a
-// grid: thousands of latency-bound levels) runs narrow queries, many resident
-// at once; a wide, shallow one runs a block per SM or more. Each unit goes to
-// the stream with the fewest units in flight, so a short query never queues
-// behind a long one on a shared stream.
+// whenever an in-flight slot and the memory a unit needs fit the budget, the
+// dispatcher admits it, first fit over the head of the queue, so a large query
+// waiting for memory does not block smaller ones behind it. A unit is one
+// single-root traversal or a multi-source wave: when two or more queries to a
+// graph are queued and one of the graph's wave buffer sets is free, up to
+// merge_batch of them run as one wave (one bit per query in 64-bit masks), each
+// root's depths written straight into its query's buffer. Units run on a pool
+// of streams and overlap on the device; each goes to the stream with the fewest
+// units in flight. Completion is observed by polling a CUDA event per unit;
+// latency runs from submission to that observation.
+//
+// Everything the dispatcher hands out is allocated when a graph is registered
+// (bfs_serve_add_graph): traversal workspaces for single queries, n-entry depth
+// buffers for queries submitted without one, and the wave buffer sets. A unit
+// that finds its pool empty waits in the queue; the dispatcher itself never
+// allocates device memory. Registration also probes the graph's launch shape:
+// the block count of its single queries, and whether waves are cheaper per
+// query than single runs (merge_policy 0 merges only then).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -48,16 +51,37 @@ struct TicketInfo {
   int32_t status;  // bfs_status once done
 };
 
+constexpr int kMaxRoots = 64;
+constexpr int kStatusSlot = kMaxRoots;  // pinned slot receiving the unit's device status word
+
 struct Unit {  // one admitted launch: a single query or a merged wave
   std::vector<Request> reqs;
+  std::vector<int32_t*> rows;     // output row of each request (caller's buffer or a pooled one)
+  std::vector<int32_t*> pooled;   // pooled depth buffers this unit holds
   int32_t graph_id = 0;
   int stream_index = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   long long bytes = 0;
-  int32_t* scratch = nullptr;  // server-owned depth buffer (single) or wave staging (k x n)
   bool wave = false;
-  long long* edges = nullptr;  // pinned: 64 slots
+  bfs::MsSet* set = nullptr;
+  long long* pinned = nullptr;  // kMaxRoots reached-edge slots, then the status slot
+};
+
+// A registered graph, its launch shape and its pools.
+struct GraphEntry {
+  bfs_graph* g = nullptr;
+  int32_t n = 0;
+  int32_t single_blocks = 0;  // blocks of a single query's persistent grid
+  int32_t wave_blocks = 0;    // blocks of a wave
+  bool merge = false;         // the probe found waves cheaper per query
+  bool waves = false;         // wave sets allocated: queued queries may merge
+  int32_t singles_max = 0;    // workspaces reserved for single queries
+  int32_t singles_inflight = 0;
+  long long single_bytes = 0;  // one traversal workspace
+  long long set_bytes = 0;     // one wave buffer set
+  std::vector<int32_t*> depth_all, depth_free;
+  std::vector<bfs::MsSet*> sets_all, sets_free;
 };
 
 }  // namespace
@@ -66,18 +90,11 @@ struct bfs_server {
   bfs_serve_config cfg{};
   int device = 0;
   int32_t sms = 0;
-  std::vector<bfs_graph*> graphs;
-  std::vector<int32_t> single_blocks;  // per graph: blocks of a single-query traversal
-  std::vector<char> merge_ok;          // per graph: queued queries may be merged into waves
-  std::vector<int32_t> wave_blocks;    // per graph: blocks of a merged wave
+  std::vector<GraphEntry> graphs;  // reserved to kMaxGraphs: entries never move
   std::vector<cudaStream_t> streams;
   std::vector<int> stream_units;  // units in flight per stream (dispatcher thread only)
   std::vector<cudaEvent_t> free_events;
   std::vector<long long*> free_pinned;
-  // per graph: free single-query depth buffers, and one wave staging buffer
-  std::vector<std::vector<int32_t*>> free_depth;
-  std::vector<int32_t*> wave_staging;
-  std::vector<char> wave_busy;
 
   std::mutex mu;
   std::condition_variable work_cv;  // dispatcher wake-up
@@ -110,6 +127,8 @@ constexpr float kLatencySlack = 4.0f;
 // single queries around it (a full-occupancy wave could only start on an idle
 // GPU and would hold all of it)
 constexpr int kWaveBlocksPerSm = 2;
+constexpr int32_t kSinglesPerGraph = 64;  // most workspaces reserved per graph for single queries
+constexpr int32_t kWaveSetsPerGraph = 2;  // waves of one graph that can run at once
 
 void finish_ticket(bfs_server* s, uint64_t t, int status) {
   auto it = s->tickets.find(t);
@@ -124,66 +143,110 @@ void finish_ticket(bfs_server* s, uint64_t t, int status) {
   }
 }
 
-long long unit_bytes(bfs_server* s, const Request& r, int k) {
-  bfs_graph* g = s->graphs[r.graph_id];
-  const long long n = bfs::graph_vertices(g);
-  if (k > 1) return 4 * n * k;  // wave staging (the mask buffers stay with the graph)
-  return bfs::workspace_bytes(g) + (r.depth_out ? 0 : 4 * n);
-}
-
 // Launch one unit (dispatcher thread, no lock held). Returns a bfs_status.
 int launch_unit(bfs_server* s, Unit& u) {
-  bfs_graph* g = s->graphs[u.graph_id];
-  const int64_t n = bfs::graph_vertices(g);
+  const GraphEntry& ge = s->graphs[u.graph_id];
+  int32_t* status_slot = reinterpret_cast<int32_t*>(&u.pinned[kStatusSlot]);
+  *status_slot = BFS_OK;
   if (!u.wave) {
-    Request& r = u.reqs[0];
-    int32_t* out = r.depth_out;
-    if (!out) {
-      auto& pool = s->free_depth[u.graph_id];
-      if (!pool.empty()) {
-        out = pool.back();
-        pool.pop_back();
-      } else if (cudaMalloc(&out, (size_t)n * 4) != cudaSuccess) {
-        cudaGetLastError();
-        return BFS_ERR_OOM;
-      }
-      u.scratch = out;
-    }
-    int rc = bfs::run_async(g, r.root, out, u.stream, BFS_MODE_PERSISTENT, u.edges, s->single_blocks[u.graph_id]);
+    const int rc = bfs::run_async(ge.g, u.reqs[0].root, u.rows[0], u.stream, BFS_MODE_PERSISTENT, u.pinned,
+                                  ge.single_blocks, status_slot);
     if (rc != BFS_OK) return rc;
   } else {
-    int32_t roots[64];
+    int32_t roots[kMaxRoots];
     const int k = (int)u.reqs.size();
     for (int i = 0; i < k; ++i) roots[i] = u.reqs[i].root;
-    int32_t* stage = s->wave_staging[u.graph_id];
-    if (!stage) {
-      if (cudaMalloc(&stage, (size_t)64 * n * 4) != cudaSuccess) {
-        cudaGetLastError();
-        return BFS_ERR_OOM;
-      }
-      s->wave_staging[u.graph_id] = stage;
-    }
-    u.scratch = stage;
-    int rc = bfs::batch_async(g, roots, k, stage, u.stream, reinterpret_cast<unsigned long long*>(u.edges),
-                              s->wave_blocks[u.graph_id]);
+    const int rc = bfs::batch_async(ge.g, u.set, roots, k, u.rows.data(), u.stream,
+                                    reinterpret_cast<unsigned long long*>(u.pinned), ge.wave_blocks, status_slot);
     if (rc != BFS_OK) return rc;
-    for (int i = 0; i < k; ++i)
-      if (u.reqs[i].depth_out &&
-          cudaMemcpyAsync(u.reqs[i].depth_out, stage + (size_t)i * n, (size_t)n * 4, cudaMemcpyDeviceToDevice,
-                          u.stream) != cudaSuccess)
-        return BFS_ERR_CUDA;
   }
   if (cudaEventRecord(u.done, u.stream) != cudaSuccess) return BFS_ERR_CUDA;
   return BFS_OK;
 }
 
+// Return a unit's resources (with s->mu held).
 void release_unit(bfs_server* s, Unit& u) {
+  GraphEntry& ge = s->graphs[u.graph_id];
   s->stream_units[u.stream_index] -= 1;
-  if (!u.wave && u.scratch) s->free_depth[u.graph_id].push_back(u.scratch);
-  if (u.wave) s->wave_busy[u.graph_id] = 0;
+  for (int32_t* p : u.pooled) ge.depth_free.push_back(p);
+  if (u.wave)
+    ge.sets_free.push_back(u.set);
+  else
+    ge.singles_inflight -= 1;
   s->free_events.push_back(u.done);
-  s->free_pinned.push_back(u.edges);
+  s->free_pinned.push_back(u.pinned);
   s->bytes_inflight -= u.bytes;
+}
+
+// Try to form a unit from the request at `it` (with s->mu held): a wave of up
+// to merge_batch queued queries of its graph when a set is free and more than
+// one can join, else a single query. False when the pools or the memory budget
+// do not allow it now.
+bool admit(bfs_server* s, std::list<Request>::iterator& it, bool idle, Unit* u) {
+  const int gid = it->graph_id;
+  GraphEntry& ge = s->graphs[gid];
+  const long long n4 = 4ll * ge.n;
+  // candidates for a wave: queued queries of this graph from `it` on; those
+  // without an output buffer need a pooled one
+  std::vector<std::list<Request>::iterator> pick;
+  // a graph whose queries merge waits for a free set rather than starting a
+  // single run (the next wave takes every query queued by then); with a set
+  // free, a lone query runs single (lower latency than a wave of one)
+  if (ge.waves && ge.sets_free.empty()) return false;
+  if (ge.waves) {
+    size_t bufs = 0;
+    const int kmax = std::min(s->cfg.merge_batch, kMaxRoots);
+    for (auto jt = it; jt != s->queue.end() && (int)pick.size() < kmax; ++jt) {
+      if (jt->graph_id != gid) continue;
+      if (!jt->depth_out) {
+        if (bufs == ge.depth_free.size()) {
+          if (jt == it) break;  // the head query itself cannot join: no wave starts here
+          continue;
+        }
+        ++bufs;
+      }
+      pick.push_back(jt);
+    }
+    if (pick.size() < 2) pick.clear();
+  }
+  long long need = 0;
+  if (!pick.empty()) {
+    need = ge.set_bytes;
+    for (auto& jt : pick)
+      if (!jt->depth_out) need += n4;
+  } else {
+    if (ge.singles_inflight >= ge.singles_max) return false;
+    if (!it->depth_out && ge.depth_free.empty()) return false;
+    pick.push_back(it);
+    need = ge.single_bytes + (it->depth_out ? 0 : n4);
+  }
+  if (s->cfg.mem_budget_bytes > 0 && s->bytes_inflight + need > s->cfg.mem_budget_bytes && !idle) return false;
+  u->graph_id = gid;
+  u->wave = pick.size() > 1;
+  u->bytes = need;
+  if (u->wave) {
+    u->set = ge.sets_free.back();
+    ge.sets_free.pop_back();
+  } else {
+    ge.singles_inflight += 1;
+  }
+  for (auto& jt : pick) {
+    int32_t* row = jt->depth_out;
+    if (!row) {
+      row = ge.depth_free.back();
+      ge.depth_free.pop_back();
+      u->pooled.push_back(row);
+    }
+    u->rows.push_back(row);
+    u->reqs.push_back(*jt);
+  }
+  // erase the picked entries (pick[0] is `it`); `it` moves to the first entry
+  // after it that was not picked
+  for (size_t q = pick.size(); q-- > 1;) s->queue.erase(pick[q]);
+  auto next = std::next(it);
+  s->queue.erase(it);
+  it = next;
+  return true;
 }
 
 void dispatcher(bfs_server* s) {
@@ -203,25 +266,26 @@ void dispatcher(bfs_server* s) {
       const auto now = Clock::now();
       Unit u = std::move(inflight[i]);
       inflight.erase(inflight.begin() + (long)i);
+      const int32_t dev_status = *reinterpret_cast<const int32_t*>(&u.pinned[kStatusSlot]);
+      const int status = e != cudaSuccess ? BFS_ERR_CUDA : dev_status != BFS_OK ? BFS_ERR_TIMEOUT : BFS_OK;
       std::lock_guard<std::mutex> lk(s->mu);
       for (size_t q = 0; q < u.reqs.size(); ++q) {
         const Request& r = u.reqs[q];
-        if (e == cudaSuccess) {
+        if (status == BFS_OK) {
           s->completed += 1;
           s->latency_ms.push_back(std::chrono::duration<double, std::milli>(now - r.t_submit).count());
-          s->edges_half += (double)u.edges[u.wave ? q : 0] / 2.0;
-          finish_ticket(s, r.ticket, BFS_OK);
+          s->edges_half += (double)u.pinned[u.wave ? q : 0] / 2.0;
         } else {
           s->failed += 1;
-          finish_ticket(s, r.ticket, BFS_ERR_CUDA);
         }
+        finish_ticket(s, r.ticket, status);
       }
       s->t_last = now;
       release_unit(s, u);
       progressed = true;
     }
     if (progressed) s->done_cv.notify_all();
-    // 2) admissions (first fit over the head of the queue; same-graph merging)
+    // 2) admissions (first fit over the head of the queue)
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop) {
@@ -235,47 +299,21 @@ void dispatcher(bfs_server* s) {
       for (auto it = s->queue.begin(); it != s->queue.end() && scanned < kScanDepth;) {
         if ((int)(inflight.size() + to_launch.size()) >= s->cfg.max_inflight || s->free_events.empty()) break;
         ++scanned;
-        const int gid = it->graph_id;
-        int k = 1;
-        if (s->cfg.merge_batch > 1 && (s->merge_ok[gid] || s->cfg.merge_policy == 1) && !s->wave_busy[gid]) {
-          for (auto jt = std::next(it); jt != s->queue.end() && k < s->cfg.merge_batch; ++jt)
-            if (jt->graph_id == gid) ++k;
-        }
-        const long long need = unit_bytes(s, *it, k);
+        Unit u;
         const bool idle = inflight.empty() && to_launch.empty();
-        if (s->cfg.mem_budget_bytes > 0 && s->bytes_inflight + need > s->cfg.mem_budget_bytes && !idle) {
+        if (!admit(s, it, idle, &u)) {
           ++it;  // does not fit now: try the next one (a query larger than the budget runs alone)
           continue;
         }
-        Unit u;
-        u.graph_id = gid;
-        u.wave = k > 1;
-        u.bytes = need;
         u.done = s->free_events.back();
         s->free_events.pop_back();
-        u.edges = s->free_pinned.back();
+        u.pinned = s->free_pinned.back();
         s->free_pinned.pop_back();
         u.stream_index = (int)(std::min_element(s->stream_units.begin(), s->stream_units.end()) -
                                s->stream_units.begin());
         u.stream = s->streams[u.stream_index];
         s->stream_units[u.stream_index] += 1;
-        u.reqs.push_back(*it);
-        it = s->queue.erase(it);  // list: erasing leaves the other iterators valid
-        if (u.wave) {
-          auto jt = it;
-          while (jt != s->queue.end() && (int)u.reqs.size() < k) {
-            if (jt->graph_id == gid) {
-              u.reqs.push_back(*jt);
-              const bool was_it = jt == it;
-              jt = s->queue.erase(jt);
-              if (was_it) it = jt;
-            } else {
-              ++jt;
-            }
-          }
-          s->wave_busy[gid] = 1;
-          s->waves += 1;
-        }
+        if (u.wave) s->waves += 1;
         const auto t_admit = Clock::now();
         for (const Request& r : u.reqs) {
           auto t = s->tickets.find(r.ticket);
@@ -283,7 +321,7 @@ void dispatcher(bfs_server* s) {
           s->wait_ms.push_back(std::chrono::duration<double, std::milli>(t_admit - r.t_submit).count());
         }
         s->admitted += (int64_t)u.reqs.size();
-        s->bytes_inflight += need;
+        s->bytes_inflight += u.bytes;
         s->peak_bytes = std::max(s->peak_bytes, s->bytes_inflight);
         to_launch.push_back(std::move(u));
       }
@@ -317,15 +355,14 @@ void dispatcher(bfs_server* s) {
 // (synchronous, on a private stream):
 //  1. traversals from up to four spread vertices (0, n/3, 2n/3, n-1); the one
 //     reaching the most edges is the probe root;
-//  2. that traversal timed on 8, 16, 32, 64 blocks, one per SM and a full
-//     occupancy wave: a query gets the block count that minimises blocks x time
-//     (the device share it holds) among those within kLatencySlack of the
-//     fastest, so latency-bound graphs run narrow and many of their queries
-//     share the GPU;
+//  2. that traversal timed on 8, 16, 32, 64 blocks, one and two per SM and a
+//     full occupancy wave: a query gets the block count that minimises
+//     blocks x time (the device share it holds) among those within
+//     kLatencySlack of the fastest, so latency-bound graphs run narrow and
+//     many of their queries share the GPU;
 //  3. one multi-source wave from 64 vertices the probe reached, on the grid
-//     waves get (at most kWaveBlocksPerSm blocks per SM): same-graph queries
-//     are merged into waves only when a wave's blocks x time per root is below
-//     a single query's.
+//     waves get (at most kWaveBlocksPerSm blocks per SM): waves are cheaper
+//     when their blocks x time per root is below a single query's.
 struct Shape {
   int32_t single_blocks = 0;
   int32_t wave_blocks = 0;
@@ -344,11 +381,14 @@ int probe_shape(bfs_server* s, bfs_graph* g, Shape* out) {
   }
   int32_t* depth = nullptr;
   int32_t* wave_out = nullptr;
+  bfs::MsSet* set = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = BFS_OK;
   if (cudaMalloc(&depth, (size_t)n * 4) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
-      cudaEventCreate(&e1) != cudaSuccess)
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
     rc = bfs::set_error_detail(BFS_ERR_OOM, "probe buffers");
+  }
   // 1. probe root
   int32_t root = 0;
   long long best_e = -1;
@@ -374,10 +414,10 @@ int probe_shape(bfs_server* s, bfs_graph* g, Shape* out) {
       return BFS_ERR_CUDA;
     return BFS_OK;
   };
-  const int32_t sizes[6] = {8, 16, 32, 64, s->sms, full};
-  float t[6] = {0, 0, 0, 0, 0, 0};
+  const int32_t sizes[7] = {8, 16, 32, 64, s->sms, 2 * s->sms, full};
+  float t[7] = {0, 0, 0, 0, 0, 0, 0};
   float fastest = 1e30f;
-  for (int i = 0; i < 6 && rc == BFS_OK; ++i) {
+  for (int i = 0; i < 7 && rc == BFS_OK; ++i) {
     bfs_options opt{};
     opt.forced_variant = BFS_VARIANT_TREE;
     opt.mode = BFS_MODE_PERSISTENT;
@@ -388,7 +428,7 @@ int probe_shape(bfs_server* s, bfs_graph* g, Shape* out) {
   double single_cost = 0;
   if (rc == BFS_OK) {
     double best_cost = 1e300;
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 7; ++i) {
       const int32_t b = std::min(sizes[i], full);
       const double cost = (double)b * t[i];
       if (t[i] <= kLatencySlack * fastest && cost < best_cost) {
@@ -398,7 +438,8 @@ int probe_shape(bfs_server* s, bfs_graph* g, Shape* out) {
     }
     single_cost = best_cost;
   }
-  // 3. merge or not: a 64-root wave from vertices the probe reached
+  // 3. merge or not: a 64-root wave from vertices the probe reached (temporary
+  // buffers; a wave that does not fit only disables merging)
   if (rc == BFS_OK) {
     std::vector<int32_t> d((size_t)n);
     if (cudaMemcpy(d.data(), depth, (size_t)n * 4, cudaMemcpyDeviceToHost) != cudaSuccess) rc = BFS_ERR_CUDA;
@@ -407,21 +448,72 @@ int probe_shape(bfs_server* s, bfs_graph* g, Shape* out) {
       if (d[(size_t)v] >= 0) reached.push_back(v);
     const int32_t wg = std::min(bfs::wave_grid(g), kWaveBlocksPerSm * s->sms);
     out->wave_blocks = std::max(wg, 1);
-    if (rc == BFS_OK && wg > 0 && cudaMalloc(&wave_out, (size_t)64 * n * 4) == cudaSuccess) {
-      int32_t roots[64];
-      for (int i = 0; i < 64; ++i) roots[i] = reached[(size_t)i * reached.size() / 64];
+    if (rc == BFS_OK && wg > 0 && !reached.empty() && cudaMalloc(&wave_out, (size_t)kMaxRoots * n * 4) == cudaSuccess &&
+        bfs::ms_set_create(g, &set) == BFS_OK) {
+      int32_t roots[kMaxRoots];
+      int32_t* rows[kMaxRoots];
+      for (int i = 0; i < kMaxRoots; ++i) {
+        roots[i] = reached[(size_t)i * reached.size() / kMaxRoots];
+        rows[i] = wave_out + (size_t)i * n;
+      }
       float wave_ms = 0;
-      rc = timed([&] { return bfs::batch_async(g, roots, 64, wave_out, stream, nullptr, wg); }, &wave_ms);
-      if (rc == BFS_OK) out->merge = (double)wg * wave_ms / 64.0 < single_cost;
+      rc = timed([&] { return bfs::batch_async(g, set, roots, kMaxRoots, rows, stream, nullptr, wg, nullptr); },
+                 &wave_ms);
+      if (rc == BFS_OK) out->merge = (double)wg * wave_ms / kMaxRoots < single_cost;
     }
-    cudaGetLastError();  // a wave buffer that did not fit only disables merging
+    cudaGetLastError();
   }
+  bfs::ms_set_free(set);
   if (wave_out) cudaFree(wave_out);
   if (depth) cudaFree(depth);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamDestroy(stream);
   return rc;
+}
+
+void free_pools(GraphEntry& ge) {
+  for (int32_t* p : ge.depth_all) cudaFree(p);
+  for (bfs::MsSet* set : ge.sets_all) bfs::ms_set_free(set);
+  ge.depth_all.clear();
+  ge.depth_free.clear();
+  ge.sets_all.clear();
+  ge.sets_free.clear();
+}
+
+// The pools a graph's units draw from, allocated once at registration.
+int make_pools(bfs_server* s, GraphEntry& ge) {
+  // as many single queries as the slots allow, up to the pool limit, and no
+  // more than the memory budget could admit at once
+  long long cap = std::min<int32_t>(s->cfg.max_inflight, kSinglesPerGraph);
+  if (s->cfg.mem_budget_bytes > 0) cap = std::min(cap, s->cfg.mem_budget_bytes / std::max(1ll, ge.single_bytes));
+  ge.singles_max = (int32_t)std::max(1ll, cap);
+  ge.waves = s->cfg.merge_batch > 1 && (ge.merge || s->cfg.merge_policy == 1);
+  int rc = bfs::reserve_workspaces(ge.g, ge.singles_max);
+  if (rc != BFS_OK) return rc;
+  const int sets = ge.waves ? kWaveSetsPerGraph : 0;
+  const int bufs = ge.singles_max + sets * std::min(s->cfg.merge_batch, kMaxRoots);
+  for (int i = 0; i < bufs; ++i) {
+    int32_t* p = nullptr;
+    if (cudaMalloc(&p, (size_t)ge.n * 4) != cudaSuccess) {
+      cudaGetLastError();
+      free_pools(ge);
+      return bfs::set_error_detail(BFS_ERR_OOM, "depth buffer pool");
+    }
+    ge.depth_all.push_back(p);
+  }
+  for (int i = 0; i < sets; ++i) {
+    bfs::MsSet* set = nullptr;
+    rc = bfs::ms_set_create(ge.g, &set);
+    if (rc != BFS_OK) {
+      free_pools(ge);
+      return rc;
+    }
+    ge.sets_all.push_back(set);
+  }
+  ge.depth_free = ge.depth_all;
+  ge.sets_free = ge.sets_all;
+  return BFS_OK;
 }
 
 }  // namespace
@@ -436,15 +528,9 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out) {
     return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "serve config out of range");
   auto* s = new bfs_server;
   s->cfg = *cfg;
-  // graphs are registered while the dispatcher runs: fixed capacity, so these
-  // vectors never reallocate under it
+  // graphs are registered while the dispatcher runs: fixed capacity, so the
+  // entries never move under it
   s->graphs.reserve(kMaxGraphs);
-  s->single_blocks.reserve(kMaxGraphs);
-  s->merge_ok.reserve(kMaxGraphs);
-  s->wave_blocks.reserve(kMaxGraphs);
-  s->free_depth.reserve(kMaxGraphs);
-  s->wave_staging.reserve(kMaxGraphs);
-  s->wave_busy.reserve(kMaxGraphs);
   if (cudaGetDevice(&s->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
     delete s;
@@ -460,7 +546,7 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out) {
     cudaEvent_t e;
     long long* p = nullptr;
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) break;
-    if (cudaMallocHost(&p, 64 * sizeof(long long)) != cudaSuccess) {
+    if (cudaMallocHost(&p, (kMaxRoots + 1) * sizeof(long long)) != cudaSuccess) {
       cudaEventDestroy(e);
       break;
     }
@@ -484,18 +570,29 @@ int bfs_serve_add_graph(bfs_server_t s, bfs_graph_t g, int32_t* graph_id) {
   if (!s || !g || !graph_id) return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "null argument");
   if (bfs::graph_device(g) != s->device)
     return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "graph lives on another device");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->graphs.size() >= kMaxGraphs) return bfs::set_error_detail(BFS_ERR_BUSY, "too many graphs (256)");
+  }
   Shape shape;
-  const int rc = probe_shape(s, g, &shape);
+  int rc = probe_shape(s, g, &shape);
+  if (rc != BFS_OK) return rc;
+  GraphEntry ge;
+  ge.g = g;
+  ge.n = bfs::graph_vertices(g);
+  ge.single_blocks = shape.single_blocks;
+  ge.wave_blocks = shape.wave_blocks;
+  ge.merge = shape.merge;
+  ge.single_bytes = bfs::workspace_bytes(g);
+  ge.set_bytes = bfs::ms_set_bytes(g);
+  rc = make_pools(s, ge);
   if (rc != BFS_OK) return rc;
   std::lock_guard<std::mutex> lk(s->mu);
-  if (s->graphs.size() >= kMaxGraphs) return bfs::set_error_detail(BFS_ERR_BUSY, "too many graphs (256)");
-  s->graphs.push_back(g);
-  s->single_blocks.push_back(shape.single_blocks);
-  s->merge_ok.push_back(shape.merge ? 1 : 0);
-  s->wave_blocks.push_back(shape.wave_blocks);
-  s->free_depth.emplace_back();
-  s->wave_staging.push_back(nullptr);
-  s->wave_busy.push_back(0);
+  if (s->graphs.size() >= kMaxGraphs) {
+    free_pools(ge);
+    return bfs::set_error_detail(BFS_ERR_BUSY, "too many graphs (256)");
+  }
+  s->graphs.push_back(std::move(ge));
   *graph_id = (int32_t)s->graphs.size() - 1;
   return BFS_OK;
 }
@@ -505,8 +602,8 @@ int bfs_serve_graph_shape(bfs_server_t s, int32_t graph_id, int32_t* query_block
   std::lock_guard<std::mutex> lk(s->mu);
   if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size())
     return bfs::set_error_detail(BFS_ERR_NOT_FOUND, "unknown graph id");
-  *query_blocks = s->single_blocks[graph_id];
-  *merges = s->merge_ok[graph_id];
+  *query_blocks = s->graphs[graph_id].single_blocks;
+  *merges = s->graphs[graph_id].merge ? 1 : 0;
   return BFS_OK;
 }
 
@@ -515,9 +612,8 @@ int bfs_serve_query_bytes(bfs_server_t s, int32_t graph_id, int32_t with_output,
   std::lock_guard<std::mutex> lk(s->mu);
   if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size())
     return bfs::set_error_detail(BFS_ERR_NOT_FOUND, "unknown graph id");
-  static int32_t dummy;
-  const Request r{0, graph_id, 0, with_output ? &dummy : nullptr, Clock::now()};
-  *bytes = unit_bytes(s, r, 1);
+  const GraphEntry& ge = s->graphs[graph_id];
+  *bytes = ge.single_bytes + (with_output ? 0 : 4ll * ge.n);
   return BFS_OK;
 }
 
@@ -526,7 +622,7 @@ int bfs_serve_submit(bfs_server_t s, int32_t graph_id, int32_t root, int32_t* de
   std::lock_guard<std::mutex> lk(s->mu);
   if (graph_id < 0 || graph_id >= (int32_t)s->graphs.size())
     return bfs::set_error_detail(BFS_ERR_NOT_FOUND, "unknown graph id");
-  if (root < 0 || root >= bfs::graph_vertices(s->graphs[graph_id]))
+  if (root < 0 || root >= s->graphs[graph_id].n)
     return bfs::set_error_detail(BFS_ERR_INVALID_ARG, "root out of range");
   if (s->stop) return bfs::set_error_detail(BFS_ERR_CANCELLED, "server is shutting down");
   if ((int)s->queue.size() >= s->cfg.queue_capacity) {
@@ -640,10 +736,7 @@ int bfs_serve_destroy(bfs_server_t s) {
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   for (cudaEvent_t e : s->free_events) cudaEventDestroy(e);
   for (long long* p : s->free_pinned) cudaFreeHost(p);
-  for (auto& pool : s->free_depth)
-    for (int32_t* p : pool) cudaFree(p);
-  for (int32_t* p : s->wave_staging)
-    if (p) cudaFree(p);
+  for (GraphEntry& ge : s->graphs) free_pools(ge);
   delete s;
   return BFS_OK;
 }
