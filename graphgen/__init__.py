@@ -127,10 +127,12 @@ def splitmix64_at(state: int, k: int) -> int:
 
 
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
-         seed: int = SEED_GRAPH, permute: bool = False) -> Graph:
-    """R-MAT graph with 2^scale vertices and edge_factor * 2^scale generated edges."""
-    ptr = _load().gg_rmat(scale, edge_factor, a, b, c, seed, int(permute))
-    return _take(ptr, f"rmat-s{scale}-ef{edge_factor}-seed{seed}{'-perm' if permute else ''}")
+         seed: int = SEED_GRAPH, permute: bool = False, directed: bool = False) -> Graph:
+    """R-MAT graph with 2^scale vertices and edge_factor * 2^scale generated edges
+    (directed: each generated edge kept in its direction, not symmetrised)."""
+    ptr = _load().gg_rmat(scale, edge_factor, a, b, c, seed, int(permute) | (int(directed) << 1))
+    return _take(ptr, f"rmat-s{scale}-ef{edge_factor}-seed{seed}{'-perm' if permute else ''}"
+                      f"{'-dir' if directed else ''}")
 
 
 def grid(rows: int, cols: int, drop: float = 0.1, seed: int = SEED_GRAPH, permute: bool = True) -> Graph:

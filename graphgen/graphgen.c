@@ -19,7 +19,7 @@
  *   Erdos-Renyi G(n, p): geometric skipping over vertex pairs (Batagelj and
  *     Brandes, "Efficient generation of large random networks", Phys. Rev. E
  *     71, 2005).
- * Every generator symmetrises, drops self-loops and duplicates, and sorts each
+ * Every generator symmetrises (R-MAT optionally not), drops self-loops and duplicates, and sorts each
  * adjacency list ascending.
  */
 #include <math.h>
@@ -203,8 +203,12 @@ static void gg_apply_perm(int64_t e, int32_t* src, int32_t* dst, const int32_t* 
   }
 }
 
-/* R-MAT with quadrant probabilities a, b, c and d = 1 - a - b - c. */
-gg_csr* gg_rmat(int scale, int64_t edge_factor, double a, double b, double c, uint64_t seed, int permute) {
+/* R-MAT with quadrant probabilities a, b, c and d = 1 - a - b - c. flags: bit 0
+ * permutes the vertex ids; bit 1 keeps each generated edge's direction (no
+ * symmetrisation: a directed graph, whose in- and out-degree distributions
+ * differ when b != c). */
+gg_csr* gg_rmat(int scale, int64_t edge_factor, double a, double b, double c, uint64_t seed, int flags) {
+  const int permute = flags & 1, symmetrize = !(flags & 2);
   if (scale < 1 || scale > 30 || edge_factor < 0) return NULL;
   int64_t n = (int64_t)1 << scale;
   int64_t e = edge_factor * n;
@@ -252,7 +256,7 @@ gg_csr* gg_rmat(int scale, int64_t edge_factor, double a, double b, double c, ui
     gg_apply_perm(e, src, dst, perm);
     free(perm);
   }
-  gg_csr* g = gg_from_pairs(n, e, src, dst, 1);
+  gg_csr* g = gg_from_pairs(n, e, src, dst, symmetrize);
   free(src);
   free(dst);
   return g;

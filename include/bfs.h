@@ -80,11 +80,20 @@ enum bfs_graph_flags {
   BFS_VALIDATE = 4u,        /* accepted for clarity: the CSR is always validated on the device */
 };
 
-/* Feature vector layout of the decision tree (Section 4.1 features). */
+/* Feature vector layout of the decision tree (Section 4.1 features): graph
+ * size; the out-degree 5-number summary (nearest rank, sorted[floor(k (n-1) /
+ * 4)]) and floor(256 sd); the level's frontier and discovered counts (also in
+ * parts per million of n), the frontier's out-degree sum and the level index;
+ * then the in-degree and total-degree (in + out) summaries, Section 4.1's
+ * degree distribution of in-, out- or total degree (for a symmetric graph the
+ * in-degree summary equals the out-degree one). */
 enum bfs_feature {
   BFS_F_N = 0, BFS_F_M = 1, BFS_F_DEG_MIN = 2, BFS_F_DEG_Q1 = 3, BFS_F_DEG_MED = 4, BFS_F_DEG_Q3 = 5,
   BFS_F_DEG_MAX = 6, BFS_F_DEG_SD256 = 7, BFS_F_FRONTIER = 8, BFS_F_FRONTIER_PPM = 9, BFS_F_DISCOVERED = 10,
-  BFS_F_DISCOVERED_PPM = 11, BFS_F_FRONTIER_EDGES = 12, BFS_F_LEVEL = 13, BFS_NUM_FEATURES = 14,
+  BFS_F_DISCOVERED_PPM = 11, BFS_F_FRONTIER_EDGES = 12, BFS_F_LEVEL = 13,
+  BFS_F_IN_DEG_MIN = 14, BFS_F_IN_DEG_Q1 = 15, BFS_F_IN_DEG_MED = 16, BFS_F_IN_DEG_Q3 = 17, BFS_F_IN_DEG_MAX = 18,
+  BFS_F_IN_DEG_SD256 = 19, BFS_F_TOT_DEG_MIN = 20, BFS_F_TOT_DEG_Q1 = 21, BFS_F_TOT_DEG_MED = 22,
+  BFS_F_TOT_DEG_Q3 = 23, BFS_F_TOT_DEG_MAX = 24, BFS_F_TOT_DEG_SD256 = 25, BFS_NUM_FEATURES = 26,
 };
 
 typedef struct bfs_graph_info {
@@ -92,6 +101,10 @@ typedef struct bfs_graph_info {
   int64_t m;                 /* directed CSR entries */
   int64_t deg_summary[5];    /* out-degree min, Q1, median, Q3, max: sorted[floor(k (n-1) / 4)] */
   int64_t deg_sd256;         /* floor(256 * population standard deviation of out-degree) */
+  int64_t in_deg_summary[5]; /* the same for in-degree */
+  int64_t in_deg_sd256;
+  int64_t tot_deg_summary[5]; /* the same for total degree (in + out) */
+  int64_t tot_deg_sd256;
   int64_t bytes_resident;    /* device bytes held by the graph (CSR, transpose, stats) */
   int32_t symmetric;         /* 1 if pull reuses the CSR, 0 if a transpose was built */
   int32_t num_workspaces;    /* per-run workspaces currently allocated */
@@ -380,14 +393,19 @@ typedef struct bfs_level_profile {
 /*
  * Per-level timing harness (Section 4.1: the fastest implementation of every
  * level labels the training set). Runs the traversal from `root` level by level
- * with a host round trip per level; at each level it snapshots the state
- * (depths, visited bitmap, counters), runs every variant `reps` times from that
- * same snapshot, timing each run with CUDA events on `stream`, records the
- * median, restores the snapshot and advances with `advance_variant` (or the
- * tree's choice when BFS_VARIANT_TREE). out: host, `capacity` entries; levels
- * beyond it are traversed but not recorded. *num_levels: levels traversed.
- * Synchronous. Uses a private depth buffer (the graph's caller buffers are not
- * touched). Errors: BFS_ERR_INVALID_ARG, BFS_ERR_OOM, BFS_ERR_CUDA.
+ * with a host round trip per level; at each level every variant expands the
+ * level `reps` times from the same state, the state being restored after each
+ * run (the level's discoveries undone), the median time is recorded, and the
+ * traversal advances with `advance_variant` (or the tree's choice when
+ * BFS_VARIANT_TREE). Where the device supports cooperative launch, each run is
+ * one level of the persistent driver (the default driver): a cooperative
+ * launch of the same level code on the same grid, timed with device
+ * timestamps from its start barrier to the end of its level-ending barrier.
+ * Otherwise each run is the graph driver's kernels for the level, timed with
+ * CUDA events on `stream`. out: host, `capacity` entries; levels beyond it are
+ * traversed but not recorded. *num_levels: levels traversed. Synchronous. Uses
+ * a private depth buffer (the graph's caller buffers are not touched). Errors:
+ * BFS_ERR_INVALID_ARG, BFS_ERR_OOM, BFS_ERR_CUDA, BFS_ERR_TIMEOUT.
  */
 int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advance_variant, bfs_stream_t stream,
                        bfs_level_profile* out, int32_t capacity, int32_t* num_levels);

@@ -155,12 +155,15 @@ def bfs_batch(off: np.ndarray, idx: np.ndarray, roots: Sequence[int]):
 
 # Feature numbering. Section 4.1 lists graph size (vertices and edges), the
 # frontier size and the discovered count (absolute or as a share of the
-# vertices) and the out-degree 5-number summary with its standard deviation;
-# the level index and the frontier's edge count are kept alongside for the
-# extended feature sets.
+# vertices) and the degree distribution (5-number summary and standard
+# deviation) of in-, out- or total degree; the level index and the frontier's
+# edge count are kept alongside for the extended feature sets. The out-degree
+# summary comes first, the in-degree and total-degree summaries last.
 FEATURES = (
     "n", "m", "deg_min", "deg_q1", "deg_med", "deg_q3", "deg_max", "deg_sd256",
     "frontier", "frontier_ppm", "discovered", "discovered_ppm", "frontier_edges", "level",
+    "in_deg_min", "in_deg_q1", "in_deg_med", "in_deg_q3", "in_deg_max", "in_deg_sd256",
+    "tot_deg_min", "tot_deg_q1", "tot_deg_med", "tot_deg_q3", "tot_deg_max", "tot_deg_sd256",
 )
 F = {name: i for i, name in enumerate(FEATURES)}
 
@@ -172,15 +175,15 @@ V = {name: i for i, name in enumerate(VARIANTS)}
 LEVEL0_DEFAULT = V["push_edge"]
 
 
-def degree_stats(off: np.ndarray):
-    """Out-degree 5-number summary and floor(256 * population std) (Section 4.1).
+def degree_summary(deg) -> list:
+    """5-number summary and floor(256 * population std) of a degree sequence (Section 4.1).
 
     Quantile rule (the paper does not fix one): nearest rank on the sorted
     degrees, q_k = sorted[floor(k (n - 1) / 4)] for k = 0..4. The standard
     deviation is exact: floor(256 sigma) = isqrt(65536 (n S2 - S1^2)) // n with
     S1, S2 the sums of degrees and squared degrees.
     """
-    deg = np.diff(np.asarray(off, dtype=np.int64))
+    deg = np.asarray(deg, dtype=np.int64)
     n = int(deg.shape[0])
     s = np.sort(deg)
     q = [int(s[(k * (n - 1)) // 4]) for k in range(5)]
@@ -190,24 +193,40 @@ def degree_stats(off: np.ndarray):
     return q + [sd256]
 
 
-def level_features(off: np.ndarray, res: BFSResult):
+def degree_stats(off: np.ndarray):
+    """Out-degree summary: degree_summary of the row lengths."""
+    return degree_summary(np.diff(np.asarray(off, dtype=np.int64)))
+
+
+def in_degrees(off: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    """In-degree of every vertex: how many adjacency entries name it."""
+    n = int(np.asarray(off).shape[0] - 1)
+    return np.bincount(np.asarray(idx, dtype=np.int64), minlength=n)[:n].astype(np.int64)
+
+
+def level_features(off: np.ndarray, idx: np.ndarray, res: BFSResult):
     """One feature vector per BFS level L, describing the frontier being expanded.
 
     Section 4.1 features: graph size, frontier size, discovered count (absolute
     and in parts per million of the vertices, floor(1e6 * count / n)), the
-    out-degree summary. "Discovered" at level L counts every vertex of depth
-    <= L, i.e. including the frontier itself.
+    out-, in- and total-degree summaries. "Discovered" at level L counts every
+    vertex of depth <= L, i.e. including the frontier itself.
     """
-    n = int(np.asarray(off).shape[0] - 1)
-    m = int(np.asarray(off)[-1])
-    ds = degree_stats(off)
+    off = np.asarray(off, dtype=np.int64)
+    n = int(off.shape[0] - 1)
+    m = int(off[-1])
+    out_deg = np.diff(off)
+    in_deg = in_degrees(off, idx)
+    ds = degree_summary(out_deg)
+    ins = degree_summary(in_deg)
+    tot = degree_summary(out_deg + in_deg)
     rows = []
     disc = 0
     for L in range(res.num_levels):
         f = int(res.level_count[L])
         disc += f
         rows.append([n, m] + ds + [f, (1_000_000 * f) // n, disc, (1_000_000 * disc) // n,
-                                   int(res.level_edges[L]), L])
+                                   int(res.level_edges[L]), L] + ins + tot)
     return rows
 
 

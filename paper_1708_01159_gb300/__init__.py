@@ -56,7 +56,9 @@ NUM_FORCED_VARIANTS = len(FORCED_VARIANTS)
 # bfs_options.count_mode: how vertex push appends reached vertices (Section 3.1.4 comparison)
 COUNT_MODES = {"block": 0, "warp": 1, "atomic": 2}
 FEATURES = ("n", "m", "deg_min", "deg_q1", "deg_med", "deg_q3", "deg_max", "deg_sd256",
-            "frontier", "frontier_ppm", "discovered", "discovered_ppm", "frontier_edges", "level")
+            "frontier", "frontier_ppm", "discovered", "discovered_ppm", "frontier_edges", "level",
+            "in_deg_min", "in_deg_q1", "in_deg_med", "in_deg_q3", "in_deg_max", "in_deg_sd256",
+            "tot_deg_min", "tot_deg_q1", "tot_deg_med", "tot_deg_q3", "tot_deg_max", "tot_deg_sd256")
 NUM_FEATURES = len(FEATURES)
 
 
@@ -70,8 +72,9 @@ class BFSError(RuntimeError):
 
 class _GraphInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("deg_summary", ctypes.c_int64 * 5),
-                ("deg_sd256", ctypes.c_int64), ("bytes_resident", ctypes.c_int64), ("symmetric", ctypes.c_int32),
-                ("num_workspaces", ctypes.c_int32)]
+                ("deg_sd256", ctypes.c_int64), ("in_deg_summary", ctypes.c_int64 * 5), ("in_deg_sd256", ctypes.c_int64),
+                ("tot_deg_summary", ctypes.c_int64 * 5), ("tot_deg_sd256", ctypes.c_int64),
+                ("bytes_resident", ctypes.c_int64), ("symmetric", ctypes.c_int32), ("num_workspaces", ctypes.c_int32)]
 
 
 class _Options(ctypes.Structure):
@@ -240,6 +243,8 @@ def bfs_graph_info(g: int) -> dict:
     info = _GraphInfo()
     _check(lib().bfs_graph_info(g, ctypes.byref(info)), "bfs_graph_info")
     return {"n": info.n, "m": info.m, "deg_summary": list(info.deg_summary), "deg_sd256": info.deg_sd256,
+            "in_deg_summary": list(info.in_deg_summary), "in_deg_sd256": info.in_deg_sd256,
+            "tot_deg_summary": list(info.tot_deg_summary), "tot_deg_sd256": info.tot_deg_sd256,
             "bytes_resident": info.bytes_resident, "symmetric": bool(info.symmetric),
             "num_workspaces": info.num_workspaces}
 

@@ -192,6 +192,7 @@ constexpr int kMaxWorkspaces = 64;
 struct Shapes {
   int init, push_thread, push_warp, push_cta, pe, pull, edge_list;
   int persist;  // cooperative grid of the persistent kernel (0: not supported)
+  int profile;  // cooperative grid of the per-level timing kernel (the persistent grid when it fits)
 };
 
 }  // namespace
@@ -214,7 +215,9 @@ struct bfs_graph {
   std::vector<void*> allocs;
   size_t bytes = 0;
   bool symmetric = false;
-  long long stats6[6] = {0, 0, 0, 0, 0, 0};
+  long long stats6[6] = {0, 0, 0, 0, 0, 0};      // out-degree summary and floor(256 sd)
+  long long stats_in6[6] = {0, 0, 0, 0, 0, 0};   // in-degree
+  long long stats_tot6[6] = {0, 0, 0, 0, 0, 0};  // total degree
   Shapes shapes{};
   std::mutex mu;
   std::vector<Workspace*> pool;   // every workspace of the graph
@@ -517,7 +520,7 @@ bool build_qs(const std::vector<TreeNode>& t, const long long* gfeat, QsTree* q)
     hi[i] = hi[nd.r];
     unsigned long long m = ~0ull;
     for (int b = lo[nd.l]; b < hi[nd.l]; ++b) m &= ~(1ull << b);
-    if (nd.f < F_FRONTIER) {
+    if (is_graph_feature(nd.f)) {
       if (!(gfeat[nd.f] <= nd.t)) q->base &= m;
       return;
     }
@@ -884,6 +887,166 @@ int bfs::batch_async(bfs_graph* g, MsSet* set, const int32_t* roots, int32_t k, 
   return BFS_OK;
 }
 
+namespace {
+
+// The 5-number summary (nearest rank) and floor(256 sd) of the degrees of all
+// n vertices, on the device: the row lengths of `off`, plus those of `off2`
+// when given (in + out = total degree). Synchronous.
+int degree_summary(const int32_t* off, const int32_t* off2, int32_t n, int blocks, long long out6[6]) {
+  unsigned int* mm = nullptr;  // [0] min, [1] max
+  unsigned long long* sums = nullptr;
+  int32_t* hist = nullptr;
+  long long* st6 = nullptr;
+  unsigned int mm_h[2] = {0xffffffffu, 0u};
+  cudaError_t e = cudaMalloc(&mm, 8);
+  if (e == cudaSuccess) e = cudaMalloc(&sums, 16);
+  if (e == cudaSuccess) e = cudaMalloc(&st6, 6 * 8);
+  if (e == cudaSuccess) e = cudaMemcpy(mm, mm_h, 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(sums, 0, 16);
+  if (e == cudaSuccess) {
+    k_deg_reduce<<<blocks, kThreads>>>(off, off2, n, sums, sums + 1, mm, mm + 1);
+    e = cudaMemcpy(mm_h, mm, 8, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&hist, ((size_t)mm_h[1] + 1) * 4);
+  if (e == cudaSuccess) e = cudaMemset(hist, 0, ((size_t)mm_h[1] + 1) * 4);
+  if (e == cudaSuccess) {
+    k_deg_hist<<<blocks, kThreads>>>(off, off2, n, hist);
+    k_deg_finish<<<1, kThreads>>>(hist, (int64_t)mm_h[1], n, sums, sums + 1, st6);
+    e = cudaMemcpy(out6, st6, 6 * 8, cudaMemcpyDeviceToHost);
+  }
+  for (void* p : {(void*)mm, (void*)sums, (void*)hist, (void*)st6})
+    if (p) cudaFree(p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA, "degree statistics: %s",
+                cudaGetErrorString(e));
+  }
+  return BFS_OK;
+}
+
+// The tree's choice for a level on the host (the same walk and unknown-
+// prediction rule the device applies): features are exact integers, so every
+// test is x[f] <= t.
+int32_t host_tree_choice(const std::vector<TreeNode>& t, const long long* x, int32_t L, int32_t prev) {
+  int32_t i = 0, v = -1;
+  for (size_t step = 0; step <= t.size() && i >= 0 && i < (int32_t)t.size(); ++step) {
+    const TreeNode& nd = t[(size_t)i];
+    if (nd.f < 0) {
+      v = nd.v;
+      break;
+    }
+    i = x[nd.f] <= nd.t ? nd.l : nd.r;
+  }
+  if (v < 0 || v >= V_NUM) v = L == 0 ? kLevel0Default : prev;
+  if (v < 0 || v >= V_NUM) v = kLevel0Default;
+  return v;
+}
+
+// The timing harness in the persistent driver: every variant expands every
+// level from the same state in a cooperative launch of k_profile_level (device
+// timestamps around the level, as the traversal kernel runs it), the state is
+// restored by k_undo_level_p, and the traversal advances with the chosen
+// variant.
+int profile_levels_persistent(bfs_graph* g, Workspace* ws, int32_t root, int32_t reps, int32_t advance_variant,
+                              cudaStream_t s, int32_t* depth, bfs_level_profile* out, int32_t capacity,
+                              int32_t* num_levels) {
+  std::vector<TreeNode> tree;
+  {
+    TreeStore& ts = tree_store();
+    std::lock_guard<std::mutex> lk(ts.mu);
+    tree = ts.nodes;
+  }
+  k_init<<<g->shapes.init, kThreads, 0, s>>>(g->dg, ws->b, ws->st, depth, root, -1, g->tree, g->tree_nodes,
+                                             g->tree_qs, 0);
+  CU(cudaGetLastError());
+  int32_t host_root = root;
+  int32_t ends[2] = {0, 0};
+  CU(cudaMemcpyAsync(ws->b.q[0], &host_root, 4, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(ends, g->dg.off + root, 8, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  DevGraph dg = g->dg;
+  Buffers b = ws->b;
+  RunState* st = ws->st;
+  const long long n = g->dg.n;
+  int32_t L = 0;
+  unsigned int f = 1;
+  unsigned long long e = (unsigned long long)(ends[1] - ends[0]);
+  long long discovered = 1;
+  uint32_t vsel = 0;
+  int32_t prev = -1;
+  std::vector<float> t((size_t)reps);
+  struct Rec {
+    long long t0, t1;
+    unsigned long long pe;
+    unsigned int pf;
+    int32_t status;
+  };
+  auto run_level = [&](int32_t v, Rec* rec) -> int {
+    k_profile_reset<<<1, 1, 0, s>>>(st, (L + 1) % 3);
+    CU(cudaGetLastError());
+    int32_t Lv = L, vv = v;
+    uint32_t ff = f, vs = vsel;
+    unsigned long long ee = e;
+    long long dd = discovered;
+    void* args[] = {&dg, &b, &st, &depth, &Lv, &vv, &ff, &ee, &dd, &vs};
+    CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_profile_level), dim3(g->shapes.profile),
+                                   dim3(kThreads), args, 0, s));
+    RunState hs;
+    CU(cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    rec->t0 = hs.prof_t0;
+    rec->t1 = hs.prof_t1;
+    rec->pf = hs.prof_f;
+    rec->pe = hs.prof_e;
+    rec->status = hs.status;
+    if (hs.status != ST_OK) return fail(BFS_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    return BFS_OK;
+  };
+  while (f > 0) {
+    long long x[F_NUM];
+    for (int k = 0; k < F_NUM; ++k) x[k] = g->dg.gfeat[k];
+    x[F_FRONTIER] = f;
+    x[F_FRONTIER_PPM] = 1000000ll * (long long)f / n;
+    x[F_DISCOVERED] = discovered;
+    x[F_DISCOVERED_PPM] = 1000000ll * discovered / n;
+    x[F_FRONTIER_EDGES] = (long long)e;
+    x[F_LEVEL] = L;
+    const int32_t tv = host_tree_choice(tree, x, L, prev);
+    if (L < capacity) {
+      bfs_level_profile& P = out[L];
+      for (int k = 0; k < F_NUM; ++k) P.features[k] = x[k];
+      P.tree_variant = tv;
+      P.pad = 0;
+      for (int v = 0; v < V_NUM; ++v) {
+        for (int k = 0; k < reps; ++k) {
+          Rec rec;
+          TRY(run_level(v, &rec));
+          t[(size_t)k] = (float)((double)(rec.t1 - rec.t0) * 1e-6);
+          k_undo_level_p<<<g->shapes.init, kThreads, 0, s>>>(b, depth, (uint32_t)((L + 1) & 1), rec.pf, vsel);
+          CU(cudaGetLastError());
+        }
+        std::sort(t.begin(), t.end());
+        P.ms[v] = t[(size_t)reps / 2];
+      }
+    }
+    // advance to the next level (the resulting state does not depend on the variant)
+    const int32_t adv = advance_variant >= 0 ? advance_variant : tv;
+    Rec rec;
+    TRY(run_level(adv, &rec));
+    if (adv == V_PULL) vsel ^= 1u;
+    prev = adv;
+    f = rec.pf;
+    e = rec.pe;
+    discovered += f;
+    ++L;
+    if (L > n) return fail(BFS_ERR_TIMEOUT, "more levels than vertices");
+  }
+  *num_levels = L;
+  return BFS_OK;
+}
+
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -981,28 +1144,8 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
     if (e != cudaSuccess) return fail(BFS_ERR_CUDA, "validate: %s", cudaGetErrorString(e));
     return fail(BFS_ERR_BAD_GRAPH, "CSR failed validation (off[0]=0, nondecreasing, off[n]=m, 0<=idx<n)");
   }
-  // out-degree statistics (Section 4.1 degree distribution)
-  k_deg_reduce<<<blocks, kThreads>>>(off, (int32_t)n, sums, sums + 1, scratch + 1, scratch + 2);
-  int32_t mm[3];
-  e = cudaMemcpy(mm, scratch, 12, cudaMemcpyDeviceToHost);
-  int32_t* hist = nullptr;
-  long long* st6 = nullptr;
-  if (e == cudaSuccess) e = cudaMalloc(&hist, ((size_t)mm[2] + 1) * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&st6, 6 * 8);
-  if (e == cudaSuccess) e = cudaMemset(hist, 0, ((size_t)mm[2] + 1) * 4);
-  if (e == cudaSuccess) {
-    k_deg_hist<<<blocks, kThreads>>>(off, (int32_t)n, hist);
-    k_deg_finish<<<1, kThreads>>>(hist, mm[2], (int32_t)n, sums, sums + 1, st6);
-    e = cudaMemcpy(g->stats6, st6, 6 * 8, cudaMemcpyDeviceToHost);
-  }
-  if (hist) cudaFree(hist);
-  if (st6) cudaFree(st6);
   cudaFree(scratch);
   cudaFree(sums);
-  if (e != cudaSuccess) {
-    cleanup();
-    return fail(BFS_ERR_CUDA, "degree statistics: %s", cudaGetErrorString(e));
-  }
   // transpose for pull when the graph may be directed
   int32_t *in_off = off, *in_idx = idx;
   if (!g->symmetric) {
@@ -1064,6 +1207,15 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
     return fail(e == cudaErrorMemoryAllocation ? BFS_ERR_OOM : BFS_ERR_CUDA, "graph create: %s",
                 cudaGetErrorString(e));
   }
+  // degree statistics (Section 4.1 degree distribution): out-degree, in-degree
+  // (the transpose's row lengths) and total degree
+  r = degree_summary(off, nullptr, (int32_t)n, blocks, g->stats6);
+  if (r == BFS_OK) r = degree_summary(in_off, nullptr, (int32_t)n, blocks, g->stats_in6);
+  if (r == BFS_OK) r = degree_summary(off, in_off, (int32_t)n, blocks, g->stats_tot6);
+  if (r != BFS_OK) {
+    cleanup();
+    return r;
+  }
   DevGraph& dg = g->dg;
   dg.off = off;
   dg.idx = idx;
@@ -1078,7 +1230,11 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
   dg.n_active = (int32_t)(n - (int64_t)iso_h);
   dg.gfeat[F_N] = n;
   dg.gfeat[F_M] = m;
-  for (int k = 0; k < 6; ++k) dg.gfeat[F_DEG_MIN + k] = g->stats6[k];
+  for (int k = 0; k < 6; ++k) {
+    dg.gfeat[F_DEG_MIN + k] = g->stats6[k];
+    dg.gfeat[F_IN_DEG_MIN + k] = g->stats_in6[k];
+    dg.gfeat[F_TOT_DEG_MIN + k] = g->stats_tot6[k];
+  }
   Shapes& s = g->shapes;
   s.init = g->sms * 4;
   s.push_thread = grid_for(reinterpret_cast<const void*>(&k_push_thread), g->sms, 8);
@@ -1095,6 +1251,12 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
     s.persist = g->sms * std::min(per_sm, 8);
   else
     s.persist = 0;
+  per_sm = 0;
+  if (s.persist > 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                           &per_sm, reinterpret_cast<const void*>(&k_profile_level), kThreads, 0) == cudaSuccess)
+    s.profile = std::min(s.persist, g->sms * std::min(per_sm, 8));
+  else
+    s.profile = 0;
   cudaGetLastError();
   *out = g.release();
   return BFS_OK;
@@ -1119,8 +1281,14 @@ int bfs_graph_info(bfs_graph_t g, bfs_graph_info_t* info) {
   std::lock_guard<std::mutex> lk(g->mu);
   info->n = g->dg.n;
   info->m = g->dg.m;
-  for (int k = 0; k < 5; ++k) info->deg_summary[k] = g->stats6[k];
+  for (int k = 0; k < 5; ++k) {
+    info->deg_summary[k] = g->stats6[k];
+    info->in_deg_summary[k] = g->stats_in6[k];
+    info->tot_deg_summary[k] = g->stats_tot6[k];
+  }
   info->deg_sd256 = g->stats6[5];
+  info->in_deg_sd256 = g->stats_in6[5];
+  info->tot_deg_sd256 = g->stats_tot6[5];
   size_t b = g->bytes;
   for (Workspace* ws : g->pool) b += ws->bytes;
   info->bytes_resident = (int64_t)b;
@@ -1345,6 +1513,7 @@ int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advanc
   if (reps < 1 || reps > 1000) return fail(BFS_ERR_INVALID_ARG, "reps %d not in [1, 1000]", reps);
   if (advance_variant < -1 || advance_variant >= V_NUM) return fail(BFS_ERR_INVALID_ARG, "advance_variant");
   if (capacity < 0 || (capacity > 0 && !out) || !num_levels) return fail(BFS_ERR_INVALID_ARG, "output");
+  *num_levels = 0;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
   DeviceGuard dgd(g->device);
   TRY(sync_tree(g));
@@ -1358,6 +1527,17 @@ int bfs_profile_levels(bfs_graph_t g, int32_t root, int32_t reps, int32_t advanc
   if (r == BFS_OK) r = dmalloc(reinterpret_cast<void**>(&snap_st), sizeof(RunState));
   if (r == BFS_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
     r = fail(BFS_ERR_CUDA, "cudaEventCreate");
+  if (r == BFS_OK && g->shapes.profile > 0) {
+    // the default driver's own timing: levels inside the persistent kernel
+    r = profile_levels_persistent(g, ws, root, reps, advance_variant, s, depth, out, capacity, num_levels);
+    cudaStreamSynchronize(s);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    for (void* p : {(void*)depth, (void*)snap_st})
+      if (p) cudaFree(p);
+    const int rr = release(g, ws, s);
+    return r != BFS_OK ? r : rr;
+  }
   int32_t L = 0;
   std::vector<float> t(reps);
   auto body = [&]() -> int {

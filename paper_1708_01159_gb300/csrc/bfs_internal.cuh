@@ -45,12 +45,22 @@ enum CountMode : int32_t {
   CM_NUM = 3,
 };
 
-// Section 4.1 features, in the order the tree file indexes them.
+// Section 4.1 features, in the order the tree file indexes them: graph size,
+// the out-degree 5-number summary and standard deviation, the level's
+// frontier and discovered counts, then the in-degree and total-degree
+// summaries (Section 4.1 names the degree distribution of in-, out- or total
+// degree; for a symmetric graph in-degree equals out-degree).
 enum Feature : int32_t {
   F_N = 0, F_M, F_DEG_MIN, F_DEG_Q1, F_DEG_MED, F_DEG_Q3, F_DEG_MAX, F_DEG_SD256,
   F_FRONTIER, F_FRONTIER_PPM, F_DISCOVERED, F_DISCOVERED_PPM, F_FRONTIER_EDGES, F_LEVEL,
+  F_IN_DEG_MIN, F_IN_DEG_Q1, F_IN_DEG_MED, F_IN_DEG_Q3, F_IN_DEG_MAX, F_IN_DEG_SD256,
+  F_TOT_DEG_MIN, F_TOT_DEG_Q1, F_TOT_DEG_MED, F_TOT_DEG_Q3, F_TOT_DEG_MAX, F_TOT_DEG_SD256,
   F_NUM,
 };
+
+// A feature of the graph itself (the same at every level), as opposed to one
+// of the level (frontier, discovered, frontier edges, level index).
+__host__ __device__ constexpr bool is_graph_feature(int32_t f) { return f < F_FRONTIER || f >= F_IN_DEG_MIN; }
 
 enum Status : int32_t { ST_OK = 0, ST_TIMEOUT = 5 };
 
@@ -85,7 +95,7 @@ static_assert(sizeof(TreeNode) == 24, "TreeNode layout");
 // the lanes of a warp evaluate one each and AND the masks, instead of a chain
 // of dependent steps. Built on the host for one graph, for trees of at most
 // kQsMax internal nodes and kQsMax leaves: the tests on the graph's own
-// features (n, m, degree summary) have the same outcome at every level, so the
+// features (n, m, degree summaries) have the same outcome at every level, so the
 // host folds them into `base` and only the tests on level features
 // (frontier, discovered, frontier edges, level) remain in node[].
 constexpr int kQsMax = 64;
@@ -129,7 +139,7 @@ struct DevGraph {
   int32_t symmetric;
   int32_t n_active;  // vertices with at least one in- or out-edge (the others start visited)
   int32_t pad_;
-  long long gfeat[8];  // F_N .. F_DEG_SD256
+  long long gfeat[F_NUM];  // the graph features (is_graph_feature); level slots unused
 };
 
 struct RunState {
@@ -171,6 +181,10 @@ struct RunState {
   int32_t log_cap;
   int32_t pad_;
   long long t_entry;  // %globaltimer (ns) when the run's first kernel started (before the depth init)
+  long long prof_t0, prof_t1;  // timing harness: %globaltimer at a profiled level's start and end
+  unsigned long long prof_e;   // timing harness: the profiled level's next frontier edge count
+  unsigned int prof_f;         // timing harness: the profiled level's next frontier size
+  int32_t pad4_;
   int32_t* log_variant;
   long long* log_frontier;
   long long* log_edges;

@@ -253,15 +253,8 @@ __device__ __forceinline__ void init_fill(const DevGraph& g, uint32_t* vis0, int
 // the tree's depth of them, and each ppm share costs a 64-bit division.
 __device__ __forceinline__ long long feature_value(const DevGraph& g, int32_t fi, int32_t L, long long f, long long e,
                                                    long long discovered) {
+  if (is_graph_feature(fi)) return g.gfeat[fi];
   switch (fi) {
-    case 0: return g.gfeat[0];
-    case 1: return g.gfeat[1];
-    case 2: return g.gfeat[2];
-    case 3: return g.gfeat[3];
-    case 4: return g.gfeat[4];
-    case 5: return g.gfeat[5];
-    case 6: return g.gfeat[6];
-    case 7: return g.gfeat[7];
     case F_FRONTIER: return f;
     case F_FRONTIER_PPM: return (1000000ll * f) / g.n;
     case F_DISCOVERED: return discovered;
@@ -1235,6 +1228,65 @@ __global__ void k_undo_level(Buffers b, RunState* st) {
 }
 
 
+// One shared-memory buffer serves the CTA variant's copy stage or the
+// edge-centric tile of the persistent kernels.
+constexpr int kPeSlot = kPeTile + 32;
+static_assert(2 * kCtaChunk <= 2 * kPeSlot, "union sizing");
+
+// Level L of a persistent traversal (frontier in q[L & 1], appending to
+// q[(L + 1) & 1] and to the (L + 1) % 3 level words; current bitmap vis[vsel]).
+__device__ __forceinline__ Level persistent_level(const DevGraph& g, const Buffers& b, RunState* st, int32_t* depth,
+                                                  int32_t L, unsigned int f, unsigned long long e,
+                                                  long long discovered, uint32_t vsel) {
+  Level lv;
+  lv.qin = (L & 1) ? b.q[1] : b.q[0];
+  lv.qout = (L & 1) ? b.q[0] : b.q[1];
+  lv.vis = vsel ? b.vis[1] : b.vis[0];
+  lv.vis_next = vsel ? b.vis[0] : b.vis[1];
+  lv.depth = depth;
+  lv.tail = &st->tail3[(L + 1) % 3];
+  lv.next_depth = L + 1;
+  lv.frontier = (int32_t)f;
+  lv.latency_bound = (long long)e < kLatencyEdges;
+  lv.pull_sparse = (long long)g.n_active - discovered < (long long)(g.n_active >> 4);
+  return lv;
+}
+
+// The level's work with variant v inside a persistent kernel (every block of
+// the cooperative grid calls it); returns the block's sum of the reached
+// vertices' out-degrees, after the block's appends are flushed.
+__device__ __forceinline__ unsigned long long persistent_level_work(const DevGraph& g, const Buffers& b, RunState* st,
+                                                                    const Level& lv, int32_t v, int32_t vw,
+                                                                    const Stage& stage, CtaPipe& pp, int32_t* ubuf,
+                                                                    int* s_split, unsigned long long& bar_target) {
+  const unsigned int f = (unsigned int)lv.frontier;
+  unsigned long long edges = 0;
+  switch (v) {
+    case V_PUSH_THREAD: body_push_thread(g, lv, stage, edges); break;
+    case V_PUSH_WARP: body_push_warp(g, lv, stage, vw, edges); break;
+    case V_PUSH_CTA: body_push_cta(g, lv, stage, pp, &st->status, edges); break;
+    case V_PUSH_EDGE:
+      if ((int)f <= kPeSmall) {
+        pe_small_scan(g, lv, ubuf, ubuf + kPeSlot);
+        body_pe_expand<true>(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
+        break;
+      }
+      body_pe_reduce(g, lv, b);
+      if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
+      if (blockIdx.x == 0) body_pe_top(b, (int)f);
+      if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
+      body_pe_scan(b, (int)f);
+      if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
+      body_pe_expand<false>(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
+      break;
+    case V_EDGE_LIST: body_edge_list<false>(g, lv, stage, edges); break;
+    case V_REV_EDGE_LIST: body_edge_list<true>(g, lv, stage, edges); break;
+    default: body_pull<false, kPullWordsPersistent>(g, lv, stage, edges); break;
+  }
+  stage_flush(stage, lv, 1);
+  return block_sum_u64(edges);
+}
+
 // epoch: a number the host changes on every launch on this workspace. Block 0
 // clears the barrier counter and the status word left by the previous run
 // (which a failed run may leave set) and then publishes epoch; every other
@@ -1255,9 +1307,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     }
     st_release_u32(&st->run_epoch, epoch);
   }
-  // one shared buffer serves the CTA variant's copy stage or the edge-centric tile
-  constexpr int kPeSlot = kPeTile + 32;
-  static_assert(2 * kCtaChunk <= 2 * kPeSlot, "union sizing");
   __shared__ alignas(128) int32_t ubuf[2 * kPeSlot];
   __shared__ alignas(8) uint64_t bar[2];
   __shared__ int s_split[2];
@@ -1322,42 +1371,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
         st->log_time[L] = (long long)global_ns();
       }
     }
-    Level lv;
-    lv.qin = (L & 1) ? b.q[1] : b.q[0];
-    lv.qout = (L & 1) ? b.q[0] : b.q[1];
-    lv.vis = vsel ? b.vis[1] : b.vis[0];
-    lv.vis_next = vsel ? b.vis[0] : b.vis[1];
-    lv.depth = depth;
-    lv.tail = &st->tail3[(L + 1) % 3];
-    lv.next_depth = L + 1;
-    lv.frontier = (int32_t)f;
-    lv.latency_bound = (long long)e < kLatencyEdges;
-    lv.pull_sparse = (long long)g.n_active - discovered < (long long)(g.n_active >> 4);
-    unsigned long long edges = 0;
-    switch (v) {
-      case V_PUSH_THREAD: body_push_thread(g, lv, stage, edges); break;
-      case V_PUSH_WARP: body_push_warp(g, lv, stage, vw, edges); break;
-      case V_PUSH_CTA: body_push_cta(g, lv, stage, pp, &st->status, edges); break;
-      case V_PUSH_EDGE:
-        if ((int)f <= kPeSmall) {
-          pe_small_scan(g, lv, ubuf, ubuf + kPeSlot);
-          body_pe_expand<true>(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
-          break;
-        }
-        body_pe_reduce(g, lv, b);
-        if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
-        if (blockIdx.x == 0) body_pe_top(b, (int)f);
-        if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
-        body_pe_scan(b, (int)f);
-        if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) break;
-        body_pe_expand<false>(g, lv, b, stage, ubuf, ubuf + kPeSlot, s_split, edges);
-        break;
-      case V_EDGE_LIST: body_edge_list<false>(g, lv, stage, edges); break;
-      case V_REV_EDGE_LIST: body_edge_list<true>(g, lv, stage, edges); break;
-      default: body_pull<false, kPullWordsPersistent>(g, lv, stage, edges); break;
-    }
-    stage_flush(stage, lv, 1);
-    const unsigned long long e_block = block_sum_u64(edges);
+    const Level lv = persistent_level(g, b, st, depth, L, f, e, discovered, vsel);
+    const unsigned long long e_block = persistent_level_work(g, b, st, lv, v, vw, stage, pp, ubuf, s_split, bar_target);
     if (v == V_PULL) vsel ^= 1u;
     prev = v;
     ok = level_arrive_wait(&st->tail3[(L + 1) % 3], &st->edg3[(L + 1) % 3], e_block, &st->status, &f, &e,
@@ -1368,6 +1383,62 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     if (L < st->log_cap) st->log_time[L] = (long long)global_ns();
     st->discovered = discovered;
     st->edges_reached = reached;
+  }
+}
+
+// Per-level timing harness inside the persistent driver: one cooperative
+// launch expands level L of a traversal whose state (queues, bitmaps, depths)
+// the host has advanced to that level, with variant v, exactly as the
+// persistent traversal would (the same level code, grid and barrier), and
+// records the device time from the start barrier to the end of the
+// level-ending barrier, with the next frontier's size and edge count. The host
+// clears the arrival count and the (L + 1) % 3 level words before each launch.
+__global__ void __launch_bounds__(kThreads, 4) k_profile_level(DevGraph g, Buffers b, RunState* st, int32_t* depth,
+                                                            int32_t L, int32_t v, uint32_t f, unsigned long long e,
+                                                            long long discovered, uint32_t vsel) {
+  __shared__ alignas(128) int32_t ubuf[2 * kPeSlot];
+  __shared__ alignas(8) uint64_t bar[2];
+  __shared__ int s_split[2];
+  BFS_DECLARE_STAGE(stage);
+  cta_pipe_init(bar);
+  CtaPipe pp{ubuf, bar, 0u, 0u, 0u};
+  int32_t vw = 32;
+  v = finish_variant(v, L, -1, f, (long long)e, &vw, true);
+  unsigned long long bar_target = 0;
+  if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->prof_t0 = (long long)global_ns();
+  const Level lv = persistent_level(g, b, st, depth, L, f, e, discovered, vsel);
+  const unsigned long long e_block = persistent_level_work(g, b, st, lv, v, vw, stage, pp, ubuf, s_split, bar_target);
+  unsigned int fn = 0;
+  unsigned long long en = 0;
+  if (!level_arrive_wait(&st->tail3[(L + 1) % 3], &st->edg3[(L + 1) % 3], e_block, &st->status, &fn, &en)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->prof_t1 = (long long)global_ns();
+    st->prof_f = fn;
+    st->prof_e = en;
+  }
+}
+
+// Before a profiled level: clear the arrival count, the status and the level
+// words the level appends to.
+__global__ void k_profile_reset(RunState* st, int32_t slot) {
+  st->bar64 = 0;
+  st->status = ST_OK;
+  st->tail3[slot] = 0;
+  st->edg3[slot] = 0;
+}
+
+// Undo a profiled level in the persistent layout: the `count` vertices it
+// appended to q[qout] lose their depth and their bit in vis[vsel] (pull set no
+// bit there; it wrote the other bitmap, which the next pull rewrites whole).
+__global__ void k_undo_level_p(Buffers b, int32_t* depth, uint32_t qout, unsigned int count, uint32_t vsel) {
+  const int32_t* q = qout ? b.q[1] : b.q[0];
+  uint32_t* vis = vsel ? b.vis[1] : b.vis[0];
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)count; i += stride) {
+    const int32_t v = q[i];
+    depth[v] = -1;
+    atomicAnd(&vis[v >> 5], ~(1u << (v & 31)));
   }
 }
 
@@ -1386,14 +1457,22 @@ __global__ void k_validate(const int32_t* off, const int32_t* idx, int32_t n, in
   if (my) atomicOr(bad, 1);
 }
 
-__global__ void k_deg_reduce(const int32_t* off, int32_t n, unsigned long long* s1, unsigned long long* s2,
-                             int32_t* dmin, int32_t* dmax) {
+// Degree of v for the statistics: the row length in `off`, plus the row
+// length in `off2` when given (in-degree + out-degree = total degree).
+__device__ __forceinline__ unsigned int stat_degree(const int32_t* off, const int32_t* off2, int64_t v) {
+  unsigned int d = (unsigned int)(off[v + 1] - off[v]);
+  if (off2) d += (unsigned int)(off2[v + 1] - off2[v]);
+  return d;
+}
+
+__global__ void k_deg_reduce(const int32_t* off, const int32_t* off2, int32_t n, unsigned long long* s1,
+                             unsigned long long* s2, unsigned int* dmin, unsigned int* dmax) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long a = 0, q = 0;
-  int32_t lo = INT32_MAX, hi = 0;
+  unsigned int lo = 0xffffffffu, hi = 0;
   for (int64_t v = tid; v < n; v += stride) {
-    const int32_t d = off[v + 1] - off[v];
+    const unsigned int d = stat_degree(off, off2, v);
     a += (unsigned long long)d;
     q += (unsigned long long)d * (unsigned long long)d;
     lo = min(lo, d);
@@ -1412,10 +1491,10 @@ __global__ void k_deg_reduce(const int32_t* off, int32_t n, unsigned long long* 
   }
 }
 
-__global__ void k_deg_hist(const int32_t* off, int32_t n, int32_t* hist) {
+__global__ void k_deg_hist(const int32_t* off, const int32_t* off2, int32_t n, int32_t* hist) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t v = tid; v < n; v += stride) atomicAdd(&hist[off[v + 1] - off[v]], 1);
+  for (int64_t v = tid; v < n; v += stride) atomicAdd(&hist[stat_degree(off, off2, v)], 1);
 }
 
 namespace {
@@ -1436,7 +1515,7 @@ __device__ unsigned long long isqrt_u128(unsigned __int128 x) {
 // One block: 5-number summary by nearest rank (q_k = sorted[floor(k (n-1)/4)])
 // from the degree histogram, and floor(256 sigma) exactly:
 // isqrt(65536 (n S2 - S1^2)) / n.
-__global__ void k_deg_finish(const int32_t* hist, int32_t maxdeg, int32_t n, const unsigned long long* s1p,
+__global__ void k_deg_finish(const int32_t* hist, int64_t maxdeg, int32_t n, const unsigned long long* s1p,
                              const unsigned long long* s2p, long long* out6) {
   __shared__ long long carry_s;
   long long rank[5];
@@ -1444,8 +1523,8 @@ __global__ void k_deg_finish(const int32_t* hist, int32_t maxdeg, int32_t n, con
   for (int k = 0; k < 5; ++k) rank[k] = ((long long)k * (n - 1)) / 4;
   if (threadIdx.x == 0) carry_s = 0;
   __syncthreads();
-  for (int base = 0; base <= maxdeg; base += blockDim.x) {
-    const int d = base + threadIdx.x;
+  for (int64_t base = 0; base <= maxdeg; base += blockDim.x) {
+    const int64_t d = base + threadIdx.x;
     const long long c = d <= maxdeg ? hist[d] : 0;
     long long tot;
     const long long ex = block_exclusive_scan<long long>(c, &tot);

@@ -34,13 +34,18 @@ __global__ void k_undo_level(Buffers b, RunState* st);
 __global__ void k_bfs_persistent(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t root, int32_t forced,
                                  const TreeNode* tree, int32_t tree_nodes, const QsTree* qs, uint32_t epoch,
                                  int32_t stall);
+__global__ void k_profile_level(DevGraph g, Buffers b, RunState* st, int32_t* depth, int32_t L, int32_t v, uint32_t f,
+                                unsigned long long e, long long discovered, uint32_t vsel);
+__global__ void k_profile_reset(RunState* st, int32_t slot);
+__global__ void k_undo_level_p(Buffers b, int32_t* depth, uint32_t qout, unsigned int count, uint32_t vsel);
 
 // graph creation
 __global__ void k_validate(const int32_t* off, const int32_t* idx, int32_t n, int32_t m, int32_t* bad);
-__global__ void k_deg_reduce(const int32_t* off, int32_t n, unsigned long long* s1, unsigned long long* s2,
-                             int32_t* dmin, int32_t* dmax);
-__global__ void k_deg_hist(const int32_t* off, int32_t n, int32_t* hist);
-__global__ void k_deg_finish(const int32_t* hist, int32_t maxdeg, int32_t n, const unsigned long long* s1,
+// degree statistics: the row lengths of `off`, plus those of `off2` when it is not null
+__global__ void k_deg_reduce(const int32_t* off, const int32_t* off2, int32_t n, unsigned long long* s1,
+                             unsigned long long* s2, unsigned int* dmin, unsigned int* dmax);
+__global__ void k_deg_hist(const int32_t* off, const int32_t* off2, int32_t n, int32_t* hist);
+__global__ void k_deg_finish(const int32_t* hist, int64_t maxdeg, int32_t n, const unsigned long long* s1,
                              const unsigned long long* s2, long long* out6);
 __global__ void k_tr_count(const int32_t* idx, int32_t m, int32_t* cnt);
 __global__ void k_scan_reduce(const int32_t* in, int32_t len, long long* bsum);

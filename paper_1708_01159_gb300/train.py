@@ -2,7 +2,7 @@
 
   collect  -- on a GPU: run the per-level timing harness (bfs_profile_levels)
               over a set of generated graphs and roots and write one CSV row
-              per (graph, root, level): the 14 integer features and the median
+              per (graph, root, level): the 26 integer features and the median
               time of every variant expanding that level from the same state.
   train    -- label every level with its fastest variant, fit a CART tree
               (Gini impurity, scikit-learn) and export it in the integer text
@@ -16,6 +16,8 @@
               relative to the per-level optimum (the shape of Table 2).
   cv       -- k-fold cross-validation by graph over feature sets, weightings
               and depths.
+  holdout  -- each generator family (R-MAT, directed R-MAT, grid, ER) held out
+              in turn: trained on the others, evaluated on it (Section 4.4).
   level-split -- the paper's random 70/30 split over levels: held-out
               per-level accuracy, for comparison with its reported accuracy.
 
@@ -27,6 +29,7 @@ levels of one traversal are correlated.
   python -m paper_1708_01159_gb300.train train --csv levels.csv --out trees/default.tree
   python -m paper_1708_01159_gb300.train evaluate --csv levels.csv --tree trees/default.tree
   python -m paper_1708_01159_gb300.train level-split --csv levels.csv
+  python -m paper_1708_01159_gb300.train holdout --csv levels.csv
 """
 from __future__ import annotations
 
@@ -52,10 +55,15 @@ LEVEL0_DEFAULT = 3  # Section 4.1: unknown at the first level -> edge list (edge
 #   m1    -- every feature Section 4.1 lists (frontier and discovered both
 #            absolute and as a share of the vertices)
 #   ext   -- m1 plus the frontier's edge count and the level index
+#   *_io  -- the same plus the in-degree and total-degree summaries (Section
+#            4.1 names the distribution of in-, out- or total degree), which
+#            tell directed graphs apart
 FEATURE_SETS = {
     "paper": [0, 1, 2, 3, 4, 5, 6, 7, 8, 11],
+    "paper_io": [0, 1, 2, 3, 4, 5, 6, 7, 8, 11] + list(range(14, 26)),
     "m1": list(range(12)),
     "ext": list(range(14)),
+    "ext_io": list(range(26)),
 }
 
 # Training graphs: (name, generator kwargs). Seeds start at 3000; the
@@ -85,7 +93,20 @@ TRAIN_GRAPHS = [
     ("er", dict(n=1 << 23, avg_degree=8.0, seed=3021)),
     ("rmat", dict(scale=23, edge_factor=16, seed=3022)),
     ("rmat", dict(scale=17, edge_factor=16, seed=3023, permute=True)),
+    # directed R-MAT (not symmetrised): with b != c the in- and out-degree
+    # distributions differ, and pull scans the transpose
+    ("rmat", dict(scale=18, edge_factor=16, seed=3024, directed=True, b=0.30, c=0.08)),
+    ("rmat", dict(scale=20, edge_factor=8, seed=3025, directed=True, b=0.08, c=0.30)),
+    ("rmat", dict(scale=21, edge_factor=16, seed=3026, directed=True)),
+    ("rmat", dict(scale=22, edge_factor=8, seed=3027, directed=True, b=0.25, c=0.13)),
 ]
+
+
+def family(name: str) -> str:
+    """Generator family of a training graph's name: rmat, rmat-dir, grid or er."""
+    if name.startswith("rmat"):
+        return "rmat-dir" if name.endswith("-dir") else "rmat"
+    return name.split("-")[0]
 
 
 def make_graph(kind, kw):
@@ -116,7 +137,8 @@ def collect(out: str, roots_per_graph: int = 4, reps: int = 3, max_levels: int =
             g = make_graph(kind, kw)
             name = g.name
             roots = gg.sample_roots(g, roots_per_graph, seed=kw["seed"] + 500, giant=True)
-            with bfs.Graph(g.off, g.idx) as G:
+            flags = 0 if kw.get("directed") else bfs.BFS_SYMMETRIC
+            with bfs.Graph(g.off, g.idx, flags) as G:
                 for r in roots:
                     feats, ms, tv = bfs.bfs_profile_levels(G.handle, int(r), reps=reps, capacity=max_levels)
                     for L in range(feats.shape[0]):
@@ -127,7 +149,9 @@ def collect(out: str, roots_per_graph: int = 4, reps: int = 3, max_levels: int =
 
 
 def load(csv_path: str):
-    rows = list(csv.DictReader(open(csv_path)))
+    import gzip
+    fh = gzip.open(csv_path, "rt") if csv_path.endswith(".gz") else open(csv_path)
+    rows = list(csv.DictReader(fh))
     graph = np.array([r["graph"] for r in rows])
     root = np.array([int(r["root"]) for r in rows])
     level = np.array([int(r["level"]) for r in rows])
@@ -163,13 +187,19 @@ def level_weights(T, trav, weighting):
     return spread / np.array([tot[k] for k in trav])
 
 
-def fit(X, T, feature_idx, max_depth=8, min_samples_leaf=8, weighting="regret", trav=None):
+# The library evaluates trees of up to 64 leaves in their bit-parallel form,
+# held in shared memory (larger ones are walked node by node in global
+# memory, about 1 us per level); the exporter keeps to that.
+MAX_LEAVES = 64
+
+
+def fit(X, T, feature_idx, max_depth=8, min_samples_leaf=8, weighting="regret", trav=None, max_leaves=MAX_LEAVES):
     """CART with Gini impurity (Section 2.1); labels: the fastest variant per level."""
     from sklearn.tree import DecisionTreeClassifier
     y = T.argmin(axis=1)
     w = level_weights(T, trav if trav is not None else np.zeros(len(T)), weighting)
     clf = DecisionTreeClassifier(criterion="gini", max_depth=max_depth, min_samples_leaf=min_samples_leaf,
-                                 random_state=0)
+                                 max_leaf_nodes=max_leaves, random_state=0)
     clf.fit(X[:, feature_idx], y, sample_weight=w)
     return clf
 
@@ -256,7 +286,8 @@ def evaluate(graph, root, level, X, T, nodes, mask=None):
     return summary
 
 
-def cross_validate(graph, root, level, X, T, folds=6, depths=(6, 8, 10)):
+def cross_validate(graph, root, level, X, T, folds=6, depths=(6, 8, 10), feature_sets=None,
+                   weightings=("uniform", "regret", "relregret")):
     """Mean held-out slowdown vs the per-level optimum, k folds split by graph."""
     import tempfile
     names = sorted(set(graph.tolist()))
@@ -265,8 +296,8 @@ def cross_validate(graph, root, level, X, T, folds=6, depths=(6, 8, 10)):
     fold_of = {nm: i % folds for i, nm in enumerate(names)}
     fold = np.array([fold_of[g] for g in graph])
     trav = np.array([f"{g}/{r}" for g, r in zip(graph, root)])
-    for fs in sorted(FEATURE_SETS):
-        for wt in ("uniform", "regret", "relregret"):
+    for fs in sorted(feature_sets or FEATURE_SETS):
+        for wt in weightings:
             for depth in depths:
                 slow, worst, best_fixed = [], 0.0, []
                 for k in range(folds):
@@ -312,6 +343,46 @@ def level_split(graph, root, level, X, T, test_frac=0.3, seed=0, depths=(6, 8, 1
                       f"within 10 % of the fastest {near:.3f} ({int(te.sum())} of {len(X)} levels)", flush=True)
 
 
+def holdout_families(graph, root, level, X, T, features="ext_io", weighting="relregret", depth=8, min_leaf=8):
+    """Section 4.4's generality question on generated families: for each
+    family (R-MAT, directed R-MAT, grid, Erdos-Renyi) in turn, train on the
+    other families only and evaluate on this one; per family, the tree's and
+    the best fixed variant's traversal time relative to the per-level optimum."""
+    import tempfile
+    fam = np.array([family(g) for g in graph])
+    trav = np.array([f"{g}/{r}" for g, r in zip(graph, root)])
+    fidx = np.array(FEATURE_SETS[features])
+    print(f"held-out family (features={features} weighting={weighting} depth={depth}):")
+    print(f"{'family':10s} {'traversals':>10s} {'tree/opt':>9s} {'worst':>7s} {'best fixed/opt':>15s} "
+          f"{'tree <= best fixed':>19s}")
+    out = {}
+    for f in sorted(set(fam.tolist())):
+        tr, te = fam != f, fam == f
+        clf = fit(X[tr], T[tr], fidx, depth, min_leaf, weighting, trav[tr])
+        with tempfile.NamedTemporaryFile("w", suffix=".tree", delete=False) as fh:
+            path = fh.name
+        export(clf, fidx, path)
+        nodes = read_tree(path)
+        os.unlink(path)
+        pred = schedule_time(nodes, X, T, level)
+        keys = sorted(set(zip(graph[te].tolist(), root[te].tolist())))
+        fixed = {g: int(T[te & (graph == g)].sum(axis=0).argmin()) for g in set(graph[te].tolist())}
+        rt, rb, wins = [], [], 0
+        for g, r in keys:
+            sel = np.nonzero(te & (graph == g) & (root == r))[0]
+            opt = T[sel].min(axis=1).sum()
+            t_tree = T[sel, pred[sel]].sum()
+            t_fix = T[sel, fixed[g]].sum()
+            rt.append(t_tree / opt)
+            rb.append(t_fix / opt)
+            wins += int(t_tree <= t_fix * 1.0001)
+        out[f] = {"traversals": len(keys), "tree_over_opt": float(np.mean(rt)), "worst": float(np.max(rt)),
+                  "best_fixed_over_opt": float(np.mean(rb)), "tree_le_best_fixed": wins / len(keys)}
+        print(f"{f:10s} {len(keys):10d} {np.mean(rt):8.3f}x {np.max(rt):6.2f}x {np.mean(rb):14.3f}x "
+              f"{wins / len(keys):18.0%}", flush=True)
+    return out
+
+
 def print_table(summary, file=sys.stdout):
     print(f"traversals: {summary['traversals']}, per-level accuracy: {summary['level_accuracy']:.3f}", file=file)
     print(f"{'algorithm':14s} {'optimal':>8s} {'1-2x':>7s} {'>5x':>6s} {'>20x':>6s} {'average':>8s} {'worst':>8s}",
@@ -340,8 +411,15 @@ def main():
     v = sub.add_parser("cv", help="k-fold cross-validation by graph over feature sets and weightings")
     v.add_argument("--csv", required=True)
     v.add_argument("--folds", type=int, default=6)
+    v.add_argument("--features", nargs="*", default=None, choices=sorted(FEATURE_SETS))
+    v.add_argument("--weightings", nargs="*", default=["uniform", "regret", "relregret"])
     ls = sub.add_parser("level-split", help="the paper's random 70/30 split over levels: held-out accuracy")
     ls.add_argument("--csv", required=True)
+    h = sub.add_parser("holdout", help="leave each graph family out in turn (Section 4.4 generality)")
+    h.add_argument("--csv", required=True)
+    h.add_argument("--features", default="ext_io", choices=sorted(FEATURE_SETS))
+    h.add_argument("--weighting", default="relregret", choices=["regret", "uniform", "relregret"])
+    h.add_argument("--max-depth", type=int, default=8)
     e = sub.add_parser("evaluate")
     e.add_argument("--csv", required=True)
     e.add_argument("--tree", required=True)
@@ -368,9 +446,11 @@ def main():
             print("held-out graphs:", ", ".join(test_graphs))
             print_table(evaluate(graph, root, level, X, T, nodes, ~train_mask))
     elif a.cmd == "cv":
-        cross_validate(graph, root, level, X, T, a.folds)
+        cross_validate(graph, root, level, X, T, a.folds, feature_sets=a.features, weightings=a.weightings)
     elif a.cmd == "level-split":
         level_split(graph, root, level, X, T)
+    elif a.cmd == "holdout":
+        holdout_families(graph, root, level, X, T, a.features, a.weighting, a.max_depth)
     else:
         print_table(evaluate(graph, root, level, X, T, read_tree(a.tree)))
 

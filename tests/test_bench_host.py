@@ -44,7 +44,7 @@ def test_algorithmic_bytes_matches_plain_count(make):
     g = make()
     for r in gg.sample_roots(g, 2, seed=74):
         res = oracle.bfs(g.off, g.idx, int(r))
-        feats = oracle.level_features(g.off, res)
+        feats = oracle.level_features(g.off, g.idx, res)
         for L in range(res.num_levels):
             f = int(res.level_count[L])
             e = int(res.level_edges[L])

@@ -259,6 +259,27 @@ def test_device_input_and_graph_info():
             assert_parity(g, G, r)
 
 
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_in_and_total_degree_statistics_match_the_oracle(symmetric):
+    """Section 4.1's in- and total-degree summaries, computed on the device at
+    graph creation (the transpose's row lengths, and their sum with the
+    out-degrees), equal the oracle's; a profiled level reports them too."""
+    rng = np.random.default_rng(31)
+    n = 20000
+    g = (gg.rmat(13, 8, seed=32) if symmetric else
+         gg.from_edges(n, rng.zipf(1.7, 90000) % n, rng.integers(0, n, 90000), symmetrize=False))
+    F = oracle.F
+    with make(g, flags=bfs.BFS_SYMMETRIC if symmetric else 0) as G:
+        info = G.info()
+        r = int(gg.sample_roots(g, 1, seed=33)[0])
+        ref = oracle.bfs(g.off, g.idx, r)
+        x = oracle.level_features(g.off, g.idx, ref)[0]
+        assert info["in_deg_summary"] + [info["in_deg_sd256"]] == x[F["in_deg_min"]:F["in_deg_sd256"] + 1]
+        assert info["tot_deg_summary"] + [info["tot_deg_sd256"]] == x[F["tot_deg_min"]:F["tot_deg_sd256"] + 1]
+        feats, _, _ = bfs.bfs_profile_levels(G.handle, r, reps=1)
+        assert feats.tolist() == oracle.level_features(g.off, g.idx, ref)
+
+
 def test_injected_oom_is_reported():
     g = gg.rmat(10, 8, seed=3)
     bfs.lib().bfs_debug_fail_alloc_after(1)
@@ -284,7 +305,7 @@ def test_tree_schedule_matches_oracle_walk():
         with make(g) as G:
             for r in gg.sample_roots(g, 3, seed=6):
                 ref, st = assert_parity(g, G, r)
-                feats = oracle.level_features(g.off, ref)
+                feats = oracle.level_features(g.off, g.idx, ref)
                 want = oracle.predict_schedule(tree, feats)
                 assert st["variant"][:len(want)].tolist() == want
 
@@ -302,7 +323,7 @@ def test_custom_tree_file_with_unknown_leaves(tmp_path):
         with make(g) as G:
             for r in gg.sample_roots(g, 3, seed=7):
                 ref, st = assert_parity(g, G, r)
-                want = oracle.predict_schedule(tree, oracle.level_features(g.off, ref))
+                want = oracle.predict_schedule(tree, oracle.level_features(g.off, g.idx, ref))
                 assert st["variant"][:len(want)].tolist() == want
     finally:
         bfs.bfs_load_tree(None)
@@ -335,14 +356,15 @@ def test_random_trees_schedule_matches_oracle_walk(tmp_path, depth):
     bit-parallel evaluation, 128 leaves its walk; every driver's schedule equals
     the oracle's walk of the tree over the oracle's per-level features."""
     rng = np.random.default_rng(100 + depth)
-    gs = [gg.rmat(13, 16, seed=43), gg.grid(50, 40, 0.1, seed=44), gg.erdos_renyi(8000, 5.0, seed=45)]
+    gs = [gg.rmat(13, 16, seed=43), gg.grid(50, 40, 0.1, seed=44), gg.erdos_renyi(8000, 5.0, seed=45),
+          gg.rmat(12, 16, seed=46, directed=True, b=0.3, c=0.08)]
     pool = []
     refs = []
     for g in gs:
         for r in gg.sample_roots(g, 2, seed=depth):
             ref = oracle.bfs(g.off, g.idx, int(r))
             refs.append((g, int(r), ref))
-            pool += oracle.level_features(g.off, ref)
+            pool += oracle.level_features(g.off, g.idx, ref)
     for k in range(3):
         tree = _random_tree(rng, depth, pool)
         p = tmp_path / f"r{k}.tree"
@@ -351,8 +373,8 @@ def test_random_trees_schedule_matches_oracle_walk(tmp_path, depth):
         bfs.bfs_load_tree(str(p))
         try:
             for g, r, ref in refs:
-                want = oracle.predict_schedule(tree, oracle.level_features(g.off, ref))
-                with make(g) as G:
+                want = oracle.predict_schedule(tree, oracle.level_features(g.off, g.idx, ref))
+                with make(g, flags=0 if g.name.endswith("-dir") else bfs.BFS_SYMMETRIC) as G:
                     for mode in (bfs.MODE_PERSISTENT, bfs.MODE_GRAPH):
                         _, st = assert_parity(g, G, r, mode=mode)
                         assert st["variant"][:len(want)].tolist() == want, (depth, k, mode)
@@ -370,6 +392,43 @@ def _stump(f, t, left, right):
             {"f": -1, "t": 0, "l": -1, "r": -1, "v": right}]
 
 
+def test_directed_graphs_tree_splits_on_in_degree(tmp_path):
+    """Directed R-MAT graphs whose in-degree distributions differ (b != c): a
+    tree that splits on the in-degree maximum and on the total-degree upper
+    quartile (Section 4.1's in- and total-degree features) sends them down
+    different branches; every schedule equals the oracle's walk and every depth
+    the oracle's, in the persistent and graph drivers."""
+    ga = gg.rmat(12, 16, seed=51, directed=True, b=0.30, c=0.08)  # skewed out-degree, flat in-degree
+    gb = gg.rmat(12, 16, seed=52, directed=True, b=0.08, c=0.30)  # flat out-degree, skewed in-degree
+    F = oracle.F
+    xa = oracle.level_features(ga.off, ga.idx, oracle.bfs(ga.off, ga.idx, 0))[0]
+    xb = oracle.level_features(gb.off, gb.idx, oracle.bfs(gb.off, gb.idx, 0))[0]
+    assert xa[F["in_deg_max"]] < xb[F["in_deg_max"]]
+    t_in = (xa[F["in_deg_max"]] + xb[F["in_deg_max"]]) // 2
+    nodes = [{"f": F["in_deg_max"], "t": t_in, "l": 1, "r": 2, "v": -1},
+             {"f": F["frontier"], "t": 40, "l": 3, "r": 4, "v": -1},
+             {"f": F["tot_deg_q3"], "t": xb[F["tot_deg_q3"]], "l": 5, "r": 6, "v": -1},
+             {"f": -1, "t": 0, "l": -1, "r": -1, "v": 0}, {"f": -1, "t": 0, "l": -1, "r": -1, "v": 4},
+             {"f": -1, "t": 0, "l": -1, "r": -1, "v": 2}, {"f": -1, "t": 0, "l": -1, "r": -1, "v": 3}]
+    p = tmp_path / "io.tree"
+    _write_tree(p, nodes)
+    bfs.bfs_load_tree(str(p))
+    try:
+        seen = set()
+        for g in (ga, gb):
+            with make(g, flags=0) as G:
+                for r in gg.sample_roots(g, 3, seed=53):
+                    ref = oracle.bfs(g.off, g.idx, int(r))
+                    want = oracle.predict_schedule({"nodes": nodes}, oracle.level_features(g.off, g.idx, ref))
+                    seen.update(want)
+                    for mode in (bfs.MODE_PERSISTENT, bfs.MODE_GRAPH):
+                        _, st = assert_parity(g, G, r, mode=mode)
+                        assert st["variant"][:len(want)].tolist() == want
+        assert {0, 4}.issubset(seen) and seen & {2, 3}  # both sides of the in-degree split ran
+    finally:
+        bfs.bfs_load_tree(None)
+
+
 def test_tree_threshold_edges(tmp_path):
     """Split thresholds at the edges of each feature's range: ppm thresholds
     below 0 and at 1e6, thresholds equal to an observed value and one below it
@@ -379,7 +438,7 @@ def test_tree_threshold_edges(tmp_path):
     g = gg.rmat(13, 16, seed=46)
     roots = [int(r) for r in gg.sample_roots(g, 2, seed=9)]
     refs = [(r, oracle.bfs(g.off, g.idx, r)) for r in roots]
-    feats = oracle.level_features(g.off, refs[0][1])
+    feats = oracle.level_features(g.off, g.idx, refs[0][1])
     mid = feats[len(feats) // 2]
     trees = [_stump(9, -1, 1, 4), _stump(11, -1, 1, 4), _stump(9, 1000000, 1, 4), _stump(11, 999999, 1, 4)]
     for fi in (8, 9, 10, 11, 12, 13):
@@ -404,7 +463,7 @@ def test_tree_threshold_edges(tmp_path):
             bfs.bfs_load_tree(str(p))
             try:
                 for r, ref in refs:
-                    want = oracle.predict_schedule({"nodes": nodes}, oracle.level_features(g.off, ref))
+                    want = oracle.predict_schedule({"nodes": nodes}, oracle.level_features(g.off, g.idx, ref))
                     for mode in (bfs.MODE_PERSISTENT, bfs.MODE_GRAPH, bfs.MODE_HOST_LOOP):
                         _, st = assert_parity(g, G, r, mode=mode)
                         assert st["variant"][:len(want)].tolist() == want, (k, nodes[0], mode)
@@ -419,7 +478,7 @@ def test_profile_levels_features_match_oracle():
     with make(g) as G:
         feats, ms, tv = bfs.bfs_profile_levels(G.handle, r, reps=3)
         assert feats.shape[0] == ref.num_levels
-        assert feats.tolist() == oracle.level_features(g.off, ref)
+        assert feats.tolist() == oracle.level_features(g.off, g.idx, ref)
         assert np.all(ms > 0)
         # the harness leaves the graph usable and results unchanged
         assert_parity(g, G, r)

@@ -238,7 +238,7 @@ def test_degree_sd_exact_cases():
 def test_level_features_layout():
     g, _ = cf.star(9)
     res = oracle.bfs(g.off, g.idx, 3)
-    feats = oracle.level_features(g.off, res)
+    feats = oracle.level_features(g.off, g.idx, res)
     assert len(feats) == 3
     F = oracle.F
     assert [x[F["frontier"]] for x in feats] == [1, 1, 7]
@@ -287,3 +287,47 @@ def test_unknown_prediction_rule_golden():
         feats.append(x)
     assert oracle.predict_schedule(fx["tree"], feats) == fx["schedule"]
     assert oracle.VARIANTS == tuple(fx["classes"])
+
+
+def test_in_and_total_degree_features_directed_fixture():
+    """Section 4.1's in- and total-degree summaries on the hand-derived directed
+    fixture (tests/golden/directed6.json)."""
+    import json
+    fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "directed6.json")))
+    src, dst = zip(*fx["edges"])
+    g = gg.from_edges(fx["n"], list(src), list(dst), symmetrize=False)
+    want = fx["degree_features"]
+    res = oracle.bfs(g.off, g.idx, 0)
+    feats = oracle.level_features(g.off, g.idx, res)
+    F = oracle.F
+    for x in feats:
+        assert [x[F[k]] for k in ("deg_min", "deg_q1", "deg_med", "deg_q3", "deg_max", "deg_sd256")] == want["out"]
+        assert [x[F[k]] for k in ("in_deg_min", "in_deg_q1", "in_deg_med", "in_deg_q3", "in_deg_max",
+                                  "in_deg_sd256")] == want["in"]
+        assert [x[F[k]] for k in ("tot_deg_min", "tot_deg_q1", "tot_deg_med", "tot_deg_q3", "tot_deg_max",
+                                  "tot_deg_sd256")] == want["total"]
+
+
+def test_in_degree_summary_is_the_transpose_out_degree_summary():
+    """The in-degree summary equals the out-degree summary of the transposed
+    graph (built by scipy); total degree against numpy's lower percentile; on a
+    symmetric graph in = out and total = out + in."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(17)
+    n = 700
+    g = gg.from_edges(n, rng.integers(0, n, 4000), rng.integers(0, n - 50, 4000), symmetrize=False)
+    a = sp.csr_matrix((np.ones(g.m), g.idx, g.off), shape=(n, n)).T.tocsr()
+    res = oracle.bfs(g.off, g.idx, int(gg.sample_roots(g, 1, seed=3)[0]))
+    x = oracle.level_features(g.off, g.idx, res)[0]
+    F = oracle.F
+    ins = [x[F[k]] for k in ("in_deg_min", "in_deg_q1", "in_deg_med", "in_deg_q3", "in_deg_max", "in_deg_sd256")]
+    assert ins == oracle.degree_stats(a.indptr.astype(np.int32))
+    tot = np.diff(g.off.astype(np.int64)) + np.diff(a.indptr.astype(np.int64))
+    q = [int(np.percentile(tot, 25 * k, method="lower")) for k in range(5)]
+    assert [x[F[k]] for k in ("tot_deg_min", "tot_deg_q1", "tot_deg_med", "tot_deg_q3", "tot_deg_max")] == q
+    sd = 256.0 * float(np.std(tot))
+    assert abs(x[F["tot_deg_sd256"]] - math.floor(sd)) <= 1
+    s = gg.rmat(9, 8, seed=5)
+    xs = oracle.level_features(s.off, s.idx, oracle.bfs(s.off, s.idx, 1))[0]
+    assert xs[F["in_deg_min"]:F["in_deg_sd256"] + 1] == xs[F["deg_min"]:F["deg_sd256"] + 1]
+    assert xs[F["tot_deg_max"]] == 2 * xs[F["deg_max"]] and xs[F["tot_deg_min"]] == 2 * xs[F["deg_min"]]

@@ -92,3 +92,44 @@ def test_evaluate_and_level_split():
     lines = out.getvalue().strip().splitlines()
     assert len(lines) == len(train.FEATURE_SETS) * 2
     assert all("held-out level accuracy" in ln for ln in lines)
+
+
+def test_family_names_and_holdout_table():
+    """Held-out families (Section 4.4): each family is evaluated by a tree that
+    never saw it; the table has one row per family."""
+    assert train.family("rmat-s18-ef16-seed3024-dir") == "rmat-dir"
+    assert train.family("rmat-s17-ef16-seed3023-perm") == "rmat"
+    assert train.family("grid-512x512-drop0.1-seed3011-perm") == "grid"
+    assert train.family("er-n1048576-d4.0-seed3015") == "er"
+    graph, root, level, X, T = _levels()
+    names = ["rmat-a", "rmat-b-dir", "grid-c", "er-d", "rmat-e"]
+    graph = np.array([names[int(g[1:])] for g in graph])
+    out = train.holdout_families(graph, root, level, X, T, features="ext_io", depth=4, min_leaf=4)
+    assert sorted(out) == ["er", "grid", "rmat", "rmat-dir"]
+    for row in out.values():
+        assert row["traversals"] > 0 and row["tree_over_opt"] >= 1.0 and row["best_fixed_over_opt"] >= 1.0
+
+
+def test_feature_sets_index_the_extended_features():
+    assert len(FEATURES) == 26
+    assert train.FEATURE_SETS["ext_io"] == list(range(26))
+    assert [FEATURES[i] for i in train.FEATURE_SETS["paper_io"][-12:]][0] == "in_deg_min"
+
+
+def test_shipped_tree_reproduces_from_committed_levels(tmp_path):
+    """trees/levels_gb300.csv.gz holds the per-level GB300 timings (persistent
+    driver) the shipped tree was trained on; training with the configuration
+    its header records reproduces trees/default.tree node for node."""
+    here = os.path.dirname(train.__file__)
+    shipped = open(os.path.join(here, "trees", "default.tree")).read()
+    meta = dict(kv.split("=") for line in shipped.splitlines() if line.startswith("# features=")
+                for kv in line[2:].split())
+    graph, root, level, X, T = train.load(os.path.join(here, "trees", "levels_gb300.csv.gz"))
+    fidx = np.array(train.FEATURE_SETS[meta["features"]])
+    trav = np.array([f"{g}/{r}" for g, r in zip(graph, root)])
+    clf = train.fit(X, T, fidx, int(meta["max_depth"]), int(meta["min_samples_leaf"]), meta["weighting"], trav)
+    out = tmp_path / "t.tree"
+    train.export(clf, fidx, str(out))
+    body = lambda text: [ln for ln in text.splitlines() if ln and not ln.startswith("#")]
+    assert body(out.read_text()) == body(shipped)
+    assert sum(1 for ln in body(shipped)[1:] if ln.startswith("-1 ")) <= train.MAX_LEAVES
