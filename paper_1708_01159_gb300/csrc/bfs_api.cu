@@ -4,6 +4,7 @@
 // kernels } }; host loop), the decision-tree store, multi-source batches and
 // the per-level timing harness.
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -542,6 +543,52 @@ bool build_qs(const std::vector<TreeNode>& t, const long long* gfeat, QsTree* q)
   if (!ok) return false;
   q->n_int = nint;
   q->n_leaf = nleaf;
+  // leaf boxes: walk again, narrowing the level features' bounds on the way
+  // down (x <= t on the left, x >= t + 1 on the right) and deciding the
+  // graph-feature tests, leaves numbered in the same left-to-right order
+  auto level_slot = [](int32_t f) {
+    return f == F_FRONTIER || f == F_FRONTIER_PPM ? 0 : f == F_DISCOVERED || f == F_DISCOVERED_PPM ? 1
+           : f == F_FRONTIER_EDGES ? 2 : 3;
+  };
+  int leaf_no = 0;
+  std::function<void(int, std::array<long long, 8>, bool)> boxes = [&](int i, std::array<long long, 8> bx,
+                                                                       bool reach) {
+    const TreeNode& nd = t[i];
+    if (nd.f < 0) {
+      const int b = leaf_no++;
+      for (int k = 0; k < 8; ++k) {
+        const long long v = std::max<long long>(INT32_MIN, std::min<long long>(INT32_MAX, bx[k]));
+        q->box[b][k] = (int32_t)v;
+      }
+      if (!reach) {
+        for (int k = 0; k < 4; ++k) {
+          q->box[b][2 * k] = INT32_MAX;
+          q->box[b][2 * k + 1] = -1;
+        }
+      }
+      return;
+    }
+    if (is_graph_feature(nd.f)) {
+      const bool left = gfeat[nd.f] <= nd.t;
+      boxes(nd.l, bx, reach && left);
+      boxes(nd.r, bx, reach && !left);
+      return;
+    }
+    long long thr = nd.t;
+    if (nd.f == F_FRONTIER_PPM || nd.f == F_DISCOVERED_PPM) thr = ppm_to_count_threshold(nd.t, gfeat[F_N]);
+    const int k = level_slot(nd.f);
+    std::array<long long, 8> lb = bx, rb = bx;
+    lb[2 * k + 1] = std::min(lb[2 * k + 1], thr);
+    rb[2 * k] = std::max(rb[2 * k], thr == std::numeric_limits<long long>::max() ? thr : thr + 1);
+    boxes(nd.l, lb, reach);
+    boxes(nd.r, rb, reach);
+  };
+  std::array<long long, 8> all{};
+  for (int k = 0; k < 4; ++k) {
+    all[2 * k] = std::numeric_limits<long long>::min();
+    all[2 * k + 1] = std::numeric_limits<long long>::max();
+  }
+  boxes(0, all, true);
   return true;
 }
 

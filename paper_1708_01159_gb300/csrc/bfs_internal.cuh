@@ -111,6 +111,13 @@ struct QsTree {
   unsigned long long base;   // AND of the masks of the graph-feature tests that fail on this graph
   QsNode node[kQsMax];
   int32_t leaf[kQsMax];  // class of each leaf, left to right (-1: unknown)
+  // Box of each leaf: the level-feature values that reach it (its path's
+  // tests; empty for a leaf this graph's graph-feature tests rule out).
+  // box[b][2k] <= x_k <= box[b][2k + 1] for the level features k = frontier,
+  // discovered, frontier edges, level (bounds clamped to int32: every such
+  // feature lies in [0, 2^31)). A level whose features stay in the previous
+  // level's leaf box reaches the same leaf, so its tree walk can be skipped.
+  int32_t box[kQsMax][8];
 };
 
 // Origin of every CSR entry (the vertex whose row holds it) and of every

@@ -303,11 +303,11 @@ __device__ __forceinline__ bool level_feature_le(int32_t fi, long long t, int32_
   return x <= t;
 }
 
-// The tree's prediction by the bit-parallel form, within one warp: lane k
-// tests the level-feature nodes k, k + 32; the graph-feature tests are already
-// folded into q.base. Every lane of the warp calls it and gets the same
-// result; no block-wide synchronisation.
-__device__ __forceinline__ int32_t qs_eval_warp(const QsTree& q, int32_t L, long long f, long long e,
+// The leaf the tree's walk reaches, by the bit-parallel form, within one warp:
+// lane k tests the level-feature nodes k, k + 32; the graph-feature tests are
+// already folded into q.base. Every lane of the warp calls it and gets the
+// same result (-1 if none); no block-wide synchronisation.
+__device__ __forceinline__ int32_t qs_leaf_warp(const QsTree& q, int32_t L, long long f, long long e,
                                                 long long discovered) {
   unsigned long long m = q.base;
   for (int k = lane_id(); k < q.n_int; k += 32) {
@@ -317,7 +317,24 @@ __device__ __forceinline__ int32_t qs_eval_warp(const QsTree& q, int32_t L, long
   const uint32_t lo = __reduce_and_sync(kFull, (uint32_t)m);
   const uint32_t hi = __reduce_and_sync(kFull, (uint32_t)(m >> 32));
   const int leaf = __ffsll((long long)(((unsigned long long)hi << 32) | lo)) - 1;
-  return (leaf >= 0 && leaf < q.n_leaf) ? q.leaf[leaf] : -1;
+  return (leaf >= 0 && leaf < q.n_leaf) ? leaf : -1;
+}
+
+// The tree's prediction (leaf class, -1 for unknown) by the bit-parallel form.
+__device__ __forceinline__ int32_t qs_eval_warp(const QsTree& q, int32_t L, long long f, long long e,
+                                                long long discovered) {
+  const int32_t leaf = qs_leaf_warp(q, L, f, e, discovered);
+  return leaf >= 0 ? q.leaf[leaf] : -1;
+}
+
+// True (in every lane) when this level's features lie in the box that lanes
+// 0-7 of the warp hold in `bound` (lane 2k: lower bound of level feature k,
+// lane 2k + 1: upper bound; k = frontier, discovered, frontier edges, level).
+__device__ __forceinline__ bool in_leaf_box(int32_t bound, int32_t L, long long f, long long e, long long discovered) {
+  const uint32_t lane = lane_id();
+  const long long x = lane < 2 ? f : lane < 4 ? discovered : lane < 6 ? e : (long long)L;
+  const bool ok = (lane & 1u) ? x <= (long long)bound : x >= (long long)bound;
+  return __all_sync(kFull, lane >= 8u || ok);
 }
 
 // Section 4.1 unknown-prediction rule on a walk's result (or the forced
@@ -1341,6 +1358,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
   long long discovered = 0, reached = 0;
   int32_t prev = -1;
   uint32_t vsel = 0;
+  // lanes 0-7 of each warp: the box of the leaf the last evaluated level
+  // reached (in_leaf_box); box_leaf < 0 until a level has been evaluated
+  int32_t box_bound = 0, box_leaf = -1;
   // level 0's frontier is the root; later levels' f and e arrive with the barrier
   unsigned int f = 1;
   unsigned long long e = (unsigned long long)(g.off[root + 1] - g.off[root]);
@@ -1356,9 +1376,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
     }
     int32_t vw = 32;
     int32_t v = forced;
-    if (v < 0 && use_qs)
-      v = qs_eval_warp(s_qs, L, f, (long long)e, discovered);
-    else if (v < 0 && tree != nullptr && tree_nodes > 0)
+    if (v < 0 && use_qs) {
+      // same leaf box as the previous level: the walk reaches the same leaf, and
+      // the level repeats the previous level's choice (for an unknown leaf too)
+      if (box_leaf >= 0 && in_leaf_box(box_bound, L, f, (long long)e, discovered)) {
+        v = prev;
+      } else {
+        box_leaf = qs_leaf_warp(s_qs, L, f, (long long)e, discovered);
+        v = box_leaf >= 0 ? s_qs.leaf[box_leaf] : -1;
+        box_bound = (box_leaf >= 0 && lane_id() < 8u) ? s_qs.box[box_leaf][lane_id()] : 0;
+      }
+    } else if (v < 0 && tree != nullptr && tree_nodes > 0)
       v = walk_tree(g, tree, tree_nodes, L, f, (long long)e, discovered);
     v = finish_variant(v, L, prev, f, (long long)e, &vw, forced >= 0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
