@@ -291,22 +291,25 @@ def bench_count_modes(bfs, torch, G, g, roots, edges, stream):
 
 def bench_c1(bfs, torch, stream, reps=5):
     """R-MAT scale 14, edge factor 16, 16 seeded roots of nonzero degree, every
-    level run by the fixed one-thread-per-vertex push (the paper's vertex push):
-    the persistent driver (one launch per traversal) and the graph driver, CUDA
-    events per traversal, harmonic-mean GTEPS over the roots (median of `reps`
-    runs per root). The graph is about 2 MB, L2-resident: latency bound."""
+    level run by one fixed top-down push kernel: the one-thread-per-vertex push
+    (the paper's vertex push) in the persistent driver (one launch per
+    traversal) and the graph driver, and each of the other push kernels in the
+    persistent driver, beside the switched traversal. CUDA events per
+    traversal, harmonic-mean GTEPS over the roots (median of `reps` runs per
+    root). The graph is about 2 MB, L2-resident: latency bound."""
     import graphgen as gg
     g = gg.rmat_s14_ef16()
     roots = gg.sample_roots(g, 16, seed=gg.SEED_ROOTS)
     out = {"workload": f"R-MAT scale 14 edge factor 16 ({g.n:,} vertices, {g.m:,} directed edges), 16 roots, "
-                       "push_thread forced"}
+                       "push_thread forced (and each push kernel in the persistent driver)"}
     with bfs.Graph(g.off, g.idx) as G:
         d = torch.empty(g.n, dtype=torch.int32, device="cuda")
         sts = [bfs.bfs_run_ex(G.handle, int(r), d, stream, forced_variant=0, stats=True, log_capacity=256)
                for r in roots]
         edges = [st["edges_reached"] for st in sts]
-        for name, mode in (("persistent", bfs.MODE_PERSISTENT), ("graph", bfs.MODE_GRAPH)):
-            bfs.bfs_run_ex(G.handle, int(roots[0]), d, stream, forced_variant=0, mode=mode)
+
+        def measure(variant, mode):
+            bfs.bfs_run_ex(G.handle, int(roots[0]), d, stream, forced_variant=variant, mode=mode)
             torch.cuda.synchronize()
             med = []
             for r in roots:
@@ -314,12 +317,17 @@ def bench_c1(bfs, torch, stream, reps=5):
                 for _ in range(reps):
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    bfs.bfs_run_ex(G.handle, int(r), d, stream, forced_variant=0, mode=mode)
+                    bfs.bfs_run_ex(G.handle, int(r), d, stream, forced_variant=variant, mode=mode)
                     e1.record(stream)
                     torch.cuda.synchronize()
                     ts.append(e0.elapsed_time(e1) / 1e3)
                 med.append(float(np.median(ts)))
-            out[name] = {"gteps": harmonic_gteps(med, edges), "us_per_traversal": 1e6 * float(np.mean(med))}
+            return {"gteps": harmonic_gteps(med, edges), "us_per_traversal": 1e6 * float(np.mean(med))}
+
+        for name, mode in (("persistent", bfs.MODE_PERSISTENT), ("graph", bfs.MODE_GRAPH)):
+            out[name] = measure(0, mode)
+        out["push_kernels_persistent"] = {bfs.VARIANTS[v]: measure(v, bfs.MODE_PERSISTENT) for v in range(4)}
+        out["switched_persistent"] = measure(bfs.VARIANT_TREE, bfs.MODE_PERSISTENT)
         out["levels"] = [st["levels"] for st in sts]
         out["device_us"] = float(np.mean([st.get("device_ns", 0) for st in sts]) / 1e3)
     return out

@@ -874,7 +874,8 @@ __device__ __forceinline__ void pull_words(const DevGraph& g, const Level& lv, c
 // (k / kWords) * stride + base0 + (k % kWords) * kWarps (consecutive warps take
 // consecutive words; increasing in k), and it takes kWords per step.
 //  - dense (most reachable vertices still unvisited): each step's words are
-//    loaded one step ahead, so that load's round trip overlaps the scans;
+//    loaded one step ahead, and their row extents prefetched into L2, so
+//    those round trips overlap the current step's scans;
 //  - sparse (few left): a batch of 32 of the warp's words is loaded at once,
 //    one per lane; words with no unvisited vertex are settled right there
 //    (their next-bitmap word is all ones), the row extents of the others are
@@ -914,6 +915,7 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
         cw[j] = cw_next[j];
         const int wn = wb + j * kWarps + stride;
         cw_next[j] = wn < g.words ? pull_load_word<kReadOnlyCache>(lv.vis, wn) : kFull;
+        if (wn < g.words) prefetch_l2(g.in_off + (size_t)wn * 32);  // the next step's row extents
       }
       pull_words<kReadOnlyCache, kWords>(g, lv, w, cw, wbuf, wcnt, edges);
       if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
