@@ -202,7 +202,34 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 
-def algorithmic_bytes(g, depth, feats, L, variant):
+HINT_SCAN = 64  # in-list entries the library examines when it chooses a vertex's pull hint
+
+
+def pull_hints(g):
+    """The pull variant's first test per vertex, as the library defines it:
+    among the first HINT_SCAN entries of the vertex's in-list (the CSR itself
+    for a symmetric graph), the in-neighbour of largest out-degree, the first
+    such on ties; -1 without in-edges."""
+    off = g.off.astype(np.int64)
+    deg = np.diff(off)
+    n = g.n
+    cap = np.minimum(deg, HINT_SCAN)
+    rows = np.repeat(np.arange(n, dtype=np.int64), cap)
+    starts = np.repeat(off[:-1], cap)
+    k = np.arange(int(cap.sum()), dtype=np.int64) - np.repeat(np.cumsum(cap) - cap, cap)  # position in the row
+    nbr = g.idx[starts + k].astype(np.int64)
+    # largest out-degree first, then the earliest position
+    score = (deg[nbr] << 8) | (255 - k)
+    hint = np.full(n, -1, dtype=np.int64)
+    if rows.size:
+        seg = np.nonzero(cap > 0)[0]
+        best = np.maximum.reduceat(score, (np.cumsum(cap) - cap)[seg])
+        kbest = 255 - (best & 255)
+        hint[seg] = g.idx[off[:-1][seg] + kbest]
+    return hint
+
+
+def algorithmic_bytes(g, depth, feats, L, variant, hint=None):
     """Bytes level L must move for the variant that expanded it (HBM traffic the
     method needs; the visited bitmaps, n/8 bytes, stay in L2 and are not counted)."""
     n = g.n
@@ -212,22 +239,26 @@ def algorithmic_bytes(g, depth, feats, L, variant):
     if variant != 4:  # push: queue read, row extents, adjacency, depth + queue writes, degree of new vertices
         e = int(feats[L][F_FE])
         return 4 * f + 8 * f + 4 * e + 4 * nxt + 4 * nxt + 8 * nxt
-    # pull: bitmap words read/written, row extents of unvisited vertices that
-    # have in-edges (the others start visited), the adjacency entries scanned
-    # up to the first frontier neighbour, writes
+    # pull: bitmap words read/written, the row extent and the hint of every
+    # unvisited vertex that has in-edges (the others start visited), the
+    # adjacency entries scanned up to the first frontier neighbour by the
+    # vertices whose hint is not in the frontier, writes
+    if hint is None:
+        hint = pull_hints(g)
     words = (n + 31) // 32
     deg = np.diff(g.off.astype(np.int64))
     unvis = ((depth < 0) | (depth > L)) & (deg > 0)
+    hint_hit = unvis & (hint >= 0) & (depth[np.maximum(hint, 0)] == L)
     hit = depth[g.idx] == L
     pos = np.arange(g.m, dtype=np.int64)
     cand = np.where(hit, pos, np.int64(g.m + 1))
-    rows = np.nonzero(unvis & (deg > 0))[0]
+    rows = np.nonzero(unvis & ~hint_hit)[0]
     first = np.minimum.reduceat(cand, g.off[:-1].astype(np.int64)[rows]) if rows.size else np.zeros(0, np.int64)
     # reduceat over the selected starts spans to the next selected start; clip to the row end
     ends = g.off[1:].astype(np.int64)[rows]
     starts = g.off[:-1].astype(np.int64)[rows]
     scanned = np.where(first < ends, first - starts + 1, ends - starts)
-    return 8 * words + 4 * int(unvis.sum()) + 4 * int(scanned.sum()) + 8 * nxt
+    return 8 * words + 8 * int(unvis.sum()) + 4 * int(scanned.sum()) + 8 * nxt
 
 
 def traffic_for(kernel_key):
@@ -687,6 +718,7 @@ def run_ours(args):
         # roots in the timed steps above (mean over steps).
         per_root_s = np.array(times, dtype=np.float64).reshape(args.steps, R).mean(axis=0)
         sample = list(range(min(4, R)))
+        hint = pull_hints(g)
         b_sched, b_td, t_sum = [], [], 0.0
         for i in sample:
             r = int(roots[i])
@@ -697,7 +729,8 @@ def run_ours(args):
             feats[:, 8] = st["frontier"][:nl]
             feats[:, 12] = st["frontier_edges"][:nl]
             # depth init (4 n) plus every level's bytes for the variant that ran it
-            b_sched.append(4 * g.n + sum(algorithmic_bytes(g, dep, feats, L, int(st["variant"][L])) for L in range(nl)))
+            b_sched.append(4 * g.n + sum(algorithmic_bytes(g, dep, feats, L, int(st["variant"][L]), hint)
+                                         for L in range(nl)))
             n_r = st["vertices_reached"]
             b_td.append(4 * st["edges_reached"] + 8 * n_r + 4 * g.n + 4 * n_r + 8 * n_r)
             t_sum += float(per_root_s[i])
@@ -720,7 +753,7 @@ def run_ours(args):
         bfs.bfs_run(G.handle, r0, depth[0], stream)
         torch.cuda.synchronize()
         dep = depth[0].cpu().numpy()
-        nbytes = algorithmic_bytes(g, dep, feats, L, v)
+        nbytes = algorithmic_bytes(g, dep, feats, L, v, hint)
         t = float(chosen[L]) * 1e-3
         line["roofline"]["dominant_level"] = {
             "kernel": f"{bfs.VARIANTS[v]} at level {L} of root {r0}", "algorithmic_bytes": int(nbytes),

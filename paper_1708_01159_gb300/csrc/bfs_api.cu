@@ -1239,6 +1239,14 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
     cleanup();
     return r;
   }
+  // the pull variant's first test per vertex (k_pull_hint)
+  int32_t* hint = nullptr;
+  r = galloc(reinterpret_cast<void**>(&hint), (size_t)n * 4);
+  if (r != BFS_OK) {
+    cleanup();
+    return r;
+  }
+  k_pull_hint<<<blocks, kThreads>>>(off, in_off, in_idx, (int32_t)n, hint);
   unsigned int* iso = nullptr;
   unsigned int iso_h = 0;
   e = cudaMalloc(&iso, sizeof(unsigned int));
@@ -1269,6 +1277,7 @@ int bfs_graph_create(const int32_t* row_offsets, const int32_t* col_indices, int
   dg.in_off = in_off;
   dg.in_idx = in_idx;
   dg.vis_init = vis_init;
+  dg.hint = hint;
   dg.aux = g->aux;
   dg.n = (int32_t)n;
   dg.m = (int32_t)m;

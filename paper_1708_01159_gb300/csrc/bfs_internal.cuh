@@ -78,6 +78,7 @@ enum Stall : int32_t {
 constexpr int32_t kLevel0Default = V_PUSH_EDGE;
 
 constexpr int kIdxPad = 8;  // int32 entries of slack after idx
+constexpr int kHintScan = 64;  // in-list entries examined when a vertex's pull hint is chosen
 
 struct TreeNode {
   long long t;  // threshold: x[f] <= t goes left
@@ -140,6 +141,11 @@ struct DevGraph {
   // their first use; kernels read it at run time, so CUDA graphs built before
   // then see the arrays too)
   const struct GraphAux* aux;
+  // per vertex, the in-neighbour with the largest out-degree among the first
+  // kHintScan entries of its in-list (-1 without in-edges): the pull variant
+  // tests it first, since a high-degree in-neighbour is the likeliest to be
+  // in an early frontier
+  const int32_t* hint;
   int32_t n;
   int32_t m;
   int32_t words;  // ceil(n / 32)

@@ -818,17 +818,29 @@ __device__ __forceinline__ void pull_words(const DevGraph& g, const Level& lv, c
   bool active[kWords], found[kWords];
   bool any = false;
 #pragma unroll
+  int32_t h[kWords];
   for (int j = 0; j < kWords; ++j) {
     v[j] = w[j] * 32 + (int32_t)lane;
     active[j] = w[j] >= 0 && cw[j] != kFull && v[j] < g.n && !((cw[j] >> lane) & 1u);
     found[j] = false;
     beg[j] = end[j] = 0;
-    if (active[j]) {
+    h[j] = -1;
+    if (active[j]) {  // three coalesced loads, issued together
       beg[j] = g.in_off[v[j]];
       end[j] = g.in_off[v[j] + 1];
+      h[j] = g.hint[v[j]];
     }
     pos[j] = beg[j];
     active[j] = active[j] && beg[j] < end[j];
+  }
+  // the hint first: a vertex whose likeliest in-neighbour is in the frontier
+  // is found without reading its in-list
+#pragma unroll
+  for (int j = 0; j < kWords; ++j) {
+    if (active[j] && h[j] >= 0 && vis_bit<kReadOnlyCache>(lv.vis, h[j])) {
+      found[j] = true;
+      active[j] = false;
+    }
     any = any || active[j];
   }
   while (any) {
@@ -1661,6 +1673,29 @@ __global__ void k_vis_init(const int32_t* off, const int32_t* in_off, int32_t n,
       vis_init[v >> 5] = word;
       if (word) atomicAdd(isolated_count, (unsigned)__popc(word));
     }
+  }
+}
+
+// Pull hint of every vertex: among the first kHintScan entries of its in-list,
+// the in-neighbour with the largest out-degree (the first such on ties; -1
+// without in-edges). Any in-neighbour is a valid first test, so the cap only
+// bounds the cost on hubs' long lists.
+__global__ void k_pull_hint(const int32_t* off, const int32_t* in_off, const int32_t* in_idx, int32_t n,
+                            int32_t* hint) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const int32_t b = in_off[v];
+    const int32_t e = min(in_off[v + 1], b + kHintScan);
+    int32_t best = -1, best_deg = -1;
+    for (int32_t k = b; k < e; ++k) {
+      const int32_t u = in_idx[k];
+      const int32_t d = off[u + 1] - off[u];
+      if (d > best_deg) {
+        best_deg = d;
+        best = u;
+      }
+    }
+    hint[v] = best;
   }
 }
 

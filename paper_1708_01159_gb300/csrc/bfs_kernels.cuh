@@ -52,6 +52,8 @@ __global__ void k_scan_reduce(const int32_t* in, int32_t len, long long* bsum);
 __global__ void k_scan_top(long long* bsum, int32_t nblocks);
 __global__ void k_scan_apply(const int32_t* in, int32_t len, const long long* bsum, int32_t* out);
 __global__ void k_tr_scatter(const int32_t* off, const int32_t* idx, int32_t n, int32_t* cursor, int32_t* in_idx);
+__global__ void k_pull_hint(const int32_t* off, const int32_t* in_off, const int32_t* in_idx, int32_t n,
+                            int32_t* hint);
 __global__ void k_vis_init(const int32_t* off, const int32_t* in_off, int32_t n, int32_t words, uint32_t* vis_init,
                            unsigned int* isolated_count);
 

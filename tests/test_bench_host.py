@@ -16,12 +16,25 @@ import graphgen as gg
 import oracle
 
 
+def _hint_plain(g, v):
+    """The pull hint of v, plainly: among the first 64 entries of its list, the
+    neighbour of largest degree, the first such on ties; -1 without edges."""
+    best, best_deg = -1, -1
+    for e in range(int(g.off[v]), min(int(g.off[v + 1]), int(g.off[v]) + 64)):
+        u = int(g.idx[e])
+        d = int(g.off[u + 1] - g.off[u])
+        if d > best_deg:
+            best, best_deg = u, d
+    return best
+
+
 def _pull_bytes_plain(g, depth, L, nxt):
     """Pull at level L, counted vertex by vertex: every bitmap word read and
-    written (8 B), the row extents of each vertex not visited by level L that
-    has in-edges (4 B), the adjacency entries it scans in order up to and
-    including its first in-neighbour at depth L, or all of them (4 B each),
-    and the depth and queue writes plus degree read of each new vertex (8 B)."""
+    written (8 B), the row extent and the hint of each vertex not visited by
+    level L that has in-edges (4 + 4 B); unless its hint is at depth L, the
+    adjacency entries it scans in order up to and including its first
+    in-neighbour at depth L, or all of them (4 B each); and the depth and queue
+    writes plus degree read of each new vertex (8 B)."""
     words = (g.n + 31) // 32
     U = S = 0
     for v in range(g.n):
@@ -29,13 +42,22 @@ def _pull_bytes_plain(g, depth, L, nxt):
         if hi == lo or 0 <= depth[v] <= L:
             continue
         U += 1
+        h = _hint_plain(g, v)
+        if h >= 0 and depth[h] == L:
+            continue
         k = 0
         for e in range(lo, hi):
             k += 1
             if depth[g.idx[e]] == L:
                 break
         S += k
-    return 8 * words + 4 * U + 4 * S + 8 * nxt
+    return 8 * words + 8 * U + 4 * S + 8 * nxt
+
+
+def test_pull_hints_match_a_plain_choice():
+    for g in (gg.rmat(10, 8, seed=75), gg.rmat(9, 16, seed=76, permute=True), gg.grid(12, 9, 0.3, seed=77)):
+        hint = bench.pull_hints(g)
+        assert [int(x) for x in hint] == [_hint_plain(g, v) for v in range(g.n)]
 
 
 @pytest.mark.parametrize("make", [lambda: gg.rmat(10, 8, seed=71), lambda: gg.grid(30, 20, 0.2, seed=72),
