@@ -330,7 +330,7 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out);
 /* Register a graph (same device; up to 256; the caller keeps it alive until
  * bfs_serve_destroy). Synchronous: probe runs on a private stream size the
  * graph's queries. Traversals from vertices 0, n/3, 2n/3 and n-1 pick the one
- * reaching the most edges; it is timed on 2, 4, 8, 16, 32, 64 blocks, one and
+ * reaching the most edges; it is timed on 8, 16, 32, 64 blocks, one and
  * two per SM and a full occupancy wave, and queries get the count with the least
  * blocks x time among those at most 4x slower than the fastest. One 64-root
  * multi-source wave (roots the probe reached, on the wave grid of at most two

@@ -355,7 +355,7 @@ void dispatcher(bfs_server* s) {
 // (synchronous, on a private stream):
 //  1. traversals from up to four spread vertices (0, n/3, 2n/3, n-1); the one
 //     reaching the most edges is the probe root;
-//  2. that traversal timed on 2, 4, 8, 16, 32, 64 blocks, one and two per SM
+//  2. that traversal timed on 8, 16, 32, 64 blocks, one and two per SM
 //     and a full occupancy wave: a query gets the block count that minimises
 //     blocks x time (the device share it holds) among those within
 //     kLatencySlack of the fastest, so latency-bound graphs run narrow and
@@ -414,9 +414,9 @@ int probe_shape(bfs_server* s, bfs_graph* g, Shape* out) {
       return BFS_ERR_CUDA;
     return BFS_OK;
   };
-  constexpr int kSizes = 9;
-  const int32_t sizes[kSizes] = {2, 4, 8, 16, 32, 64, s->sms, 2 * s->sms, full};
-  float t[kSizes] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  constexpr int kSizes = 7;
+  const int32_t sizes[kSizes] = {8, 16, 32, 64, s->sms, 2 * s->sms, full};
+  float t[kSizes] = {0, 0, 0, 0, 0, 0, 0};
   float fastest = 1e30f;
   for (int i = 0; i < kSizes && rc == BFS_OK; ++i) {
     bfs_options opt{};
