@@ -804,25 +804,44 @@ __device__ __forceinline__ void warp_stage_flush(int32_t* wbuf, unsigned int cnt
   __syncwarp();
 }
 
-// The scan of kWords bitmap words (w[j] < 0: none) with current words cw[j]:
-// each lane takes vertex w[j] * 32 + lane of every word, scans its
-// in-neighbours four per round, interleaving the kWords scans, and stops at
-// the first visited one; found vertices get their depth and a slot of the
-// warp's stage, and the next bitmap's words are written.
+// A pull level runs in two phases per warp. The hint pass takes kWords bitmap
+// words per step (w[j] < 0: none; cw[j] the current word): each lane takes
+// vertex w[j] * 32 + lane of every word and, when it is unvisited, tests its
+// hint (the in-neighbour of largest out-degree among the first entries of its
+// in-list, chosen at graph create); a vertex whose hint is in the frontier is
+// found there, without reading its in-list, and the next bitmap's words are
+// written. The others (misses) go to the warp's miss list in shared memory;
+// whenever it holds 32, the miss pass scans their in-lists, one vertex per
+// lane, four in-neighbours per round, stopping at the first visited one, and
+// sets the found vertices' bits in the next bitmap. So a step of the hint pass
+// costs one round trip to the hint and its bitmap word, and no lane of a miss
+// scan waits on vertices that need no scan. Found vertices get their depth and
+// a slot of the warp's stage.
+template <int kWords>
+struct PullMisses {
+  static constexpr int kCap = 32 * (kWords + 1);  // up to 31 left over plus one step's misses
+  int32_t* v;                                     // kCap entries each, in shared memory
+  int32_t* beg;
+  int32_t* end;
+};
+
+// Shared-memory ints the miss lists of a block's warps take.
+template <int kWords>
+constexpr int pull_scratch_ints() {
+  return (kThreads / 32) * 3 * PullMisses<kWords>::kCap;
+}
+
 template <bool kReadOnlyCache, int kWords>
 __device__ __forceinline__ void pull_words(const DevGraph& g, const Level& lv, const int32_t (&w)[kWords],
                                            const uint32_t (&cw)[kWords], int32_t* wbuf, unsigned int& wcnt,
-                                           unsigned long long& edges) {
+                                           const PullMisses<kWords>& ms, int& mcnt, unsigned long long& edges) {
   const uint32_t lane = lane_id();
-  int32_t v[kWords], pos[kWords], beg[kWords], end[kWords];
+  int32_t v[kWords], beg[kWords], end[kWords], h[kWords];
   bool active[kWords], found[kWords];
-  bool any = false;
 #pragma unroll
-  int32_t h[kWords];
   for (int j = 0; j < kWords; ++j) {
     v[j] = w[j] * 32 + (int32_t)lane;
     active[j] = w[j] >= 0 && cw[j] != kFull && v[j] < g.n && !((cw[j] >> lane) & 1u);
-    found[j] = false;
     beg[j] = end[j] = 0;
     h[j] = -1;
     if (active[j]) {  // three coalesced loads, issued together
@@ -830,44 +849,10 @@ __device__ __forceinline__ void pull_words(const DevGraph& g, const Level& lv, c
       end[j] = g.in_off[v[j] + 1];
       h[j] = g.hint[v[j]];
     }
-    pos[j] = beg[j];
     active[j] = active[j] && beg[j] < end[j];
   }
-  // the hint first: a vertex whose likeliest in-neighbour is in the frontier
-  // is found without reading its in-list
 #pragma unroll
-  for (int j = 0; j < kWords; ++j) {
-    if (active[j] && h[j] >= 0 && vis_bit<kReadOnlyCache>(lv.vis, h[j])) {
-      found[j] = true;
-      active[j] = false;
-    }
-    any = any || active[j];
-  }
-  while (any) {
-    int32_t u[kWords][4];
-#pragma unroll
-    for (int j = 0; j < kWords; ++j) {
-      const int nv = active[j] ? min(4, end[j] - pos[j]) : 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) u[j][k] = nv ? g.in_idx[k < nv ? pos[j] + k : pos[j]] : 0;
-    }
-    any = false;
-#pragma unroll
-    for (int j = 0; j < kWords; ++j) {
-      if (!active[j]) continue;
-      uint32_t hit = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) hit |= vis_bit<kReadOnlyCache>(lv.vis, u[j][k]);
-      pos[j] += 4;
-      if (hit) {
-        found[j] = true;
-        active[j] = false;
-      } else if (pos[j] >= end[j]) {
-        active[j] = false;
-      }
-      any = any || active[j];
-    }
-  }
+  for (int j = 0; j < kWords; ++j) found[j] = active[j] && h[j] >= 0 && vis_bit<kReadOnlyCache>(lv.vis, h[j]);
 #pragma unroll
   for (int j = 0; j < kWords; ++j) {
     const uint32_t fm = __ballot_sync(kFull, found[j]);
@@ -879,28 +864,109 @@ __device__ __forceinline__ void pull_words(const DevGraph& g, const Level& lv, c
     }
     wcnt += (unsigned)__popc(fm);
     if (lane == 0 && w[j] >= 0) lv.vis_next[w[j]] = cw[j] | fm;
+    const bool miss = active[j] && !found[j];
+    const uint32_t mm = __ballot_sync(kFull, miss);
+    if (miss) {
+      const int slot = mcnt + __popc(mm & lanemask_lt());
+      ms.v[slot] = v[j];
+      ms.beg[slot] = beg[j];
+      ms.end[slot] = end[j];
+    }
+    mcnt += __popc(mm);
   }
 }
 
-// Two walks over the bitmap words share pull_words. This warp's k-th word is
-// (k / kWords) * stride + base0 + (k % kWords) * kWarps (consecutive warps take
-// consecutive words; increasing in k), and it takes kWords per step.
+// The miss pass over entries base .. base + cnt - 1 (cnt <= 32) of the warp's
+// miss list.
+template <bool kReadOnlyCache, int kWords>
+__device__ __forceinline__ void pull_misses(const DevGraph& g, const Level& lv, const PullMisses<kWords>& ms,
+                                            int base, int cnt, int32_t* wbuf, unsigned int& wcnt,
+                                            unsigned long long& edges) {
+  // orders the list entries and this warp's next-bitmap word stores before
+  // the reads and bit sets below
+  __syncwarp();
+  const uint32_t lane = lane_id();
+  bool active = (int)lane < cnt;
+  int32_t v = 0, beg = 0, pos = 0, end = 0;
+  if (active) {
+    v = ms.v[base + lane];
+    beg = ms.beg[base + lane];
+    end = ms.end[base + lane];
+    pos = beg;
+  }
+  bool found = false;
+  while (__any_sync(kFull, active)) {
+    const int nv = active ? min(4, end - pos) : 0;
+    int32_t u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = nv ? g.in_idx[k < nv ? pos + k : pos] : 0;
+    if (active) {
+      uint32_t hit = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) hit |= vis_bit<kReadOnlyCache>(lv.vis, u[k]);
+      pos += 4;
+      if (hit) {
+        found = true;
+        active = false;
+      } else if (pos >= end) {
+        active = false;
+      }
+    }
+  }
+  const uint32_t fm = __ballot_sync(kFull, found);
+  if (found) {
+    const int32_t deg = g.symmetric ? end - beg : g.off[v + 1] - g.off[v];
+    lv.depth[v] = lv.next_depth;
+    edges += (unsigned long long)deg;
+    wbuf[wcnt + __popc(fm & lanemask_lt())] = v;
+    atomicOr(lv.vis_next + (v >> 5), 1u << (v & 31));
+  }
+  wcnt += (unsigned)__popc(fm);
+  __syncwarp();  // the list entries are read before the hint pass overwrites them
+}
+
+// After a hint-pass step: scan the misses 32 at a time while the list holds
+// that many (all of them when drain), keeping the warp's stage below capacity.
+template <bool kReadOnlyCache, int kWords>
+__device__ __forceinline__ void pull_settle(const DevGraph& g, const Level& lv, const PullMisses<kWords>& ms,
+                                            int& mcnt, bool drain, int32_t* wbuf, unsigned int& wcnt,
+                                            unsigned long long& edges) {
+  if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
+    warp_stage_flush(wbuf, wcnt, lv);
+    wcnt = 0;
+  }
+  while (mcnt >= 32 || (drain && mcnt > 0)) {  // uniform
+    const int take = min(32, mcnt);
+    mcnt -= take;
+    pull_misses<kReadOnlyCache, kWords>(g, lv, ms, mcnt, take, wbuf, wcnt, edges);
+    if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
+      warp_stage_flush(wbuf, wcnt, lv);
+      wcnt = 0;
+    }
+  }
+}
+
+// Two walks over the bitmap words share the hint pass. This warp's k-th word
+// is (k / kWords) * stride + base0 + (k % kWords) * kWarps (consecutive warps
+// take consecutive words; increasing in k), and it takes kWords per step.
 //  - dense (most reachable vertices still unvisited): each step's words are
-//    loaded one step ahead, and their row extents prefetched into L2, so
-//    those round trips overlap the current step's scans;
+//    loaded one step ahead, and their row extents and hints prefetched into
+//    L2, so those round trips overlap the current step;
 //  - sparse (few left): a batch of 32 of the warp's words is loaded at once,
 //    one per lane; words with no unvisited vertex are settled right there
-//    (their next-bitmap word is all ones), the row extents of the others are
-//    prefetched into L2, and only those are scanned. A late level whose words
-//    are nearly all full then costs one round trip per 32 words instead of
-//    one per kWords.
+//    (their next-bitmap word is all ones), the row extents and hints of the
+//    others are prefetched into L2, and only those are taken. A late level
+//    whose words are nearly all full then costs one round trip per 32 words
+//    instead of one per kWords.
+// scratch: pull_scratch_ints<kWords>() ints of the block's shared memory.
 template <bool kReadOnlyCache>
 __device__ __forceinline__ uint32_t pull_load_word(const uint32_t* vis, int32_t w) {
   return kReadOnlyCache ? ld_nc_u32(vis + w) : vis[w];
 }
 
 template <bool kReadOnlyCache, int kWords>
-__device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage, unsigned long long& edges) {
+__device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage, int32_t* scratch,
+                          unsigned long long& edges) {
   static_assert(kWords * 32 <= kWarpStage, "a step must fit a stage slice");
   static_assert(32 % kWords == 0, "a batch holds whole steps");
   const uint32_t lane = lane_id();
@@ -908,6 +974,10 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
   const int wib = threadIdx.x >> 5;
   int32_t* wbuf = stage.buf + wib * kWarpStage;  // the block stage is empty on entry
   unsigned int wcnt = 0;
+  constexpr int kCap = PullMisses<kWords>::kCap;
+  int32_t* mine = scratch + wib * 3 * kCap;
+  const PullMisses<kWords> ms{mine, mine + kCap, mine + 2 * kCap};
+  int mcnt = 0;
   const int stride = gridDim.x * kWarps * kWords;
   const int base0 = blockIdx.x * kWarps * kWords + wib;
   if (!lv.pull_sparse) {
@@ -927,13 +997,13 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
         cw[j] = cw_next[j];
         const int wn = wb + j * kWarps + stride;
         cw_next[j] = wn < g.words ? pull_load_word<kReadOnlyCache>(lv.vis, wn) : kFull;
-        if (wn < g.words) prefetch_l2(g.in_off + (size_t)wn * 32);  // the next step's row extents
+        if (wn < g.words) {  // the next step's row extents and hints
+          prefetch_l2(g.in_off + (size_t)wn * 32);
+          prefetch_l2(g.hint + (size_t)wn * 32);
+        }
       }
-      pull_words<kReadOnlyCache, kWords>(g, lv, w, cw, wbuf, wcnt, edges);
-      if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
-        warp_stage_flush(wbuf, wcnt, lv);
-        wcnt = 0;
-      }
+      pull_words<kReadOnlyCache, kWords>(g, lv, w, cw, wbuf, wcnt, ms, mcnt, edges);
+      pull_settle<kReadOnlyCache, kWords>(g, lv, ms, mcnt, false, wbuf, wcnt, edges);
     }
   } else {
     for (int k0 = 0;; k0 += 32) {
@@ -944,7 +1014,10 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
       const uint32_t cwl = inb ? pull_load_word<kReadOnlyCache>(lv.vis, wl) : kFull;
       const bool open = inb && cwl != kFull;
       if (inb && !open) lv.vis_next[wl] = kFull;
-      if (open) prefetch_l2(g.in_off + (size_t)wl * 32);
+      if (open) {
+        prefetch_l2(g.in_off + (size_t)wl * 32);
+        prefetch_l2(g.hint + (size_t)wl * 32);
+      }
       uint32_t todo = __ballot_sync(kFull, open);
       while (todo) {  // uniform
         int32_t w[kWords];
@@ -957,14 +1030,12 @@ __device__ void body_pull(const DevGraph& g, const Level& lv, const Stage& stage
           w[j] = have ? __shfl_sync(kFull, wl, src) : -1;
           cw[j] = have ? __shfl_sync(kFull, cwl, src) : kFull;
         }
-        pull_words<kReadOnlyCache, kWords>(g, lv, w, cw, wbuf, wcnt, edges);
-        if (wcnt > (unsigned)(kWarpStage - kWords * 32)) {
-          warp_stage_flush(wbuf, wcnt, lv);
-          wcnt = 0;
-        }
+        pull_words<kReadOnlyCache, kWords>(g, lv, w, cw, wbuf, wcnt, ms, mcnt, edges);
+        pull_settle<kReadOnlyCache, kWords>(g, lv, ms, mcnt, false, wbuf, wcnt, edges);
       }
     }
   }
+  pull_settle<kReadOnlyCache, kWords>(g, lv, ms, mcnt, true, wbuf, wcnt, edges);
   if (wcnt) warp_stage_flush(wbuf, wcnt, lv);
 }
 
@@ -1230,7 +1301,8 @@ __global__ void __launch_bounds__(kThreads) k_pull(DevGraph g, Buffers b, RunSta
   BFS_DECLARE_STAGE(stage);
   const Level lv = load_level(g, b, st);
   unsigned long long edges = 0;
-  body_pull<true, kPullWordsLaunch>(g, lv, stage, edges);
+  __shared__ int32_t s_scratch[pull_scratch_ints<kPullWordsLaunch>()];
+  body_pull<true, kPullWordsLaunch>(g, lv, stage, s_scratch, edges);
   stage_flush(stage, lv, 1);
   block_add_u64(edges, &st->next_edges);
 }
@@ -1263,6 +1335,7 @@ __global__ void k_undo_level(Buffers b, RunState* st) {
 // edge-centric tile of the persistent kernels.
 constexpr int kPeSlot = kPeTile + 32;
 static_assert(2 * kCtaChunk <= 2 * kPeSlot, "union sizing");
+static_assert(pull_scratch_ints<kPullWordsPersistent>() <= 2 * kPeSlot, "union sizing");
 
 // Level L of a persistent traversal (frontier in q[L & 1], appending to
 // q[(L + 1) & 1] and to the (L + 1) % 3 level words; current bitmap vis[vsel]).
@@ -1312,7 +1385,7 @@ __device__ __forceinline__ unsigned long long persistent_level_work(const DevGra
       break;
     case V_EDGE_LIST: body_edge_list<false>(g, lv, stage, edges); break;
     case V_REV_EDGE_LIST: body_edge_list<true>(g, lv, stage, edges); break;
-    default: body_pull<false, kPullWordsPersistent>(g, lv, stage, edges); break;
+    default: body_pull<false, kPullWordsPersistent>(g, lv, stage, ubuf, edges); break;
   }
   stage_flush(stage, lv, 1);
   return block_sum_u64(edges);
