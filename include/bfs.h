@@ -223,9 +223,10 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
  * (row i for roots[i]), caller-owned. Roots are processed in waves of up to 64
  * by one persistent kernel per wave, one bit per root in 64-bit visited /
  * frontier masks per vertex, each level pushing or pulling for all roots at
- * once; depths up to 13 are kept as 4-bit codes per vertex and root until the
- * wave ends, when each output row is written once (76 n bytes of buffers in
- * all, allocated on the first call and kept with the graph).
+ * once; the frontier masks of depths 0-14 are kept per depth until the wave
+ * ends, when each output row is written once from them (deeper depths are
+ * written when found; 164 n bytes of buffers in all, allocated on the first
+ * call and kept with the graph).
  * Batches on one graph are ordered after each other on the device.
  * edges_out: optional host array of k int64 reached-edge counts; when given,
  * the call synchronises `stream`. Errors as bfs_run.
@@ -294,7 +295,7 @@ int bfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int64
  * over the head of the queue. A unit is one query's traversal (charged its
  * workspace, plus an n-entry depth buffer when the caller passes none) or a
  * multi-source wave merging up to merge_batch queued queries of one graph
- * (charged one wave buffer set, 76 n bytes, plus a depth buffer per query
+ * (charged one wave buffer set, 164 n bytes, plus a depth buffer per query
  * without one): continuous batching. Units run on a pool of streams and overlap
  * on the device; each wave root's depths go straight to its query's buffer.
  * Results are the same as alone: depths are exact. Workspaces, depth buffers
@@ -334,12 +335,13 @@ int bfs_serve_create(const bfs_serve_config* cfg, bfs_server_t* out);
  * two per SM and a full occupancy wave, and queries get the count with the least
  * blocks x time among those at most 4x slower than the fastest. One 64-root
  * multi-source wave (roots the probe reached, on the wave grid of at most two
- * blocks per SM that merged queries run on; needs 332 n bytes of temporary
+ * blocks per SM that merged queries run on; needs 420 n bytes of temporary
  * memory, skipped if that does not fit) decides whether queued queries are
  * merged (merge_policy 0): when its blocks x time per root is below a single
- * query's. Then the graph's pools are allocated: min(max_inflight, 16)
- * traversal workspaces, and when its queries may merge (merge_batch > 1 and
- * the probe or merge_policy 1 allows it) two wave buffer sets (76 n bytes
+ * query's. Then the graph's pools are allocated: min(max_inflight, 64, the
+ * number the memory budget admits at once) traversal workspaces, and when its
+ * queries may merge (merge_batch > 1 and the probe or merge_policy 1 allows
+ * it) two wave buffer sets (164 n bytes
  * each, so two waves of the graph can run at once), plus n-entry depth buffers
  * for queries submitted without one (one per workspace and merge_batch per
  * set). Takes a few traversals' time, up to a few seconds on a high-diameter

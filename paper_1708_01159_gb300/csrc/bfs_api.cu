@@ -13,6 +13,7 @@
 #include <fstream>
 #include <functional>
 #include <limits>
+#include <utility>
 #include <memory>
 #include <mutex>
 #include <sstream>
@@ -881,10 +882,10 @@ int bfs::ms_set_create(bfs_graph* g, MsSet** out) {
     return p;
   };
   set->mb.visit = static_cast<unsigned long long*>(A(n * 8));
+  set->mb.hist = static_cast<unsigned long long*>(A(n * 8 * (size_t)kMsHistLevels));
   set->mb.front[0] = static_cast<unsigned long long*>(A(n * 8));
   set->mb.front[1] = static_cast<unsigned long long*>(A(n * 8));
   set->mb.next = static_cast<unsigned long long*>(A(n * 8));
-  set->mb.codes = static_cast<unsigned long long*>(A(n * 32));
   set->mb.flist[0] = static_cast<int32_t*>(A(n * 4));
   set->mb.flist[1] = static_cast<int32_t*>(A(n * 4));
   set->mb.tlist = static_cast<int32_t*>(A(n * 4));
@@ -894,7 +895,27 @@ int bfs::ms_set_create(bfs_graph* g, MsSet** out) {
     r = fail(BFS_ERR_CUDA, "cudaEventCreate");
   }
   if (r == BFS_OK) {
-    MsState init{};
+    // the masks start zero (the kernel keeps them so between waves)
+    cudaStream_t zs;
+    cudaError_t e = cudaStreamCreateWithFlags(&zs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+      const std::pair<void*, size_t> masks[] = {{set->mb.visit, n * 8},
+                                                {set->mb.hist, n * 8 * (size_t)kMsHistLevels},
+                                                {set->mb.front[0], n * 8},
+                                                {set->mb.front[1], n * 8},
+                                                {set->mb.next, n * 8}};
+      for (const auto& z : masks)
+        if (e == cudaSuccess) e = cudaMemsetAsync(z.first, 0, z.second, zs);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(zs);
+      cudaStreamDestroy(zs);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      r = fail(BFS_ERR_CUDA, "wave set zeroing: %s", cudaGetErrorString(e));
+    }
+  }
+  if (r == BFS_OK) {
+    MsState init{};  // clean_blocks == clean_grid: the masks are zero
     r = upload_now(set->st, &init, sizeof init);
   }
   if (r != BFS_OK) {

@@ -18,12 +18,20 @@
 // Output. A depth found at a level is not written to the k x n output then:
 // each output sector holds 8 vertices of one root, which would be filled piece
 // by piece over several levels (and, being far larger than L2, read back and
-// merged each time). Instead each vertex keeps a 4-bit code per root in a
-// 32-byte block (0: not reached, d + 1: depth d <= 13, 15: deeper), updated
-// whole by the one lane that owns the vertex at that level (the pull lane, or
-// the commit lane of a touched vertex), and a final pass writes every output
-// sector once, -1 included. Depths beyond 13 (high-diameter graphs) are
-// written when found and their code 15 tells the final pass to leave them.
+// merged each time). Instead the frontier masks of depths below kMsHistLevels
+// are kept, one n-mask array per depth (the history: hist[d][u] holds the
+// roots that reached u at depth d, disjoint over d), and a final pass builds
+// every vertex's depths from its history masks and writes every output sector
+// once, -1 included. Depths of kMsHistLevels and beyond (high-diameter graphs)
+// are written when found; the final pass leaves an entry whose root reached
+// the vertex but whose history holds no depth.
+//
+// The traversal's own frontier masks alternate between front[0] and front[1]
+// (zeroed with visit and next when a wave starts, so they stay in L2); the
+// history is written beside them, one plain store per vertex and depth it is
+// reached at, and read only by the final pass, which zeroes what it read, so
+// that the history arrays are zero whenever a wave starts (a wave that did
+// not finish leaves the next one to zero them all).
 //
 // Level L uses frontier slot L % 4 (ftail, fedges), appends to (L + 1) % 4 and
 // clears (L + 2) % 4, which every block finished reading two levels ago; the
@@ -44,33 +52,21 @@ __device__ __forceinline__ unsigned long long warp_or64(unsigned long long x) {
   return x;
 }
 
-// Bit k of b (k < 16) moved to bit 4k: a nibble of 1 for every set bit.
-__device__ __forceinline__ unsigned long long nibble_spread16(unsigned long long b) {
-  b &= 0xffffull;
-  b = (b | (b << 24)) & 0x000000ff000000ffull;
-  b = (b | (b << 12)) & 0x000f000f000f000full;
-  b = (b | (b << 6)) & 0x0303030303030303ull;
-  b = (b | (b << 3)) & 0x1111111111111111ull;
-  return b;
+// Bit k of x (k < 16) moved to bit 4k, through a table of the 256 byte
+// spreads (lut[x]: bit k of x at bit 4k of a 32-bit word).
+__device__ __forceinline__ unsigned long long nibble_spread16(const uint32_t* lut, unsigned long long x) {
+  return (unsigned long long)lut[x & 255ull] | ((unsigned long long)lut[(x >> 8) & 255ull] << 32);
 }
 
-// Record that vertex u was reached at depth d by the roots in nb: the lane
-// that owns u at this level reads its 32-byte code block, sets those roots'
-// nibbles and writes the whole block back (one full sector). Depths beyond
-// kMsCodeMaxDepth get code 15 and go to the output rows now.
-__device__ __forceinline__ void ms_record(const MsBuffers& mb, const MsRows& rows, int64_t u, unsigned long long nb,
-                                          int32_t d) {
-  const unsigned long long c = d <= kMsCodeMaxDepth ? (unsigned long long)(d + 1) : 15ull;
-  ulonglong2* p = reinterpret_cast<ulonglong2*>(mb.codes + 4 * u);
-  ulonglong2 lo = p[0], hi = p[1];
-  lo.x |= nibble_spread16(nb) * c;
-  lo.y |= nibble_spread16(nb >> 16) * c;
-  hi.x |= nibble_spread16(nb >> 32) * c;
-  hi.y |= nibble_spread16(nb >> 48) * c;
-  p[0] = lo;
-  p[1] = hi;
-  if (d > kMsCodeMaxDepth)
+// Vertex u was reached at depth d by the roots in nb: the history keeps the
+// depths below kMsHistLevels; deeper ones are written to their rows now.
+__device__ __forceinline__ void ms_record(const MsBuffers& mb, const MsRows& rows, int64_t n, int64_t u,
+                                          unsigned long long nb, int32_t d) {
+  if (d < kMsHistLevels) {
+    mb.hist[(size_t)d * (size_t)n + (size_t)u] = nb;
+  } else {
     for (unsigned long long m = nb; m; m &= m - 1) rows.row[__ffsll((long long)m) - 1][u] = d;
+  }
 }
 
 }  // namespace
@@ -78,6 +74,7 @@ __device__ __forceinline__ void ms_record(const MsBuffers& mb, const MsRows& row
 __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, MsState* st, int32_t k,
                                                        MsRows rows, MsConfig cfg, int32_t stall) {
   __shared__ unsigned long long s_edges[64];
+  __shared__ uint32_t s_spread[256];
   __shared__ int32_t s_big[kMsThreads];
   __shared__ int s_nbig;
   BFS_DECLARE_STAGE(stage);
@@ -89,19 +86,30 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
   const int wib = threadIdx.x >> 5;
   constexpr int kWarps = kMsThreads / 32;
   for (int i = threadIdx.x; i < 64; i += blockDim.x) s_edges[i] = 0;
-  // init: masks and codes cleared (the output rows are written once, at the end)
+  for (int x = threadIdx.x; x < 256; x += blockDim.x) {
+    uint32_t y = 0;
+    for (int b = 0; b < 8; ++b) y |= ((uint32_t)(x >> b) & 1u) << (4 * b);
+    s_spread[x] = y;
+  }
+  // init: visit, frontier and next masks cleared; the history is zero unless
+  // the last wave on this set did not finish (then it is zeroed here); the
+  // output rows are written once, at the end. Every block reads the counts
+  // before the first barrier, block 0 resets them after it.
+  const bool hist_dirty = *reinterpret_cast<volatile unsigned int*>(&st->clean_blocks) !=
+                          *reinterpret_cast<volatile unsigned int*>(&st->clean_grid);
   for (int64_t v = tid; v < n; v += stride) {
     mb.visit[v] = 0;
     mb.front[0][v] = 0;
     mb.front[1][v] = 0;
     mb.next[v] = 0;
-    ulonglong2* c = reinterpret_cast<ulonglong2*>(mb.codes + 4 * v);
-    c[0] = make_ulonglong2(0ull, 0ull);
-    c[1] = make_ulonglong2(0ull, 0ull);
+    if (hist_dirty)
+      for (int d = 0; d < kMsHistLevels; ++d) mb.hist[(size_t)d * (size_t)n + (size_t)v] = 0;
   }
   unsigned long long bar_target = 0;  // this block's copy of the barriers' arrival target
   if (!grid_arrive_wait(&st->bar64, bar_target, &st->status, stall == STALL_GRID_BARRIER ? 1u : 0u)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->clean_blocks = 0;
+    st->clean_grid = gridDim.x;
     // roots: the level 0 frontier; a vertex repeated as several roots carries several bits
     unsigned int fc = 0;
     unsigned long long fe = 0;
@@ -113,7 +121,7 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
       }
       mb.visit[r] |= 1ull << i;
       mb.front[0][r] |= 1ull << i;
-      mb.codes[4 * (int64_t)r + (i >> 4)] |= 1ull << (4 * (i & 15));  // code 1: depth 0
+      mb.hist[r] |= 1ull << i;  // depth 0
     }
     for (int i = 0; i < 64; ++i) st->edges[i] = 0;
     for (int s = 0; s < 4; ++s) {
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
           if (nb) {
             my_fe += (unsigned long long)(g.off[u + 1] - g.off[u]);
             stage_put(stage, out_list, out_tail, u);
-            ms_record(mb, rows, u, nb, L + 1);
+            ms_record(mb, rows, n, u, nb, L + 1);
           }
         }
         stage_drain(stage, out_list, out_tail, kStageCap / 2);
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
               mb.visit[u] = vis | nb;
               my_fe += (unsigned long long)(g.off[u + 1] - g.off[u]);
               stage_put(stage, out_list, out_tail, (int32_t)u);
-              ms_record(mb, rows, u, nb, L + 1);
+              ms_record(mb, rows, n, u, nb, L + 1);
             }
           }
           nxt[u] = nb;
@@ -264,29 +272,61 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
     ok = grid_arrive_wait(&st->bar64, bar_target, &st->status);
   }
   // Final pass, a warp per 32 consecutive vertices: every output sector written
-  // once from the codes (coalesced 128-byte row segments, one per root), and
-  // the per-root reached-edge counts: for each root, the sum of out-degrees of
-  // the vertices whose visit mask carries its bit. (The loop ended right after
-  // a grid barrier, so every block's codes are visible.)
+  // once from the history (coalesced 128-byte row segments, one per root),
+  // the per-root reached-edge counts (for each root, the sum of out-degrees of
+  // the vertices whose visit mask carries its bit), and the history cleared
+  // for the next wave. (The loop ended right after a grid barrier, so
+  // every block's masks are visible.) Depths 0 .. L - 1 occurred; those below
+  // kMsHistLevels are in the history.
+  const int32_t dmax = min(L - 1, kMsHistLevels - 1);
   for (int64_t wbase = (int64_t)blockIdx.x * kWarps; wbase < words; wbase += (int64_t)gridDim.x * kWarps) {
     const int64_t w = wbase + wib;
     if (w >= words) continue;  // whole warp
     const int64_t u = w * 32 + lane;
     const bool valid = u < n;
-    if (ok) {
-      ulonglong2 lo = make_ulonglong2(0ull, 0ull), hi = make_ulonglong2(0ull, 0ull);
-      if (valid) {
-        const ulonglong2* c = reinterpret_cast<const ulonglong2*>(mb.codes + 4 * u);
-        lo = c[0];
-        hi = c[1];
+    const unsigned long long vis = valid ? mb.visit[u] : 0ull;
+    if (ok && valid) {
+      // bit b of the code (d + 1 for depth d) of root i is bit i of plane b
+      // (the history masks of u are disjoint); loads five depths at a time
+      unsigned long long p0 = 0ull, p1 = 0ull, p2 = 0ull, p3 = 0ull;
+      constexpr int kChunk = 5;
+      static_assert(kMsHistLevels % kChunk == 0, "whole chunks");
+      static_assert(kMsHistLevels <= 15, "codes d + 1 fit four bits");
+#pragma unroll 1
+      for (int32_t d0 = 0; d0 <= dmax; d0 += kChunk) {
+        unsigned long long m[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)  // an unreached vertex has no history
+          m[j] = vis && d0 + j <= dmax ? mb.hist[(size_t)(d0 + j) * (size_t)n + (size_t)u] : 0ull;
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          if (m[j]) {
+            mb.hist[(size_t)(d0 + j) * (size_t)n + (size_t)u] = 0ull;
+            const int c = d0 + j + 1;
+            if (c & 1) p0 |= m[j];
+            if (c & 2) p1 |= m[j];
+            if (c & 4) p2 |= m[j];
+            if (c & 8) p3 |= m[j];
+          }
+        }
       }
-      for (int i = 0; i < k; ++i) {
-        const unsigned long long word = i < 16 ? lo.x : i < 32 ? lo.y : i < 48 ? hi.x : hi.y;
-        const unsigned int code = (unsigned int)(word >> (4 * (i & 15))) & 15u;
-        if (valid && code != 15u) rows.row[i][u] = code == 0u ? -1 : (int32_t)code - 1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        // nibble r: the code of root 16 q + r
+        const unsigned long long word = nibble_spread16(s_spread, p0 >> (16 * q)) |
+                                        (nibble_spread16(s_spread, p1 >> (16 * q)) << 1) |
+                                        (nibble_spread16(s_spread, p2 >> (16 * q)) << 2) |
+                                        (nibble_spread16(s_spread, p3 >> (16 * q)) << 3);
+        const int rn = min(16, k - 16 * q);
+#pragma unroll 1
+        for (int r = 0; r < rn; ++r) {
+          const int i = 16 * q + r;
+          const unsigned int code = (unsigned int)(word >> (4 * r)) & 15u;
+          // reached, but not in the history: a deeper depth, written when found
+          if (code != 0u || ((vis >> i) & 1ull) == 0ull) rows.row[i][u] = code == 0u ? -1 : (int32_t)code - 1;
+        }
       }
     }
-    const unsigned long long vis = valid ? mb.visit[u] : 0ull;
     const unsigned deg = valid ? (unsigned)(g.off[u + 1] - g.off[u]) : 0u;
     unsigned long long any = warp_or64(vis);
     while (any) {
@@ -300,6 +340,10 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
   for (int i = threadIdx.x; i < k; i += blockDim.x)
     if (s_edges[i]) atomicAdd(&st->edges[i], s_edges[i]);
   if (blockIdx.x == 0 && threadIdx.x == 0) st->levels = L;
+  // this block's share of the history is zero again (a block that stopped
+  // early or saw an error does not count, and the next wave zeroes it all)
+  if (threadIdx.x == 0 && ok && *reinterpret_cast<volatile int32_t*>(&st->status) == ST_OK)
+    atomicAdd(&st->clean_blocks, 1u);
 }
 
 __global__ void k_ms_reset(MsState* st) {

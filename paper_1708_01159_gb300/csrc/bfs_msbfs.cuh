@@ -7,22 +7,24 @@ namespace bfs {
 
 constexpr int kMsThreads = 256;
 constexpr int kMsMaxRoots = 64;
-// Depths up to this value are kept as 4-bit codes (code d + 1) until the wave
-// ends; deeper ones (code 15) are written to the output when found.
-constexpr int32_t kMsCodeMaxDepth = 13;
+// Depths below this value are recorded in the per-level history (one mask per
+// vertex and depth) until the wave ends; deeper ones are written to the output
+// when found.
+constexpr int32_t kMsHistLevels = 15;
 
 // One wave's device buffers (a set): every traversal state the kernel keeps.
 struct MsBuffers {
   unsigned long long* visit;     // n masks: bit i = reached by root i
-  unsigned long long* front[2];  // n masks each: bit i = in root i's frontier (nonzero only on frontier vertices)
+  unsigned long long* hist;      // kMsHistLevels x n masks: hist[d n + u] bit i = root i reached u at depth d
+                                 // (written once per vertex and depth, read by the final pass; zero between waves)
+  unsigned long long* front[2];  // n masks each: bit i = in root i's frontier, level L's in front[L & 1]
   unsigned long long* next;      // n masks: bits pushed to the vertex during a push level (zero between levels)
-  unsigned long long* codes;     // 4 n words: vertex u's 64 nibbles in codes[4u .. 4u + 3], nibble i for root i
   int32_t* flist[2];             // frontier vertex lists (any lane), for level L in flist[L & 1]
   int32_t* tlist;                // vertices whose next mask became nonzero during a push level
 };
 
-// Bytes of one set for n vertices (visit, two frontiers, next, codes, three lists).
-constexpr long long ms_set_bytes_per_vertex() { return 8 + 16 + 8 + 32 + 12; }
+// Bytes of one set for n vertices (visit, history, two frontiers, next, three lists).
+constexpr long long ms_set_bytes_per_vertex() { return 8 + 8 * kMsHistLevels + 16 + 8 + 12; }
 
 struct MsState {
   unsigned long long bar64;        // monotonic arrival count of the grid barriers (reset before each wave)
@@ -32,6 +34,12 @@ struct MsState {
   unsigned int ttail[2];           // touched list length of a push level L in slot L % 2
   unsigned long long fedges[4];    // out-degree sum of level L's frontier, slot L % 4
   unsigned long long edges[kMsMaxRoots];  // reached-edge count per root
+  // Between waves the history arrays are all zero when clean_blocks ==
+  // clean_grid: every block of the last wave cleared what the wave set (the
+  // counts are not reset by k_ms_reset; a new set is zeroed when it is
+  // allocated).
+  unsigned int clean_blocks;
+  unsigned int clean_grid;
 };
 
 struct MsConfig {

@@ -572,7 +572,7 @@ def test_persistent_grid_blocks(grid_blocks):
 
 @pytest.mark.parametrize("which", ["rmat", "grid"])
 @pytest.mark.parametrize("push_mode", [0, 1])
-@pytest.mark.parametrize("alpha,grid_blocks", [(1, 0), (8, 3), (1 << 20, 0), (8, 1 << 20)])
+@pytest.mark.parametrize("alpha,grid_blocks", [(1, 0), (8, 3), (64, 0), (1 << 20, 0), (8, 1 << 20)])
 def test_batch_configs(which, push_mode, alpha, grid_blocks):
     """Multi-source BFS in every configuration (alpha 1: pull from level 1 on;
     huge alpha: push only) equals independent oracle runs, repeated and isolated
@@ -589,6 +589,38 @@ def test_batch_configs(which, push_mode, alpha, grid_blocks):
         edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
         assert np.array_equal(out.cpu().numpy().reshape(len(roots), g.n), D)
         assert np.array_equal(edges, E)
+
+
+@pytest.mark.parametrize("alpha", [1, 4, 1 << 20])
+def test_batch_depth_history_boundary(alpha):
+    """Depths on both sides of the end of the multi-source depth history (the
+    frontier masks of depths 0-14 are kept for the final pass; deeper depths
+    are written when found): a path of 80 vertices with a 40-vertex clique
+    hung on path vertex 16, roots along the path, so that with alpha 4 the
+    levels that reach the clique pull (frontier edges x 4 > m) between push
+    levels at depths 14-18, and pull-only and push-only as well."""
+    P, C = 80, 40
+    src, dst = [], []
+    for i in range(P - 1):
+        src.append(i)
+        dst.append(i + 1)
+    for a in range(C):
+        src.append(16)
+        dst.append(P + a)
+        for b in range(a + 1, C):
+            src.append(P + a)
+            dst.append(P + b)
+    g = gg.from_edges(P + C, np.array(src, np.int32), np.array(dst, np.int32), name="path+clique")
+    roots = np.array([0, 1, 2, 3, 0, 79, 60, 30, P + 5, 15, 14], np.int32)
+    D, E = oracle.bfs_batch(g.off, g.idx, roots)
+    assert D.max() > 20  # depths well past the history
+    with make(g) as G:
+        for push_mode in (0, 1):
+            bfs.bfs_batch_set_config(G.handle, push_mode, alpha, 0)
+            out = torch.full((len(roots) * g.n,), -7, dtype=torch.int32, device="cuda")
+            edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
+            assert np.array_equal(out.cpu().numpy().reshape(len(roots), g.n), D)
+            assert np.array_equal(edges, E)
 
 
 def test_batch_uneven_graphs_concurrently():
