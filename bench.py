@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-grid", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-only", action="store_true",
+                   help="only the serving section, one JSON object (the main run starts it as a child process)")
     p.add_argument("--serve-rates", default="1000,4000,16000,50000", help="offered loads (queries/s)")
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--mode", default="default", choices=["default", "persistent", "graph", "host_loop"],
@@ -532,6 +534,7 @@ def bench_serve(bfs, torch, args):
                      "the drain"}
     budget = 40 << 30
     out["mem_budget_bytes"] = budget
+    out["cuda_device_max_connections"] = os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8 (default)")
     s = bfs.bfs_serve_create(mem_budget_bytes=budget, max_inflight=256, num_streams=256, queue_capacity=1 << 17,
                              merge_batch=64)
     try:
@@ -802,7 +805,7 @@ def run_ours(args):
         line["high_diameter"] = bench_grid(bfs, torch, stream)
         progress("high-diameter done")
     if not args.no_serve:
-        line["serve"] = bench_serve(bfs, torch, args)
+        line["serve"] = serve_in_child(args, local)
         progress("serve done")
 
     # the oracle on the host, bounded sample (rank 0, one GPU)
@@ -841,8 +844,39 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def serve_in_child(args, local):
+    """The serving section in a child process on the same GPU, started with 32
+    hardware work queues instead of CUDA's default 8 (the setting is read when
+    a process creates its CUDA context): with 8, the query server's short
+    queries wait behind long ones (a 4096^2 grid query runs about 90 ms) of
+    other streams that share their hardware queue. The other sections keep the
+    default, which the graph driver's conditional graphs run faster under."""
+    env = dict(os.environ, CUDA_DEVICE_MAX_CONNECTIONS="32", BENCH_SERVE_DEVICE=str(local))
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE", "MASTER_ADDR", "MASTER_PORT"):
+        env.pop(k, None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--serve-only", "--serve-rates", args.serve_rates,
+           "--serve-seconds", str(args.serve_seconds)]
+    r = subprocess.run(cmd, env=env, stdout=subprocess.PIPE, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"serving section failed (exit {r.returncode})")
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    return json.loads(lines[-1])
+
+
+def run_serve_only(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("BENCH_SERVE_DEVICE", "0")))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1708_01159_gb300 as bfs
+    print(json.dumps(bench_serve(bfs, torch, args)), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.serve_only:
+        run_serve_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

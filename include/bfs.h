@@ -300,7 +300,11 @@ int bfs_run_static(const int32_t* row_offsets, const int32_t* col_indices, int64
  * on the device; each wave root's depths go straight to its query's buffer.
  * Results are the same as alone: depths are exact. Workspaces, depth buffers
  * and wave sets are allocated when a graph is registered; the dispatcher
- * allocates no device memory (a unit whose pool is empty waits).
+ * allocates no device memory (a unit whose pool is empty waits). A serving
+ * process should start with CUDA_DEVICE_MAX_CONNECTIONS=32 in its environment
+ * (read when the CUDA context is created): with CUDA's default of 8 hardware
+ * queues, a unit's completion copy waits in a queue that other streams share,
+ * behind long traversals, and short queries wait with it.
  */
 typedef struct bfs_server* bfs_server_t;
 

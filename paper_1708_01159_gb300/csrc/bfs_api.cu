@@ -491,6 +491,43 @@ long long ppm_to_count_threshold(long long t, long long n) {
 // way it leaves no node for the device. A test on a ppm share becomes the same
 // test on the count. False when the tree is too large for it or node 0 does
 // not root a tree (a node reached twice).
+// The tree as one graph sees it: every test on a graph feature is decided by
+// the graph's own features (the node becomes the child it takes), and a test
+// whose two sides end in leaves of one class becomes that leaf, bottom up. The
+// prediction is the same for every level of the graph; the level-feature
+// tests and leaves left are fewer, so the per-level evaluation is shorter and
+// the leaf boxes larger. Children keep larger indices than their parents. An
+// input whose shared subtrees would be copied past 4x its size is returned
+// unchanged.
+std::vector<TreeNode> simplify_tree(const std::vector<TreeNode>& t, const long long* gfeat) {
+  std::vector<TreeNode> out;
+  const size_t cap = 4 * t.size() + 16;
+  bool ok = true;
+  std::function<int(int)> rec = [&](int i) -> int {
+    while (t[i].f >= 0 && is_graph_feature(t[i].f)) i = gfeat[t[i].f] <= t[i].t ? t[i].l : t[i].r;
+    if (!ok || out.size() >= cap) {
+      ok = false;
+      return 0;
+    }
+    const int me = (int)out.size();
+    out.push_back(t[i]);
+    if (t[i].f < 0) return me;
+    const int l = rec(t[i].l);
+    const int r = rec(t[i].r);
+    if (!ok) return 0;
+    if (out[l].f < 0 && out[r].f < 0 && out[l].v == out[r].v) {
+      out[me] = out[l];  // the two leaves were the last entries appended
+      out.resize((size_t)me + 1);
+      return me;
+    }
+    out[me].l = l;
+    out[me].r = r;
+    return me;
+  };
+  rec(0);
+  return ok ? out : t;
+}
+
 bool build_qs(const std::vector<TreeNode>& t, const long long* gfeat, QsTree* q) {
   if (t.empty() || t.size() > 1024) return false;
   std::memset(q, 0, sizeof *q);
@@ -598,13 +635,15 @@ int sync_tree(bfs_graph* g) {
   std::lock_guard<std::mutex> lk(ts.mu);
   std::lock_guard<std::mutex> lk2(g->mu);
   if (g->tree_version == ts.version && g->tree) return BFS_OK;
-  // one device block: the node array, then the bit-parallel form when it exists
-  const size_t tree_bytes = ts.nodes.size() * sizeof(TreeNode);
+  // one device block: the graph's simplified node array, then its
+  // bit-parallel form when it exists
+  const std::vector<TreeNode> nodes = simplify_tree(ts.nodes, g->dg.gfeat);
+  const size_t tree_bytes = nodes.size() * sizeof(TreeNode);
   const size_t qs_off = (tree_bytes + 15) & ~size_t(15);
   QsTree qs;
-  const bool has_qs = build_qs(ts.nodes, g->dg.gfeat, &qs);
+  const bool has_qs = build_qs(nodes, g->dg.gfeat, &qs);
   std::vector<char> host(qs_off + sizeof(QsTree), 0);
-  std::memcpy(host.data(), ts.nodes.data(), tree_bytes);
+  std::memcpy(host.data(), nodes.data(), tree_bytes);
   if (has_qs) std::memcpy(host.data() + qs_off, &qs, sizeof qs);
   void* p = nullptr;
   TRY(dmalloc(&p, host.size()));
@@ -616,7 +655,7 @@ int sync_tree(bfs_graph* g) {
   g->trees.push_back(static_cast<TreeNode*>(p));
   g->tree = static_cast<TreeNode*>(p);
   g->tree_qs = has_qs ? reinterpret_cast<QsTree*>(static_cast<char*>(p) + qs_off) : nullptr;
-  g->tree_nodes = (int32_t)ts.nodes.size();
+  g->tree_nodes = (int32_t)nodes.size();
   g->tree_version = ts.version;
   return BFS_OK;
 }
