@@ -134,7 +134,13 @@ typedef struct bfs_options {
                                 per flush (the default, and the only mode of the other variants), 1 one
                                 global atomic per warp, 2 one global atomic per vertex. Nonzero only
                                 with BFS_MODE_HOST_LOOP. */
-  int32_t reserved[3];       /* must be zero */
+  int32_t host_async;        /* with depth_on_host and no stats: 1 returns once the copy to depth_out is
+                                enqueued on `stream` (the caller synchronises `stream` before reading
+                                depth_out), so that with pinned host memory one traversal's copy
+                                overlaps the next traversal on another stream (a copy to pageable
+                                memory completes before the call returns); 0 (the default) returns
+                                after the copy has landed */
+  int32_t reserved[2];       /* must be zero */
 } bfs_options;
 
 typedef struct bfs_run_stats {
@@ -208,7 +214,8 @@ int bfs_run(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t stream
 
 /*
  * bfs_run with options and statistics. With opts->depth_on_host, depth_out is
- * host memory and the call returns after the result has been copied there.
+ * host memory and the call returns after the result has been copied there
+ * (with opts->host_async, once the copy is enqueued on `stream`).
  * With stats != NULL the call synchronises `stream` and fills *stats (host);
  * it then also returns the device-side status (BFS_ERR_TIMEOUT if a bounded
  * wait gave up). opts may be NULL (tree switching, device output).

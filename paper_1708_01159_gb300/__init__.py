@@ -79,7 +79,8 @@ class _GraphInfo(ctypes.Structure):
 
 class _Options(ctypes.Structure):
     _fields_ = [("forced_variant", ctypes.c_int32), ("depth_on_host", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("grid_blocks", ctypes.c_int32), ("count_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("grid_blocks", ctypes.c_int32), ("count_mode", ctypes.c_int32), ("host_async", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Stats(ctypes.Structure):
@@ -264,14 +265,16 @@ def bfs_run(g: int, root: int, depth_out, stream=None) -> None:
 
 def bfs_run_ex(g: int, root: int, depth_out, stream=None, forced_variant: int = VARIANT_TREE,
                depth_on_host: Optional[bool] = None, stats: bool = False, log_capacity: int = 0,
-               mode: int = MODE_DEFAULT, grid_blocks: int = 0, count_mode: int = 0):
+               mode: int = MODE_DEFAULT, grid_blocks: int = 0, count_mode: int = 0, host_async: bool = False):
     """BFS with options. Returns a stats dict when stats=True (then the stream is synchronised).
     grid_blocks: persistent driver only, blocks of the cooperative grid (0: a full occupancy wave).
-    count_mode: host-loop driver only, how vertex push appends to the next queue (COUNT_MODES)."""
+    count_mode: host-loop driver only, how vertex push appends to the next queue (COUNT_MODES).
+    host_async: with host output (pinned) and no stats, return once the copy is enqueued on the
+    stream; synchronise the stream before reading depth_out."""
     p, dev, _ = _ptr(depth_out, what="depth_out")
     host = (not dev) if depth_on_host is None else bool(depth_on_host)
     opts = _Options(forced_variant=int(forced_variant), depth_on_host=int(host), mode=int(mode),
-                    grid_blocks=int(grid_blocks), count_mode=int(count_mode))
+                    grid_blocks=int(grid_blocks), count_mode=int(count_mode), host_async=int(bool(host_async)))
     st = None
     logs = None
     if stats:

@@ -1438,13 +1438,13 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
   if (!depth_out) return fail(BFS_ERR_INVALID_ARG, "depth_out is null");
   if (root < 0 || root >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root %d not in [0, %d)", root, g->dg.n);
   int32_t forced = -1, mode = BFS_MODE_DEFAULT, grid_blocks = 0, count_mode = CM_BLOCK;
-  bool host_out = false;
+  bool host_out = false, host_async = false;
   if (opts) {
     if (opts->forced_variant < -1 || opts->forced_variant >= V_FORCED_NUM)
       return fail(BFS_ERR_INVALID_ARG, "forced_variant %d out of range", opts->forced_variant);
     if (opts->mode < BFS_MODE_DEFAULT || opts->mode > BFS_MODE_HOST_LOOP)
       return fail(BFS_ERR_INVALID_ARG, "mode %d out of range", opts->mode);
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 2; ++k)
       if (opts->reserved[k]) return fail(BFS_ERR_INVALID_ARG, "reserved option fields must be zero");
     if (opts->count_mode < 0 || opts->count_mode >= CM_NUM)
       return fail(BFS_ERR_INVALID_ARG, "count_mode %d out of range", opts->count_mode);
@@ -1457,6 +1457,10 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
     forced = opts->forced_variant;
     mode = opts->mode;
     host_out = opts->depth_on_host != 0;
+    if (opts->host_async != 0 && opts->host_async != 1) return fail(BFS_ERR_INVALID_ARG, "host_async is 0 or 1");
+    if (opts->host_async && (!host_out || stats))
+      return fail(BFS_ERR_INVALID_ARG, "host_async applies to host output without statistics");
+    host_async = opts->host_async != 0;
     grid_blocks = opts->grid_blocks;
   }
   DeviceGuard dgd(g->device);
@@ -1496,7 +1500,7 @@ int bfs_run_ex(bfs_graph_t g, int32_t root, int32_t* depth_out, bfs_stream_t str
     }
     if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "stats: %s", cudaGetErrorString(e));
   }
-  if (r == BFS_OK && host_out && !stats) {
+  if (r == BFS_OK && host_out && !stats && !host_async) {
     cudaError_t e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) r = fail(BFS_ERR_CUDA, "sync: %s", cudaGetErrorString(e));
   }

@@ -235,6 +235,30 @@ def test_unaligned_depth_output_and_host_output():
         assert np.array_equal(pinned.numpy(), ref.depth)
 
 
+def test_host_output_async_on_two_streams():
+    """host_async: each call returns once its copy is enqueued; 12 roots
+    alternating between two streams, each into its own pinned buffer, equal
+    the oracle once both streams are synchronised. host_async needs host
+    output and no statistics."""
+    g = gg.rmat(13, 16, seed=19)
+    roots = [int(r) for r in gg.sample_roots(g, 12, seed=20)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    with make(g) as G:
+        bufs = [torch.full((g.n,), -7, dtype=torch.int32).pin_memory() for _ in roots]
+        torch.cuda.synchronize()
+        for i, r in enumerate(roots):
+            bfs.bfs_run_ex(G.handle, r, bufs[i], streams[i & 1], depth_on_host=True, host_async=True)
+        for st in streams:
+            st.synchronize()
+        for r, b in zip(roots, bufs):
+            assert np.array_equal(b.numpy(), oracle.bfs(g.off, g.idx, r).depth)
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for kw in ({"host_async": True}, {"host_async": True, "depth_on_host": True, "stats": True}):
+            with pytest.raises(bfs.BFSError) as e:
+                bfs.bfs_run_ex(G.handle, roots[0], d if "depth_on_host" not in kw else bufs[0], **kw)
+            assert e.value.code == bfs.BFS_ERR_INVALID_ARG
+
+
 def test_bad_graphs_rejected_on_device():
     off = np.array([0, 2, 3], np.int32)
     with pytest.raises(bfs.BFSError) as e:
