@@ -511,7 +511,18 @@ def bench_grid(bfs, torch, stream):
         out["best_fixed"] = {"variant": best, "gteps": fixed[best], "roots": fixed_roots[best],
                              "switched_gteps": switched, "switched_over_best_fixed": switched / fixed[best],
                              "note": "switched re-timed on the same roots right after the fixed variants"}
+        out["warp_width_tuning"] = warp_width_tuning(bfs, G, roots[:4])
     return out
+
+
+def warp_width_tuning(bfs, G, roots):
+    """The virtual-warp width autotuner on these roots (device time of the
+    switched traversals under each policy); the graph goes back to the
+    default policy (the mean-degree rule), which every other number uses."""
+    res = bfs.bfs_tune_warp_width(G.handle, roots)
+    bfs.bfs_set_warp_width(G.handle, 0)
+    return {"roots": len(roots), "fastest": res["name"], "ms": res["ms"],
+            "rule_over_fastest": res["ms"]["rule"] / res["ms"][res["name"]]}
 
 
 def bench_serve(bfs, torch, args):
@@ -793,6 +804,7 @@ def run_ours(args):
             "best_fixed_over_optimal": float(fixed_ms.min()) / opt_ms,
             "note": "sums of per-level kernel times from the timing harness (each variant from the same snapshot); "
                     "init and driver overheads excluded"}
+        line["warp_width_tuning"] = warp_width_tuning(bfs, G, roots[:16])
 
     # Section 3.1.4's frontier-count alternatives in the vertex push (host-loop
     # driver, push_thread forced): block-staged appends (the kernels' own),

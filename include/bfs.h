@@ -192,6 +192,48 @@ int bfs_graph_destroy(bfs_graph_t g);
 int bfs_graph_info(bfs_graph_t g, bfs_graph_info_t* info);
 
 /*
+ * Virtual-warp width policy of the push_warp variant, per graph (Section 3.1.3:
+ * virtual warps of W lanes per frontier vertex, and the right W depends on the
+ * graph and the level). BFS_VW_RULE (the default): the power of two nearest
+ * above the level's mean frontier degree floor(e / f), clamped to [4, 32];
+ * BFS_VW_RULE_X2 / BFS_VW_RULE_HALF: that width doubled / halved (clamped);
+ * BFS_VW_4 .. BFS_VW_32: one width for every level. It applies to every driver
+ * and to forced push_warp runs; the tree's choice of variant is unchanged.
+ */
+enum bfs_warp_width {
+  BFS_VW_RULE = 0,
+  BFS_VW_RULE_X2 = 1,
+  BFS_VW_RULE_HALF = 2,
+  BFS_VW_4 = 3,
+  BFS_VW_8 = 4,
+  BFS_VW_16 = 5,
+  BFS_VW_32 = 6,
+  BFS_VW_NUM = 7
+};
+
+/* Set or read a graph's width policy. Not concurrent with runs on the graph
+ * (runs already enqueued keep the policy they were launched with).
+ * BFS_ERR_INVALID_ARG for a policy outside [0, BFS_VW_NUM). */
+int bfs_set_warp_width(bfs_graph_t g, int32_t policy);
+int bfs_get_warp_width(bfs_graph_t g, int32_t* policy);
+
+typedef struct bfs_warp_tune {
+  int32_t policy;          /* the fastest policy, now set on the graph */
+  int32_t reserved;
+  float ms[BFS_VW_NUM];    /* device time of the k traversals under each policy */
+} bfs_warp_tune;
+
+/*
+ * Autotune the width policy: for each policy, one untimed traversal and then
+ * the k traversals from roots (host, 1..4096 int32) timed on `stream` with the
+ * default driver and the tree; the fastest policy is set on the graph and
+ * returned with every policy's time (host struct). Synchronous; allocates an
+ * n-entry depth buffer for its duration. Not concurrent with other runs on the
+ * graph.
+ */
+int bfs_tune_warp_width(bfs_graph_t g, const int32_t* roots, int32_t k, bfs_stream_t stream, bfs_warp_tune* out);
+
+/*
  * Load the process-wide decision tree (Section 2.1, Section 4.3: the trained
  * tree exported as an array plus a lookup function) from a text file, or with
  * NULL restore the built-in tree. File format: optional '#' comment lines, then

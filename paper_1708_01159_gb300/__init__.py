@@ -110,6 +110,14 @@ class _BatchConfig(ctypes.Structure):
                 ("grid_blocks", ctypes.c_int32)]
 
 
+# virtual-warp width policies of the push_warp variant (enum bfs_warp_width)
+WARP_WIDTHS = ("rule", "rule_x2", "rule_half", "w4", "w8", "w16", "w32")
+
+
+class _WarpTune(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms", ctypes.c_float * len(WARP_WIDTHS))]
+
+
 class _LevelProfile(ctypes.Structure):
     _fields_ = [("features", ctypes.c_int64 * NUM_FEATURES), ("ms", ctypes.c_float * NUM_VARIANTS),
                 ("tree_variant", ctypes.c_int32), ("pad", ctypes.c_int32)]
@@ -152,6 +160,9 @@ def lib():
             "bfs_debug_fail_alloc_after": (ctypes.c_int, [ctypes.c_int]),
             "bfs_debug_stall_next_launch": (ctypes.c_int, [ctypes.c_int]),
             "bfs_run_static": (ctypes.c_int, [vp, vp, c_i64, c_i64, c_i32, vp, vp]),
+            "bfs_set_warp_width": (ctypes.c_int, [vp, c_i32]),
+            "bfs_get_warp_width": (ctypes.c_int, [vp, ctypes.POINTER(c_i32)]),
+            "bfs_tune_warp_width": (ctypes.c_int, [vp, vp, c_i32, vp, ctypes.POINTER(_WarpTune)]),
             "bfs_batch_set_config": (ctypes.c_int, [vp, ctypes.POINTER(_BatchConfig)]),
             "bfs_batch_tune": (ctypes.c_int, [vp, vp, c_i32, vp, vp, ctypes.POINTER(_BatchConfig)]),
             "bfs_serve_create": (ctypes.c_int, [ctypes.POINTER(_ServeConfig), ctypes.POINTER(vp)]),
@@ -317,6 +328,58 @@ def bfs_run_batch(g: int, roots, depth_out, stream=None, edges: bool = False):
     _check(lib().bfs_run_batch(g, r.ctypes.data, r.size, p, _stream(stream),
                                e.ctypes.data if e is not None else None), "bfs_run_batch")
     return e[: r.size] if e is not None else None
+
+
+def bfs_set_warp_width(g: int, policy) -> None:
+    """Set a graph's virtual-warp width policy (an index or a name of WARP_WIDTHS)."""
+    p = WARP_WIDTHS.index(policy) if isinstance(policy, str) else int(policy)
+    _check(lib().bfs_set_warp_width(g, p), "bfs_set_warp_width")
+
+
+def bfs_get_warp_width(g: int) -> int:
+    """A graph's virtual-warp width policy (index into WARP_WIDTHS)."""
+    p = ctypes.c_int32(0)
+    _check(lib().bfs_get_warp_width(g, ctypes.byref(p)), "bfs_get_warp_width")
+    return p.value
+
+
+def bfs_tune_warp_width(g: int, roots, stream=None) -> dict:
+    """Autotune the width policy on these roots (synchronous): the fastest is set
+    on the graph; returns it and every policy's device time in ms."""
+    r = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
+    out = _WarpTune()
+    _check(lib().bfs_tune_warp_width(g, r.ctypes.data, int(r.size), _stream(stream), ctypes.byref(out)),
+           "bfs_tune_warp_width")
+    return {"policy": out.policy, "name": WARP_WIDTHS[out.policy],
+            "ms": {WARP_WIDTHS[i]: float(out.ms[i]) for i in range(len(WARP_WIDTHS))}}
+
+
+def warp_width_cache_key(device_name: str, info: dict) -> str:
+    """Key of a graph in the width-tuning cache: the GPU's name and the graph's
+    class (size and out-degree summary)."""
+    deg = ",".join(str(int(x)) for x in info["deg_summary"])
+    return f"{device_name}|n={info['n']}|m={info['m']}|deg={deg}"
+
+
+def tune_warp_width_cached(g: int, roots, cache_path: str, device_name: str, info: dict, stream=None) -> dict:
+    """The width policy from a JSON cache (keyed by warp_width_cache_key), or
+    tuned on `roots` and added to the cache; the policy is set on the graph."""
+    import json
+    key = warp_width_cache_key(device_name, info)
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as fh:
+            cache = json.load(fh)
+    if key in cache:
+        bfs_set_warp_width(g, cache[key]["policy"])
+        return dict(cache[key], cached=True)
+    res = bfs_tune_warp_width(g, roots, stream)
+    cache[key] = res
+    tmp = cache_path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path)
+    return dict(res, cached=False)
 
 
 def bfs_batch_set_config(g: int, push_mode: int, alpha: int, grid_blocks: int = 0) -> None:

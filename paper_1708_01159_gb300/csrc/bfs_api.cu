@@ -1413,6 +1413,76 @@ int bfs_graph_info(bfs_graph_t g, bfs_graph_info_t* info) {
   return BFS_OK;
 }
 
+static_assert((int)BFS_VW_NUM == (int)VW_NUM && (int)BFS_VW_RULE == (int)VW_RULE && (int)BFS_VW_32 == (int)VW_32,
+              "width policy numbering");
+
+int bfs_set_warp_width(bfs_graph_t g, int32_t policy) {
+  TRY(check_graph(g));
+  if (policy < 0 || policy >= VW_NUM) return fail(BFS_ERR_INVALID_ARG, "width policy %d out of range", policy);
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->dg.vw_policy = policy;
+  return BFS_OK;
+}
+
+int bfs_get_warp_width(bfs_graph_t g, int32_t* policy) {
+  TRY(check_graph(g));
+  if (!policy) return fail(BFS_ERR_INVALID_ARG, "null argument");
+  std::lock_guard<std::mutex> lk(g->mu);
+  *policy = g->dg.vw_policy;
+  return BFS_OK;
+}
+
+int bfs_tune_warp_width(bfs_graph_t g, const int32_t* roots, int32_t k, bfs_stream_t stream_, bfs_warp_tune* out) {
+  TRY(check_graph(g));
+  if (!roots || !out || k < 1 || k > 4096) return fail(BFS_ERR_INVALID_ARG, "tune takes 1..4096 roots and an output");
+  for (int32_t i = 0; i < k; ++i)
+    if (roots[i] < 0 || roots[i] >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root %d out of range", roots[i]);
+  DeviceGuard dgd(g->device);
+  TRY(sync_tree(g));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+  void* depth = nullptr;
+  TRY(dmalloc(&depth, (size_t)g->dg.n * 4));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int r = BFS_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = fail(BFS_ERR_CUDA, "events");
+  const int32_t keep = g->dg.vw_policy;
+  int32_t best = keep;
+  float best_ms = 1e30f;
+  for (int32_t p = 0; p < VW_NUM && r == BFS_OK; ++p) {
+    g->dg.vw_policy = p;
+    float ms = 0.f;
+    for (int32_t i = -1; i < k && r == BFS_OK; ++i) {  // i = -1: untimed
+      Workspace* ws = nullptr;
+      r = acquire(g, s, &ws);
+      if (r != BFS_OK) break;
+      if (i == 0 && cudaEventRecord(e0, s) != cudaSuccess) r = fail(BFS_ERR_CUDA, "event record");
+      if (r == BFS_OK)
+        r = launch_run(g, ws, roots[i < 0 ? 0 : i], static_cast<int32_t*>(depth), -1, BFS_MODE_DEFAULT, s);
+      const int rr = release(g, ws, s);
+      if (r == BFS_OK) r = rr;
+    }
+    if (r == BFS_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+      r = fail(BFS_ERR_CUDA, "tuning run failed");
+    if (r != BFS_OK) break;
+    out->ms[p] = ms;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = p;
+    }
+  }
+  g->dg.vw_policy = r == BFS_OK ? best : keep;
+  if (r == BFS_OK) {
+    out->policy = best;
+    out->reserved = 0;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(depth);
+  return r;
+}
+
 int bfs_load_tree(const char* path_or_null) {
   std::vector<TreeNode> nodes;
   if (!path_or_null) {

@@ -34,6 +34,22 @@ enum Variant : int32_t {
   V_FORCED_NUM = 7,
 };
 
+// Virtual-warp width policy of the push_warp variant (Section 3.1.3: the right
+// width depends on the graph and the level), chosen per graph by the tuner:
+// the rule (the power of two nearest above the frontier's mean degree,
+// clamped to [4, 32]), the rule doubled or halved (clamped), or one fixed
+// width for every level.
+enum WarpWidthPolicy : int32_t {
+  VW_RULE = 0,
+  VW_RULE_X2 = 1,
+  VW_RULE_HALF = 2,
+  VW_4 = 3,
+  VW_8 = 4,
+  VW_16 = 5,
+  VW_32 = 6,
+  VW_NUM = 7,
+};
+
 // How a push level appends the vertices it reaches to the next queue (whose
 // tail is the next frontier size). Section 3.1.4 compares a global atomic per
 // vertex with warp and block reductions in front of it; the level kernels use
@@ -151,7 +167,7 @@ struct DevGraph {
   int32_t words;  // ceil(n / 32)
   int32_t symmetric;
   int32_t n_active;  // vertices with at least one in- or out-edge (the others start visited)
-  int32_t pad_;
+  int32_t vw_policy;  // virtual-warp width policy of the push_warp variant (VW_*)
   long long gfeat[F_NUM];  // the graph features (is_graph_feature); level slots unused
 };
 
@@ -171,7 +187,7 @@ struct RunState {
   int32_t status;            // ST_OK / ST_TIMEOUT
   int32_t vw;                // virtual warp width of the push_warp variant at this level
   int32_t levels;            // levels completed (set when the run ends)
-  int32_t pad0_;
+  int32_t vw_policy;         // the graph's width policy, copied by k_init (graph and host-loop drivers)
   unsigned long long next_count;  // f_{L+1}: output queue tail
   unsigned long long next_edges;  // e_{L+1}
   long long frontier_edges;  // e_L

@@ -338,16 +338,23 @@ __device__ __forceinline__ bool in_leaf_box(int32_t bound, int32_t L, long long 
 }
 
 // Section 4.1 unknown-prediction rule on a walk's result (or the forced
-// variant), and the virtual-warp width: the power of two nearest above the
-// frontier's mean degree floor(e / f), clamped to [4, 32] (floor(e / f) <= k is
-// e < (k + 1) f).
+// variant), and the virtual-warp width under the graph's policy: the rule is
+// the power of two nearest above the frontier's mean degree floor(e / f),
+// clamped to [4, 32] (floor(e / f) <= k is e < (k + 1) f).
 __device__ __forceinline__ int32_t finish_variant(int32_t v, int32_t L, int32_t prev, long long f, long long e,
-                                                  int32_t* vw, bool forced) {
+                                                  int32_t* vw, bool forced, int32_t policy) {
   if (!forced) {
     if (v < 0 || v >= V_NUM) v = (L == 0) ? kLevel0Default : prev;  // unknown prediction
     if (v < 0 || v >= V_NUM) v = kLevel0Default;
   }
-  *vw = (f <= 0 || e < 5 * f) ? 4 : e < 9 * f ? 8 : e < 17 * f ? 16 : 32;
+  const int32_t rule = (f <= 0 || e < 5 * f) ? 4 : e < 9 * f ? 8 : e < 17 * f ? 16 : 32;
+  *vw = policy == VW_RULE_X2     ? min(32, 2 * rule)
+        : policy == VW_RULE_HALF ? max(4, rule / 2)
+        : policy == VW_4         ? 4
+        : policy == VW_8         ? 8
+        : policy == VW_16        ? 16
+        : policy == VW_32        ? 32
+                                 : rule;
   return v;
 }
 
@@ -1101,6 +1108,7 @@ __global__ void __launch_bounds__(kThreads) k_init(DevGraph g, Buffers b, RunSta
     st->frontier = 0;
     st->status = ST_OK;
     st->vw = 32;
+    st->vw_policy = g.vw_policy;
     st->levels = 0;
     st->frontier_edges = 0;
     st->discovered = 0;
@@ -1174,7 +1182,7 @@ __global__ void __launch_bounds__(kDecideThreads) k_decide(DevGraph g, Buffers b
   if (v < 0 && qs == nullptr && s.tree != nullptr && s.tree_nodes > 0)
     v = walk_tree(g, s.tree, s.tree_nodes, L, f, e, discovered);
   int32_t vw = 32;
-  v = finish_variant(v, L, s.variant, f, e, &vw, s.forced >= 0);
+  v = finish_variant(v, L, s.variant, f, e, &vw, s.forced >= 0, s.vw_policy);
   for (int i = 0; i < F_NUM; ++i) s.feat[i] = feature_value(g, i, L, f, e, discovered);
   s.variant = v;
   s.vw = vw;
@@ -1475,7 +1483,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_bfs_persistent(DevGraph g, Buff
       }
     } else if (v < 0 && tree != nullptr && tree_nodes > 0)
       v = walk_tree(g, tree, tree_nodes, L, f, (long long)e, discovered);
-    v = finish_variant(v, L, prev, f, (long long)e, &vw, forced >= 0);
+    v = finish_variant(v, L, prev, f, (long long)e, &vw, forced >= 0, g.vw_policy);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->tail3[(L + 2) % 3] = 0;  // the slot of level L - 2's barrier, which every block has left
       st->edg3[(L + 2) % 3] = 0;
@@ -1518,7 +1526,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_profile_level(DevGraph g, Buffe
   cta_pipe_init(bar);
   CtaPipe pp{ubuf, bar, 0u, 0u, 0u};
   int32_t vw = 32;
-  v = finish_variant(v, L, -1, f, (long long)e, &vw, true);
+  v = finish_variant(v, L, -1, f, (long long)e, &vw, true, g.vw_policy);
   unsigned long long bar_target = 0;
   if (!grid_arrive_wait(&st->bar64, bar_target, &st->status)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->prof_t0 = (long long)global_ns();

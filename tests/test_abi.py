@@ -154,3 +154,11 @@ def test_stall_hook_modes_checked_on_the_host(lib):
     assert lib.bfs_debug_stall_next_launch(4) == bfs.BFS_ERR_INVALID_ARG
     assert lib.bfs_debug_stall_next_launch(-1) == bfs.BFS_ERR_INVALID_ARG
     assert lib.bfs_debug_stall_next_launch(0) == bfs.BFS_OK
+
+
+def test_warp_width_calls_checked_on_the_host(lib):
+    p = ctypes.c_int32(0)
+    assert lib.bfs_set_warp_width(None, 0) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_get_warp_width(None, ctypes.byref(p)) == bfs.BFS_ERR_INVALID_ARG
+    assert lib.bfs_tune_warp_width(None, None, 1, None, None) == bfs.BFS_ERR_INVALID_ARG
+    assert len(bfs.WARP_WIDTHS) == 7

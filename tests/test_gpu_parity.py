@@ -712,3 +712,42 @@ def test_grid_4096_full_size():
     with make(g) as G:
         ref, st = assert_parity(g, G, r)
         assert ref.num_levels > 1000
+
+
+@pytest.mark.parametrize("policy", list(range(len(bfs.WARP_WIDTHS))))
+def test_warp_width_policies_exact(policy):
+    """Every virtual-warp width policy (the mean-degree rule, doubled, halved,
+    fixed 4/8/16/32) gives the oracle's depths with push_warp forced and with
+    the tree, in the persistent and graph drivers, on a skewed, a
+    high-diameter and a directed graph."""
+    cases = ((gg.rmat(12, 16, seed=811), bfs.BFS_SYMMETRIC), (gg.grid(40, 30, 0.1, seed=812), bfs.BFS_SYMMETRIC),
+             (gg.rmat(11, 8, seed=813, directed=True), 0))
+    for g, flags in cases:
+        with make(g, flags) as G:
+            bfs.bfs_set_warp_width(G.handle, policy)
+            assert bfs.bfs_get_warp_width(G.handle) == policy
+            for r in gg.sample_roots(g, 2, seed=814):
+                ref = oracle.bfs(g.off, g.idx, int(r))
+                for mode in (bfs.MODE_PERSISTENT, bfs.MODE_GRAPH):
+                    for v in (bfs.VARIANTS.index("push_warp"), bfs.VARIANT_TREE):
+                        d = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")
+                        st = bfs.bfs_run_ex(G.handle, int(r), d, forced_variant=v, mode=mode, stats=True)
+                        assert np.array_equal(d.cpu().numpy(), ref.depth), (policy, mode, v)
+                        assert st["edges_reached"] == ref.edges_reached
+
+
+def test_warp_width_tuner_sets_the_fastest():
+    g = gg.grid(120, 90, 0.1, seed=815)
+    roots = gg.sample_roots(g, 3, seed=816)
+    with make(g) as G:
+        res = bfs.bfs_tune_warp_width(G.handle, roots)
+        assert 0 <= res["policy"] < len(bfs.WARP_WIDTHS)
+        assert res["ms"][res["name"]] == min(res["ms"].values()) and min(res["ms"].values()) > 0
+        assert bfs.bfs_get_warp_width(G.handle) == res["policy"]
+        with pytest.raises(bfs.BFSError) as e:
+            bfs.bfs_set_warp_width(G.handle, len(bfs.WARP_WIDTHS))
+        assert e.value.code == bfs.BFS_ERR_INVALID_ARG
+        d = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for r in roots:  # exact under the tuned policy
+            bfs.bfs_run(G.handle, int(r), d)
+            assert np.array_equal(d.cpu().numpy(), oracle.bfs(g.off, g.idx, int(r)).depth)
