@@ -726,7 +726,9 @@ def run_ours(args):
     line["e2e"] = {"value": float(edges.sum()) / 2.0 / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * R,
                    "d2h_bytes_per_step": 4 * g.n * R,
                    "note": "one step: every root's depths copied to a pinned host buffer of its own inside the timed "
-                           "region; roots alternate between two streams, each copy overlapping the next traversal"}
+                           "region; roots alternate between two streams, each copy overlapping the next traversal, "
+                           "and each traversal queued before the previous one ends (so this can exceed `value`, "
+                           "whose per-root intervals include the gap between launches on one stream)"}
     del pinned
 
     # roofline of the dominant kernel: per-level launches timed with CUDA events
