@@ -288,8 +288,10 @@ typedef struct bfs_batch_config {
   int32_t push_mode;  /* 0: one thread per frontier vertex, 1: one warp per frontier vertex */
   int32_t alpha;      /* a level pulls when its frontier's edge count x alpha exceeds m */
   float ms;           /* bfs_batch_tune: measured time of one wave with this configuration */
-  int32_t grid_blocks; /* blocks of the multi-source kernel, 0 for one full occupancy wave (larger
-                          values are clamped to it) */
+  int32_t grid_blocks; /* blocks of the multi-source kernel (larger values are clamped to one full
+                          occupancy wave); 0 for a grid sized to the graph: one block per 4096
+                          vertices, at least a quarter of the SMs, at most one full occupancy
+                          wave (so that small graphs' waves on several streams run together) */
 } bfs_batch_config;
 
 /* Set the graph's multi-source configuration. Errors: BFS_ERR_INVALID_ARG. */

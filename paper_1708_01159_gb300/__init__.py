@@ -385,7 +385,7 @@ def tune_warp_width_cached(g: int, roots, cache_path: str, device_name: str, inf
 def bfs_batch_set_config(g: int, push_mode: int, alpha: int, grid_blocks: int = 0) -> None:
     """Fix the multi-source launch shape of a graph: push_mode 0 (thread per vertex,
     block for hubs) or 1 (warp per vertex), pull when frontier edges x alpha > m,
-    grid_blocks (0: a full occupancy wave)."""
+    grid_blocks (0: a grid sized to the graph, one block per 4096 vertices within [SMs / 4, a full wave])."""
     c = _BatchConfig(push_mode=push_mode, alpha=alpha, grid_blocks=grid_blocks)
     _check(lib().bfs_batch_set_config(g, ctypes.byref(c)), "bfs_batch_set_config")
 

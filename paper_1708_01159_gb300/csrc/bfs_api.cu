@@ -835,7 +835,11 @@ int ms_launch_wave(bfs_graph* g, MsSet* set, const int32_t* roots, int32_t k, in
   MsState* st = set->st;
   int32_t stall = take_stall();
   void* args[] = {&dg, &mb, &st, &k, &rows, &cfg, &stall};
-  const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->ms_grid) : g->ms_grid;
+  // default: a grid sized to the graph (one block per 4096 vertices, at least
+  // a quarter of the SMs, at most one full occupancy wave), so that waves of
+  // small graphs on different streams can be resident together
+  const long long sized = std::max<long long>(((long long)g->dg.n + 4095) / 4096, std::max(1, g->sms / 4));
+  const int grid = grid_blocks > 0 ? std::min(grid_blocks, g->ms_grid) : (int)std::min<long long>(sized, g->ms_grid);
   CU(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&k_msbfs), dim3(grid), dim3(kMsThreads), args, 0, s));
   return BFS_OK;
 }
