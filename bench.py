@@ -407,7 +407,9 @@ def bench_batch(bfs, torch, stream):
 def bench_batch_graphs(bfs, torch):
     """Multi-source BFS over a batch of 32 uneven R-MAT graphs (scale 12-20, edge
     factor 8-32, seeded): each graph's 64 roots in one launch, the 32 launches
-    spread over 8 streams; against the same 2048 roots as single-source runs."""
+    spread over 8 streams (graphs of scale 16 and up tuned for 8 waves at once,
+    the others on the default grid sized to the graph); against the same 2048
+    roots as single-source runs."""
     import graphgen as gg
     specs = gg.rmat_batch_specs()
     streams = [torch.cuda.Stream() for _ in range(8)]
@@ -424,7 +426,8 @@ def bench_batch_graphs(bfs, torch):
             out = torch.empty(64 * g.n, dtype=torch.int32, device="cuda")
             outs.append(out)
             if sc >= 16:  # smaller graphs keep the default configuration
-                bfs.bfs_batch_tune(G.handle, r, out)
+                # tuned for waves that run 8 at a time (one per stream)
+                bfs.bfs_batch_tune(G.handle, r, out, concurrency=len(streams))
                 tuned += 1
             edges_total += int(bfs.bfs_run_batch(G.handle, r, out, edges=True).sum())
         single = [torch.empty(G.n, dtype=torch.int32, device="cuda") for G in Gs]

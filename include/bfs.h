@@ -308,6 +308,19 @@ int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* dept
                    bfs_batch_config* best);
 
 /*
+ * The autotuner for waves that run together: `concurrency` (1..64) waves of
+ * different graphs at once, as with a batch spread over that many streams.
+ * The grids tried are those no larger than twice a full occupancy wave
+ * divided by `concurrency` (waves of uneven graphs rarely all run at once; at
+ * least 1/16 of a full wave), halving, the three largest; the rest as
+ * bfs_batch_tune (which is concurrency 1: a full wave, 1/2 and 1/4).
+ * Smaller grids let the waves share the device, where one wave alone is
+ * fastest on the full grid.
+ */
+int bfs_batch_tune_ex(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_scratch, bfs_stream_t stream,
+                      int32_t concurrency, bfs_batch_config* best);
+
+/*
  * Single-source BFS that allocates nothing. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory while they
  * run (code working inside a memory arena it does not own, a plugin given

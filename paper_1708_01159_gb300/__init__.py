@@ -165,6 +165,7 @@ def lib():
             "bfs_tune_warp_width": (ctypes.c_int, [vp, vp, c_i32, vp, ctypes.POINTER(_WarpTune)]),
             "bfs_batch_set_config": (ctypes.c_int, [vp, ctypes.POINTER(_BatchConfig)]),
             "bfs_batch_tune": (ctypes.c_int, [vp, vp, c_i32, vp, vp, ctypes.POINTER(_BatchConfig)]),
+            "bfs_batch_tune_ex": (ctypes.c_int, [vp, vp, c_i32, vp, vp, c_i32, ctypes.POINTER(_BatchConfig)]),
             "bfs_serve_create": (ctypes.c_int, [ctypes.POINTER(_ServeConfig), ctypes.POINTER(vp)]),
             "bfs_serve_add_graph": (ctypes.c_int, [vp, vp, ctypes.POINTER(c_i32)]),
             "bfs_serve_graph_shape": (ctypes.c_int, [vp, c_i32, ctypes.POINTER(c_i32), ctypes.POINTER(c_i32)]),
@@ -390,14 +391,17 @@ def bfs_batch_set_config(g: int, push_mode: int, alpha: int, grid_blocks: int = 
     _check(lib().bfs_batch_set_config(g, ctypes.byref(c)), "bfs_batch_set_config")
 
 
-def bfs_batch_tune(g: int, roots, depth_scratch, stream=None) -> dict:
-    """Autotune the multi-source kernel on up to 64 roots; returns the chosen configuration."""
+def bfs_batch_tune(g: int, roots, depth_scratch, stream=None, concurrency: int = 1) -> dict:
+    """Autotune the multi-source kernel on up to 64 roots; returns the chosen
+    configuration. concurrency > 1: for waves of that many graphs running at
+    once (grids up to a full wave / concurrency)."""
     r = np.ascontiguousarray(np.asarray(roots, dtype=np.int32))
     p, dev, _ = _ptr(depth_scratch, what="depth_scratch")
     if not dev:
         raise ValueError("depth_scratch must be device memory")
     c = _BatchConfig()
-    _check(lib().bfs_batch_tune(g, r.ctypes.data, r.size, p, _stream(stream), ctypes.byref(c)), "bfs_batch_tune")
+    _check(lib().bfs_batch_tune_ex(g, r.ctypes.data, r.size, p, _stream(stream), int(concurrency), ctypes.byref(c)),
+           "bfs_batch_tune")
     return {"push_mode": c.push_mode, "alpha": c.alpha, "ms": c.ms, "grid_blocks": c.grid_blocks}
 
 

@@ -1643,9 +1643,15 @@ int bfs_batch_set_config(bfs_graph_t g, const bfs_batch_config* cfg) {
 
 int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_scratch, bfs_stream_t stream,
                    bfs_batch_config* best) {
+  return bfs_batch_tune_ex(g, roots, k, depth_scratch, stream, 1, best);
+}
+
+int bfs_batch_tune_ex(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* depth_scratch, bfs_stream_t stream,
+                      int32_t concurrency, bfs_batch_config* best) {
   TRY(check_graph(g));
   if (k < 1 || k > 64 || !roots || !depth_scratch || !best)
     return fail(BFS_ERR_INVALID_ARG, "tune takes 1..64 roots, a k*n scratch buffer and an output");
+  if (concurrency < 1 || concurrency > 64) return fail(BFS_ERR_INVALID_ARG, "concurrency %d not in [1, 64]", concurrency);
   for (int32_t i = 0; i < k; ++i)
     if (roots[i] < 0 || roots[i] >= g->dg.n) return fail(BFS_ERR_INVALID_ARG, "root out of range");
   DeviceGuard dgd(g->device);
@@ -1660,13 +1666,21 @@ int bfs_batch_tune(bfs_graph_t g, const int32_t* roots, int32_t k, int32_t* dept
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   const int alphas[] = {2, 4, 8, 16, 32, 64};
-  const int grids[] = {g->ms_grid, g->ms_grid / 2, g->ms_grid / 4};
+  // the grids tried: a full occupancy wave and its halves down to 1/16, those
+  // no larger than twice the device's even share of one of `concurrency` waves
+  // running together (waves of uneven graphs rarely all run at once), at
+  // least the smallest
+  const int share = std::max(std::min(g->ms_grid, 2 * g->ms_grid / concurrency), g->ms_grid / 16);
+  int grids[5], ng = 0;
+  for (int d = 1; d <= 16; d *= 2)
+    if (g->ms_grid / d <= share) grids[ng++] = std::max(1, g->ms_grid / d);
+  if (ng > 3) ng = 3;  // the three largest that qualify
   float best_ms = 1e30f;
   MsConfig best_cfg = g->ms_cfg;
   int best_grid = g->ms_grid_user;
   int r = BFS_OK;
-  for (int gi = 0; gi < 3 && r == BFS_OK; ++gi) {
-    const int grid = std::max(1, grids[gi]);
+  for (int gi = 0; gi < ng && r == BFS_OK; ++gi) {
+    const int grid = grids[gi];
     for (int pm = 0; pm < 2 && r == BFS_OK; ++pm)
       for (int a : alphas) {
         const MsConfig c{pm, a};

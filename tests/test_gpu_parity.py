@@ -685,6 +685,19 @@ def test_batch_directed_and_tuner():
         edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
         assert np.array_equal(out.cpu().numpy().reshape(64, n), D)
         assert np.array_equal(edges, E)
+        # tuned for 8 waves at once: a grid of at most 1/4 of a full wave
+        full = bfs.bfs_batch_tune(G.handle, roots, scratch, concurrency=1)
+        c8 = bfs.bfs_batch_tune(G.handle, roots, scratch, concurrency=8)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        assert 1 <= c8["grid_blocks"] <= max(1, 8 * sms // 4)
+        out.fill_(-7)
+        edges = bfs.bfs_run_batch(G.handle, roots, out, edges=True)
+        assert np.array_equal(out.cpu().numpy().reshape(64, n), D)
+        assert np.array_equal(edges, E)
+        assert full["grid_blocks"] >= c8["grid_blocks"]
+        with pytest.raises(bfs.BFSError) as e:
+            bfs.bfs_batch_tune(G.handle, roots, scratch, concurrency=0)
+        assert e.value.code == bfs.BFS_ERR_INVALID_ARG
 
 
 # --------------------------------------------------------- full-size workloads
