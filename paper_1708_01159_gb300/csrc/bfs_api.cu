@@ -1180,7 +1180,7 @@ const char* bfs_status_string(int status) {
 
 const char* bfs_last_error_detail(void) { return t_detail.c_str(); }
 
-int bfs_version(void) { return 100; }
+int bfs_version(void) { return 200; }
 
 // Test hook (not part of the public header's contract): make the n-th device
 // allocation from now fail with BFS_ERR_OOM; 0 disables.
