@@ -1449,6 +1449,9 @@ int bfs_tune_warp_width(bfs_graph_t g, const int32_t* roots, int32_t k, bfs_stre
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int r = BFS_OK;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = fail(BFS_ERR_CUDA, "events");
+  // the policy is written between launches of this thread without g->mu
+  // (acquire takes it); the call is documented as not concurrent with other
+  // runs on the graph
   const int32_t keep = g->dg.vw_policy;
   int32_t best = keep;
   float best_ms = 1e30f;
