@@ -176,10 +176,22 @@ __global__ void __launch_bounds__(kMsThreads) k_msbfs(DevGraph g, MsBuffers mb, 
               s_big[atomicAdd(&s_nbig, 1)] = v;
             } else {
               const unsigned long long fv = cur[v];
-              for (int32_t e = beg; e < end; ++e) {
-                const int32_t u = g.idx[e];
-                const unsigned long long nb = fv & ~mb.visit[u];
-                if (nb && atomicOr(&mb.next[u], nb) == 0ull) stage_put(stage, mb.tlist, ttail, u);
+              // four edges per step: their adjacency entries, then their
+              // targets' visit masks, then the pushes, each group issued
+              // together rather than one edge's chain after another
+              for (int32_t e = beg; e < end; e += 4) {
+                const int nv = min(4, end - e);
+                int32_t u[4];
+                unsigned long long vis[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) u[q] = q < nv ? g.idx[e + q] : 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) vis[q] = q < nv ? mb.visit[u[q]] : ~0ull;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const unsigned long long nb = fv & ~vis[q];
+                  if (nb && atomicOr(&mb.next[u[q]], nb) == 0ull) stage_put(stage, mb.tlist, ttail, u[q]);
+                }
               }
             }
           }
